@@ -1,0 +1,308 @@
+/*
+ * qsim.h -- C ABI of the GB300 quadrotor-training hot path of "Learning to Fly in
+ * Seconds" (Eschmann, Albani, Loianno; arXiv 2311.13081).
+ *
+ * The library simulates batches of quadrotors (Sec. IV "Methodology": 17-D state
+ * {p, q, v, omega, omega_m}, first-order motor lag, RK4 at 100 Hz), steps them with an
+ * actor MLP and exploration noise, stores transitions in a device replay buffer and
+ * trains an asymmetric TD3 actor-critic on them (Sec. IV; TD3 of Fujimoto et al. 2018),
+ * including the reward curriculum and reward recalculation (Sec. IV, Sec. VI "Ablation
+ * study"), many independent runs per launch, and reverse-mode gradients through the
+ * simulator.
+ *
+ * Conventions for every entry point:
+ *  - All sizes are element counts.  "Device pointer" means memory of the current CUDA
+ *    device (e.g. torch.Tensor.data_ptr()); "host pointer" means pageable or pinned
+ *    host memory.  Field-major layouts are written [field][env]: element (f, e) lives
+ *    at f * ld + e, where ld is the padded env count returned by qsim_info().
+ *  - Calls that take a `stream` (a cudaStream_t; NULL = legacy default stream) are
+ *    asynchronous: argument errors found on the host return at once; device-side
+ *    conditions (bounded waits that ran out, non-finite states) are recorded in the
+ *    handle's status word and returned by qsim_sync()/ac_sync().
+ *  - Nothing throws across the ABI.  On failure the return value is negative and
+ *    qsim_last_error() holds a message (thread-local, owned by the library).
+ *  - Handles own their device buffers (allocated at create, freed at destroy).  Pointer
+ *    arguments stay owned by the caller and are only borrowed for the stream-ordered
+ *    call.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QSIM_ABI_VERSION 1
+
+typedef enum qsim_status {
+    QSIM_OK = 0,
+    QSIM_EINVAL = -1,   /* bad argument: null/misaligned pointer, size out of range */
+    QSIM_ENOMEM = -2,   /* device allocation failed */
+    QSIM_ECUDA = -3,    /* a CUDA call failed (message in qsim_last_error) */
+    QSIM_ETIMEOUT = -4, /* a bounded device-side wait ran out */
+    QSIM_ESTATE = -5,   /* handle not in a state that allows the call */
+    QSIM_EVERSION = -6  /* checkpoint written by another ABI / layout */
+} qsim_status;
+
+/* Critic observation layouts (Sec. IV: the critic sees privileged information). */
+typedef enum qsim_critic_layout {
+    QSIM_CRITIC_HIST = 0,    /* actor obs (noise-free) + 4 normalised motor speeds        */
+    QSIM_CRITIC_PRIV = 1,    /* ... + true mass, inertia, thrust coeff., motor T (rel.)  */
+    QSIM_CRITIC_PAPER28 = 2  /* {p, R, v, omega, omega_m, f_r, tau_r}: the 28-D vector   */
+} qsim_critic_layout;
+
+/* Nominal vehicle (Sec. IV "standard dynamics of a quadrotor subject to motor delays";
+ * values for the Crazyflie-class platform of the paper: 27 g, 0.15 s motor constant). */
+typedef struct qsim_params {
+    float mass;          /* kg */
+    float J[3];          /* principal inertia, kg m^2 */
+    float kf;            /* thrust per rotor = kf * rpm^2, N / rpm^2 */
+    float km;            /* yaw torque per rotor = dir * km * thrust, m */
+    float motor_tau;     /* first-order motor time constant, s */
+    float rotor_pos[4][3]; /* body-frame rotor positions, m */
+    float rotor_dir[4];  /* +1 / -1 yaw-torque sign per rotor */
+    float rpm_min, rpm_max;
+    float g;             /* m/s^2, world z up */
+} qsim_params;
+
+/* Environment-set configuration (Sec. IV MDP; constants of the supplement replaced by
+ * the values documented with each field). */
+typedef struct qsim_config {
+    int32_t n_envs;          /* >= 1 */
+    int32_t n_hist;          /* action-history length N_H, 0..16 (obs = 18 + 4 N_H) */
+    int32_t episode_len;     /* truncation length in steps */
+    int32_t critic_layout;   /* qsim_critic_layout */
+    int32_t renorm_q;        /* renormalise q after each RK4 step (1) or not (0) */
+    int32_t learning_starts; /* global steps with uniform random actions (TD3 warm-up) */
+    int32_t replay_capacity; /* time slots per env in the replay ring (0 = no buffer) */
+    int32_t reserved0;
+    float dt;                /* integration step, s (0.01 = 100 Hz) */
+    uint32_t run_id;         /* random-stream id of this run */
+    uint64_t seed;           /* Philox key */
+    /* initial-state distribution: p, attitude angles, v, omega uniform in +-range */
+    float init_p, init_att, init_v, init_w, init_rpm_lo, init_rpm_hi;
+    /* domain randomisation: relative half-widths and motor-time-constant range */
+    float dr_mass, dr_J, dr_kf, tm_lo, tm_hi;
+    /* per-episode force / torque disturbance half-widths (N, N m) */
+    float dist_f, dist_tau;
+    /* actor observation noise std-devs: position, rotation matrix, velocity, omega */
+    float sig_p, sig_R, sig_v, sig_w;
+    float term_pos;          /* episode terminates when any |p_i| exceeds this, m */
+    /* reward constants C_rp C_rq C_rv C_rw C_ra C_rab C_rs (Sec. IV reward formula) */
+    float reward[7];
+    /* curriculum (Sec. IV): every `curriculum_interval` env interactions multiply each
+     * constant by its factor until it reaches its target; the exploration std-dev is
+     * multiplied by sigma_factor down to sigma_min.  interval 0 disables it. */
+    float curriculum_factor[7];
+    float curriculum_target[7];
+    float sigma_e;           /* exploration std-dev at start */
+    float sigma_factor, sigma_min;
+    int32_t recalc_rewards;  /* recompute stored rewards after each change (1) */
+    int64_t curriculum_interval;
+} qsim_config;
+
+typedef struct qsim_handle qsim_handle;
+typedef struct ac_handle ac_handle;
+
+/* Sizes and device pointers of an env set (for inspection and teacher forcing).
+ * All arrays are field-major with leading dimension `ld` unless noted. */
+typedef struct qsim_info {
+    int32_t n_envs, ld;       /* env count and padded leading dimension (multiple of 32) */
+    int32_t obs_dim;          /* actor observation dims, 18 + 4 N_H */
+    int32_t critic_obs_dim;   /* critic observation dims without the action */
+    int32_t record_fields;    /* floats per transition record: 17 s, 4 a, r, flags, priv */
+    int32_t n_priv;
+    int64_t capacity;         /* replay time slots */
+    int64_t t_now;            /* global steps taken */
+    int64_t head, size;       /* replay ring head (next slot) and filled slots */
+    float* state;             /* [17][ld] p(3) q(4: w,x,y,z) v(3) omega(3) omega_m(4) */
+    float* params;            /* [8][ld]  m Jx Jy Jz kf km T_m 0 */
+    float* dist;              /* [6][ld]  f_r(3) tau_r(3) */
+    float* hist;              /* [64][ld] a_{t-1} .. a_{t-16}, newest first */
+    uint32_t* ep_index;       /* [ld] episodes started so far (random counter) */
+    uint32_t* ep_step;        /* [ld] steps into the current episode */
+    float* ep_ret;            /* [ld] return of the current episode */
+    uint32_t* n_done;         /* [ld] completed episodes */
+    uint32_t* len_sum;        /* [ld] sum of completed episode lengths */
+    float* ret_sum;           /* [ld] sum of completed episode returns */
+    float* records;           /* [capacity][record_fields][ld]; flags are uint32 bits:
+                                 bit0 terminated, bit1 truncated, bits 8.. episode step */
+    float* side;              /* [capacity][17][ld] s' where the episode ended */
+    float* reward_c;          /* [8] device: current C_* (7) and exploration std-dev */
+} qsim_info;
+
+/* ---------------------------------------------------------------- library / errors */
+const char* qsim_last_error(void);
+int32_t qsim_abi_version(void);
+/* Plain cudaMemcpyAsync (kind = cudaMemcpyDefault) for bindings without a CUDA runtime. */
+qsim_status qsim_memcpy(void* dst, const void* src, size_t bytes, void* stream);
+qsim_status qsim_stream_sync(void* stream);
+
+/* --------------------------------------------------------------------- random streams
+ * Philox4x32-10 (Salmon et al., SC'11) with key = (seed lo, seed hi) and counter
+ * (c0 = i, c1, tag << 24 | sub, run).  Writes n blocks of 4 uint32 to `out` (device).
+ * kind 0: raw uint32; 1: uniforms ((x >> 9) + 1/2) 2^-23 as float bits;
+ * 2: Box-Muller normals (cosine branch, two per block) as float bits. */
+qsim_status qsim_philox_fill(uint64_t seed, uint32_t run, uint32_t tag, uint32_t sub,
+                             uint32_t c1, int32_t n, int32_t kind, uint32_t* out,
+                             void* stream);
+/* Host-side Philox (same stream) for small draws such as per-run hyper-parameters. */
+void qsim_philox_host(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* ------------------------------------------------------------------------- dynamics
+ * One or more teacher-forced RK4 steps (Sec. IV dynamics; Sec. V 100 Hz) of n
+ * independent bodies with the RPM set-point `rpm` held constant:
+ *   state_in/out [17][ld], params [8][ld] (m Jx Jy Jz kf km T_m -), dist [6][ld] or
+ *   NULL (no disturbance), rpm [4][ld].  All device pointers, 16-byte aligned, ld >= n
+ *   and a multiple of 4.  state_out may alias state_in.  Vehicle geometry comes from
+ *   `veh` (host pointer).  renorm: renormalise q after each step. */
+qsim_status qsim_dynamics_step(const qsim_params* veh, const float* params, const float* dist,
+                               const float* state_in, const float* rpm, float dt,
+                               int32_t renorm, int32_t n, int32_t ld, int32_t n_steps,
+                               float* state_out, void* stream);
+
+/* Dynamics-only throughput kernel in the shape of the paper's simulator benchmark
+ * (Sec. V "Simulation": envs x steps of forward dynamics, no policy): every env holds
+ * its state in registers for n_steps RK4 steps at the hover set-point of `veh`;
+ * final states are written to state_out [17][ld] (device). */
+qsim_status qsim_dynamics_bench(const qsim_params* veh, int32_t n, int32_t ld,
+                                int32_t n_steps, float dt, float* state_out, void* stream);
+
+/* ----------------------------------------------------------------------- env sets
+ * qsim_create allocates n_envs environments (+ a replay ring when replay_capacity > 0)
+ * on the current device and resets every env to episode 0 (state, domain-randomised
+ * parameters, disturbance, empty history).  Synchronous. */
+qsim_status qsim_create(const qsim_config* cfg, const qsim_params* veh, qsim_handle** out);
+qsim_status qsim_destroy(qsim_handle* h);
+qsim_status qsim_info_get(const qsim_handle* h, qsim_info* out);
+/* Overwrite host-side counters (used when teacher-forcing a buffer): t_now, head, size. */
+qsim_status qsim_set_counters(qsim_handle* h, int64_t t_now, int64_t head, int64_t size);
+/* Device status word: QSIM_OK or the first device-side error since the last call. */
+qsim_status qsim_sync(qsim_handle* h);
+
+/* Actor and critic observations of the current states (Sec. IV: o_a = {p, R, v, omega,
+ * H} with noise of the current step; o_c privileged and noise-free).  obs_a
+ * [obs_dim][ld], obs_c [critic_obs_dim][ld] (either may be NULL); device pointers. */
+qsim_status qsim_observe(qsim_handle* h, float* obs_a, float* obs_c, void* stream);
+
+/* One environment step with external normalised actions [4][ld] in [-1,1] (clipped):
+ * RPM set-point, RK4, reward, termination/truncation, transition write into the replay
+ * ring, history update, reset of finished envs.  Outputs (device, any may be NULL):
+ * reward [ld], terminated [ld], truncated [ld] (uint8), and the observations of the
+ * next step as qsim_observe would return them. */
+qsim_status qsim_step(qsim_handle* h, const float* actions, float* obs_a, float* obs_c,
+                      float* reward, uint8_t* terminated, uint8_t* truncated, void* stream);
+
+/* Fused rollout of n_steps steps for every env (the ENV STEP of the hot path): actor
+ * MLP (obs_dim -> hidden -> hidden -> 4, ReLU/ReLU/tanh; parameters `actor` in the
+ * layout W1[h][in] b1 W2[h][h] b2 W3[4][h] b3, device) with Gaussian exploration of
+ * std-dev sigma_e (sigma_e < 0: the handle's current value) or uniform warm-up actions
+ * while t < learning_starts, then RK4 dynamics, reward, termination, reset and the
+ * transition write.  hidden must be 64 for the warp-tiled kernel; other widths run on
+ * the generic tile path. */
+qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t hidden, int32_t n_steps,
+                         float sigma_e, void* stream);
+
+/* Warps per block for the rollout kernel (0 = autotuned choice).  Returns the value in
+ * effect. */
+int32_t qsim_rollout_tune(qsim_handle* h, int32_t warps_per_block);
+
+/* Recompute every stored reward from (s', a) with the current reward constants (Sec. VI
+ * reward recalculation). */
+qsim_status qsim_recalc_rewards(qsim_handle* h, void* stream);
+/* Set the current reward constants (7 floats) and exploration std-dev (host values). */
+qsim_status qsim_set_reward(qsim_handle* h, const float c[7], float sigma_e, void* stream);
+
+/* Reduced episode statistics (host out; synchronises the stream). */
+typedef struct qsim_stats {
+    int64_t episodes;       /* completed episodes */
+    double mean_length;     /* mean completed-episode length, steps */
+    double mean_return;     /* mean completed-episode return */
+} qsim_stats;
+qsim_status qsim_stats_get(qsim_handle* h, qsim_stats* out, void* stream);
+
+/* ---------------------------------------------------------------------- learner
+ * TD3 with an asymmetric critic (Sec. IV; TD3): actor obs_dim -> H -> H -> 4 (tanh),
+ * twin critics (critic_obs_dim + 4) -> H -> H -> 1, target networks, Adam. */
+typedef struct ac_config {
+    int32_t hidden;          /* H in {32, 64, 128} (any multiple of 32 up to 128) */
+    int32_t batch;           /* minibatch B, multiple of 32, <= 1024 */
+    int32_t policy_delay;    /* actor + target update every d-th critic update */
+    int32_t updates_per_step;/* updates per env step in ac_train (update-to-data) */
+    float gamma, tau, lr, beta1, beta2, eps;
+    float sigma_target;      /* target-policy smoothing std-dev */
+    float noise_clip;        /* smoothing noise clip */
+    int32_t cluster;         /* CTAs that cooperate on one update (1..16; 0 = auto) */
+    int32_t reserved0;
+} ac_config;
+
+/* Sizes and device pointers of a learner (all float32, device). */
+typedef struct ac_info {
+    int32_t obs_dim, critic_in, hidden, batch;
+    int32_t n_actor, n_critic;      /* parameter counts */
+    int64_t t_actor, t_critic;      /* Adam steps taken */
+    int64_t updates;                /* updates taken (random counter) */
+    float *actor, *actor_t, *c1, *c1_t, *c2, *c2_t;
+    float *m_a, *v_a, *m_c1, *v_c1, *m_c2, *v_c2;
+    float* stats;                   /* [4] last critic loss, last actor loss, -, - */
+} ac_info;
+
+/* Create a learner sized for env set `env` (observation layouts), initialise the three
+ * online networks with PyTorch-style U(+-1/sqrt(fan_in)) from Philox tag 7 (networks
+ * 0 actor, 1 critic 1, 2 critic 2) and copy them into the targets.  Synchronous. */
+qsim_status ac_create(const ac_config* cfg, const qsim_handle* env, ac_handle** out);
+qsim_status ac_destroy(ac_handle* a);
+qsim_status ac_info_get(const ac_handle* a, ac_info* out);
+qsim_status ac_set_counters(ac_handle* a, int64_t t_actor, int64_t t_critic, int64_t updates);
+
+/* n_updates TD3 updates (the AC UPDATE of the hot path): minibatch sample + gather from
+ * `env`'s replay ring, target actor + smoothing, twin target critics, critic regression,
+ * Adam on the critics, and every policy_delay-th update the actor gradient through
+ * critic 1, Adam on the actor and Polyak averaging of all targets. */
+qsim_status ac_update(ac_handle* a, qsim_handle* env, int32_t n_updates, void* stream);
+
+/* Train n_runs independent runs for steps_per_run env steps each: per step, the fused
+ * env step of each run's envs (actor, exploration, dynamics, reward, reset, transition
+ * write) followed by updates_per_step updates once the buffer allows sampling, plus the
+ * curriculum with reward recalculation when configured.  persistent = 1: one
+ * persistent launch per chunk of steps for all runs, captured in a CUDA graph;
+ * persistent = 0: the same kernel launched per run and per step (the plain form). */
+qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
+                     int64_t steps_per_run, int32_t persistent, void* stream);
+qsim_status ac_sync(ac_handle* a);
+
+/* Checkpoint: weights, targets, Adam moments and counters, the env set's states and
+ * counters and current reward constants (not the replay buffer).  Versioned binary. */
+qsim_status ac_save(const ac_handle* a, const qsim_handle* env, const char* path);
+qsim_status ac_load(ac_handle* a, qsim_handle* env, const char* path);
+
+/* ------------------------------------------------------------------ differentiation
+ * Reverse-mode gradient through an H-step RK4 rollout of n envs without resets:
+ *   loss_e = sum_{t=1..H} [w_p |p_t|^2 + w_q (1 - q_w,t^2) + w_v |v_t|^2]
+ *            + w_a sum_{t=0..H-1} |a_t|^2
+ * mode 0 (open loop): actions [H][4][ld] given; returns d loss_e / d a_t in g_actions.
+ * mode 1 (closed loop): a_t = actor(o_a,t) with o_a built from the state and the
+ * history of the rollout's own actions (zeros before t = 0, no noise); returns
+ * d sum_e loss_e / d actor in g_actor.
+ * Both modes return d loss_e / d (m, Jx, Jy, Jz) in g_params [4][ld] and loss [ld].
+ * States are checkpointed every `ckpt` steps and recomputed inside each segment.
+ * s0 [17][ld], params [8][ld]; workspace: device scratch of qsim_vjp_workspace() bytes. */
+typedef struct qsim_vjp_desc {
+    int32_t n, ld, H, ckpt, mode, n_hist, hidden, reserved0;
+    float w_p, w_q, w_v, w_a;
+    float dt;
+    int32_t renorm;
+} qsim_vjp_desc;
+size_t qsim_vjp_workspace(const qsim_vjp_desc* d);
+qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_params* veh, const float* s0,
+                             const float* params, const float* actions, const float* actor,
+                             float* loss, float* g_actions, float* g_actor, float* g_params,
+                             float* actions_out, void* workspace, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

@@ -1,0 +1,1121 @@
+// qsim_learner.cu -- asymmetric TD3 learner (Sec. IV; TD3 of Fujimoto et al. 2018) and the
+// batched multi-run training kernel.
+//
+// One run is processed by a thread-block cluster of S CTAs.  Each CTA owns B/S samples of
+// the minibatch: it gathers them from the replay ring, rebuilds the actor and privileged
+// critic observations, and runs every forward / backward GEMM of its slice with
+// activations in its own scratch (L2-resident).  Weight gradients are reduced across the
+// cluster in a fixed order (deterministic, no float atomics): each CTA sums one slice of
+// the parameter vector over the S partials and applies Adam (and Polyak) to that slice,
+// with hardware cluster barriers between phases.  A persistent grid of clusters walks a
+// host-computed longest-processing-time-first list of runs; each run advances n_iters
+// iterations of {env step of its envs, updates_per_step updates} before the cluster moves
+// to its next run.  The same kernel launched for one run and one iteration is the plain
+// (one-run-per-launch) form.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <numeric>
+#include <vector>
+
+#include <cooperative_groups.h>
+
+#include "qsim_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace qsim {
+
+constexpr int LT = 256;                 // threads per CTA
+constexpr int GM = 64, GN = 64, GK = 32, GLD = 68;
+constexpr int GEMM_SMEM = 2 * GK * GLD; // floats
+
+struct LearnHyper {
+    float gamma, tau, lr, beta1, beta2, eps, sigma_t, noise_clip;
+    int policy_delay, updates_per_step;
+};
+
+// Everything the training kernel knows about one run.  Counters are updated in place by
+// the kernel so that a captured graph can be replayed.
+struct RunDesc {
+    EnvCfg C;
+    EnvPtrs E;
+    int64_t capacity, head, size, t_now;
+    int64_t next_curr, curr_interval;
+    float cf[7], ct[7];
+    float sig_f, sig_min;
+    int recalc;
+    int n_env;
+    float *actor, *actor_t, *c1, *c1_t, *c2, *c2_t;
+    float *m_a, *v_a, *m_c1, *v_c1, *m_c2, *v_c2;
+    float* stats;
+    int H, B, DA, DC, PA, PC;
+    int64_t t_a, t_c, u;
+    int64_t start_updates;
+    LearnHyper hp;
+    float* scratch_extra;  // unused, keeps the struct 16-byte multiple
+};
+
+// L2-only load (operands may have been written by another SM of the cluster).  The asm is
+// volatile so that it executes only where control flow reaches it: a conditional
+// `cond ? load : 0` must never be turned into an unconditional load.
+__device__ __forceinline__ float ldcg(const float* p) {
+    float r;
+    asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(r) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ldcg(const uint32_t* p) {
+    uint32_t r;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+
+struct Mat {
+    const float* p;
+    int64_t s0, s1;  // element (i, j) = p[i * s0 + j * s1]
+};
+
+__device__ __forceinline__ int psize(int in, int h, int out) { return h * in + h + h * h + h + out * h + out; }
+
+// ------------------------------------------------------------------ CTA-wide SIMT GEMM
+// C(m, n) = sum_k A(m, k) B(k, n) for m < M, n < N; epi(m, n, value) consumes each output.
+// Operands are read with L2-only loads (they may have been written by other SMs of the
+// cluster), staged in shared memory 64 x 32 / 32 x 64 per step, 4 x 4 outputs per thread.
+template <class Epi>
+__device__ void cta_gemm(int M, int N, int K, Mat A, Mat B, float* sm, Epi epi) {
+    float* As = sm;
+    float* Bs = sm + GK * GLD;
+    const int tid = threadIdx.x, tm = tid >> 4, tn = tid & 15;
+    for (int m0 = 0; m0 < M; m0 += GM) {
+        for (int n0 = 0; n0 < N; n0 += GN) {
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+            for (int k0 = 0; k0 < K; k0 += GK) {
+                for (int i = tid; i < GM * GK; i += LT) {
+                    int mm, kk;
+                    if (A.s1 == 1) { kk = i % GK; mm = i / GK; } else { mm = i % GM; kk = i / GM; }
+                    const int m = m0 + mm, k = k0 + kk;
+                    float v = 0.0f;
+                    if (m < M && k < K) v = ldcg(A.p + m * A.s0 + k * A.s1);
+                    As[kk * GLD + mm] = v;
+                }
+                for (int i = tid; i < GK * GN; i += LT) {
+                    int kk, nn;
+                    if (B.s1 == 1) { nn = i % GN; kk = i / GN; } else { kk = i % GK; nn = i / GK; }
+                    const int k = k0 + kk, n = n0 + nn;
+                    float v = 0.0f;
+                    if (k < K && n < N) v = ldcg(B.p + k * B.s0 + n * B.s1);
+                    Bs[kk * GLD + nn] = v;
+                }
+                __syncthreads();
+                const int kc = min(GK, K - k0);
+                for (int kk = 0; kk < kc; ++kk) {
+                    const float4 a = *reinterpret_cast<const float4*>(As + kk * GLD + tm * 4);
+                    const float4 b = *reinterpret_cast<const float4*>(Bs + kk * GLD + tn * 4);
+                    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int m = m0 + tm * 4 + i, n = n0 + tn * 4 + j;
+                    if (m < M && n < N) epi(m, n, acc[i][j]);
+                }
+        }
+    }
+    __syncthreads();
+}
+
+// Forward of in -> H (ReLU) -> H (ReLU) -> out (tanh or linear) for M rows of X [M][ldx].
+__device__ void mlp_fwd(const float* W, int in, int H, int out, const float* X, int ldx, int M,
+                        float* H1, float* H2, float* Y, int ldy, bool tanh_out, float* sm) {
+    const float* W1 = W;
+    const float* b1 = W1 + H * in;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + out * H;
+    cta_gemm(M, H, in, Mat{X, ldx, 1}, Mat{W1, 1, in}, sm,
+             [&](int m, int n, float v) { H1[m * H + n] = fmaxf(v + ldcg(b1 + n), 0.0f); });
+    cta_gemm(M, H, H, Mat{H1, H, 1}, Mat{W2, 1, H}, sm,
+             [&](int m, int n, float v) { H2[m * H + n] = fmaxf(v + ldcg(b2 + n), 0.0f); });
+    cta_gemm(M, out, H, Mat{H2, H, 1}, Mat{W3, 1, H}, sm, [&](int m, int n, float v) {
+        const float z = v + ldcg(b3 + n);
+        Y[m * ldy + n] = tanh_out ? tanhf(z) : z;
+    });
+}
+
+// Reverse through the MLP for M rows.  dZ3 [M][out] holds dLoss/d(pre-activation of the
+// output layer).  Writes the parameter gradient (this CTA's partial) into G (layout of
+// W) and, if dX != nullptr, dLoss/dX [M][in] (only columns [x_lo, in) are needed).
+__device__ void mlp_bwd(const float* W, int in, int H, int out, const float* X, int ldx, int M,
+                        const float* H1, const float* H2, const float* dZ3, float* dZ2,
+                        float* dZ1, float* G, float* dX, int x_lo, float* sm) {
+    const float* W2 = W + H * in + H;
+    const float* W3 = W2 + H * H + H;
+    float* gW1 = G;
+    float* gb1 = gW1 + H * in;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + H * H;
+    float* gW3 = gb2 + H;
+    float* gb3 = gW3 + out * H;
+    // dW3 = dZ3^T H2 ; db3 = colsum dZ3
+    if (G) {
+        cta_gemm(out, H, M, Mat{dZ3, 1, out}, Mat{H2, H, 1}, sm,
+                 [&](int m, int n, float v) { gW3[m * H + n] = v; });
+        for (int n = threadIdx.x; n < out; n += LT) {
+            float s = 0.0f;
+            for (int m = 0; m < M; ++m) s += ldcg(dZ3 + m * out + n);
+            gb3[n] = s;
+        }
+    }
+    // dZ2 = (dZ3 W3) * (H2 > 0)
+    cta_gemm(M, H, out, Mat{dZ3, out, 1}, Mat{W3, H, 1}, sm, [&](int m, int n, float v) {
+        dZ2[m * H + n] = ldcg(H2 + m * H + n) > 0.0f ? v : 0.0f;
+    });
+    if (G) {
+        cta_gemm(H, H, M, Mat{dZ2, 1, H}, Mat{H1, H, 1}, sm,
+                 [&](int m, int n, float v) { gW2[m * H + n] = v; });
+        for (int n = threadIdx.x; n < H; n += LT) {
+            float s = 0.0f;
+            for (int m = 0; m < M; ++m) s += ldcg(dZ2 + m * H + n);
+            gb2[n] = s;
+        }
+    }
+    // dZ1 = (dZ2 W2) * (H1 > 0)
+    cta_gemm(M, H, H, Mat{dZ2, H, 1}, Mat{W2, H, 1}, sm, [&](int m, int n, float v) {
+        dZ1[m * H + n] = ldcg(H1 + m * H + n) > 0.0f ? v : 0.0f;
+    });
+    if (G) {
+        cta_gemm(H, in, M, Mat{dZ1, 1, H}, Mat{X, ldx, 1}, sm,
+                 [&](int m, int n, float v) { gW1[m * in + n] = v; });
+        for (int n = threadIdx.x; n < H; n += LT) {
+            float s = 0.0f;
+            for (int m = 0; m < M; ++m) s += ldcg(dZ1 + m * H + n);
+            gb1[n] = s;
+        }
+    }
+    if (dX) {
+        const float* W1 = W;
+        cta_gemm(M, in - x_lo, H, Mat{dZ1, H, 1}, Mat{W1 + x_lo, in, 1}, sm,
+                 [&](int m, int n, float v) { dX[m * in + x_lo + n] = v; });
+    }
+    __syncthreads();
+}
+
+// -------------------------------------------------------------------- cluster helpers
+__device__ __forceinline__ void cluster_sync_all(int S) {
+    if (S > 1) {
+        __threadfence();
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+}
+
+// Scratch layout of one CTA (floats), for Bc samples.
+struct Scr {
+    float *oa, *oa2, *oc, *oc2, *r, *term, *y, *q1, *q2, *mu, *da, *dz3, *X1, *X2, *H1a, *H2a,
+        *H1b, *H2b, *dZ2, *dZ1, *ga, *g1, *g2, *loss, *env_obs, *env_h1, *env_h2, *env_mu;
+};
+
+__host__ __device__ inline size_t scratch_floats(int Bc, int H, int DA, int DC, int PA, int PC,
+                                                 int n_env) {
+    size_t f = 0;
+    f += 2 * (size_t)Bc * DA + 2 * (size_t)Bc * DC;  // oa oa2 oc oc2
+    f += 5 * (size_t)Bc;                              // r term y q1 q2
+    f += 3 * 4 * (size_t)Bc;                          // mu da dz3
+    f += 8 * (size_t)Bc * H;                          // X1 X2 H1a H2a H1b H2b dZ2 dZ1
+    f += (size_t)PA + 2 * (size_t)PC + 8;             // partial grads + loss
+    f += (size_t)n_env * (DA + 2 * H + 4);            // env-step tile
+    return (f + 31) & ~(size_t)31;
+}
+
+__device__ Scr carve(float* base, int Bc, int H, int DA, int DC, int PA, int PC, int n_env) {
+    Scr s;
+    float* p = base;
+    auto take = [&](size_t n) { float* q = p; p += n; return q; };
+    s.oa = take((size_t)Bc * DA); s.oa2 = take((size_t)Bc * DA);
+    s.oc = take((size_t)Bc * DC); s.oc2 = take((size_t)Bc * DC);
+    s.r = take(Bc); s.term = take(Bc); s.y = take(Bc); s.q1 = take(Bc); s.q2 = take(Bc);
+    s.mu = take(4 * (size_t)Bc); s.da = take(4 * (size_t)Bc); s.dz3 = take(4 * (size_t)Bc);
+    s.X1 = take((size_t)Bc * H); s.X2 = take((size_t)Bc * H);
+    s.H1a = take((size_t)Bc * H); s.H2a = take((size_t)Bc * H);
+    s.H1b = take((size_t)Bc * H); s.H2b = take((size_t)Bc * H);
+    s.dZ2 = take((size_t)Bc * H); s.dZ1 = take((size_t)Bc * H);
+    s.ga = take(PA); s.g1 = take(PC); s.g2 = take(PC); s.loss = take(8);
+    s.env_obs = take((size_t)n_env * DA); s.env_h1 = take((size_t)n_env * H);
+    s.env_h2 = take((size_t)n_env * H); s.env_mu = take((size_t)n_env * 4);
+    return s;
+}
+
+// ------------------------------------------------------------------- env-step helpers
+__device__ __forceinline__ void load_env(const RunDesc& R, int e, float* s, float* d, Prm& P) {
+    const int ld = R.C.ld;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) s[i] = ldcg(R.E.state + i * ld + e);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) d[i] = ldcg(R.E.dist + i * ld + e);
+    const float* pr = R.E.prm;
+    P = make_prm(ldcg(pr + e), ldcg(pr + ld + e), ldcg(pr + 2 * ld + e), ldcg(pr + 3 * ld + e),
+                 ldcg(pr + 4 * ld + e), ldcg(pr + 5 * ld + e), ldcg(pr + 6 * ld + e));
+}
+
+// One env step of all envs of run R (executed by one CTA): observation, actor forward
+// (generic GEMM path), warm-up / exploration, RK4, reward, termination, record write,
+// history update and reset.
+__device__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, int64_t slot, float* sm) {
+    const EnvCfg& C = R.C;
+    const int ld = C.ld, n = R.n_env, DA = R.DA, H = R.H;
+    const bool warm = (int64_t)t < (int64_t)C.learning_starts;
+    if (!warm) {
+        for (int e = threadIdx.x; e < n; e += LT) {
+            float s[NS], o[18];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) s[i] = ldcg(R.E.state + i * ld + e);
+            obs_state(s, o);
+            if (C.any_noise) {
+                float nz[18];
+                obs_noise(C, (uint32_t)e, t, nz);
+#pragma unroll
+                for (int k = 0; k < 18; ++k) o[k] += nz[k];
+            }
+            float* row = S.env_obs + (size_t)e * DA;
+#pragma unroll
+            for (int k = 0; k < 18; ++k) row[k] = o[k];
+            for (int k = 0; k < 4 * C.n_hist; ++k) row[18 + k] = ldcg(R.E.hist + k * ld + e);
+        }
+        __syncthreads();
+        mlp_fwd(R.actor, DA, H, 4, S.env_obs, DA, n, S.env_h1, S.env_h2, S.env_mu, 4, true, sm);
+    }
+    const float sigma = ldcg(R.E.rewardC + 7);
+    float Cr[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Cr[i] = ldcg(R.E.rewardC + i);
+    for (int e = threadIdx.x; e < n; e += LT) {
+        float s[NS], d[6], a[4];
+        Prm P;
+        load_env(R, e, s, d, P);
+        if (warm) {
+            const uint4 r = draw(C, (uint32_t)e, t, TAG_WARM, 0);
+            a[0] = 2.0f * u01(r.x) - 1.0f; a[1] = 2.0f * u01(r.y) - 1.0f;
+            a[2] = 2.0f * u01(r.z) - 1.0f; a[3] = 2.0f * u01(r.w) - 1.0f;
+        } else {
+            float mu[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mu[j] = ldcg(S.env_mu + e * 4 + j);
+            if (sigma > 0.0f) {
+                const uint4 r0 = draw(C, (uint32_t)e, t, TAG_EXPL, 0);
+                const uint4 r1 = draw(C, (uint32_t)e, t, TAG_EXPL, 1);
+                a[0] = clampf(fmaf(sigma, gauss(r0.x, r0.y), mu[0]), -1.0f, 1.0f);
+                a[1] = clampf(fmaf(sigma, gauss(r0.z, r0.w), mu[1]), -1.0f, 1.0f);
+                a[2] = clampf(fmaf(sigma, gauss(r1.x, r1.y), mu[2]), -1.0f, 1.0f);
+                a[3] = clampf(fmaf(sigma, gauss(r1.z, r1.w), mu[3]), -1.0f, 1.0f);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a[j] = clampf(mu[j], -1.0f, 1.0f);
+            }
+        }
+        float u[4], s2[NS];
+        action_to_rpm(C.veh, a, u);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) s2[i] = s[i];
+        rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
+        const float r = reward(Cr, s2, a);
+        const bool term = terminated(C, s2);
+        const uint32_t ep_step = ldcg(R.E.ep_step + e);
+        const uint32_t ep_after = ep_step + 1;
+        const bool trunc = !term && (int)ep_after >= C.episode_len;
+        if (R.capacity > 0) {
+            float* rec = R.E.rec + (size_t)slot * C.F * ld + e;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) rec[i * ld] = s[i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) rec[(17 + i) * ld] = a[i];
+            rec[21 * ld] = r;
+            rec[22 * ld] = __uint_as_float(pack_flags(term, trunc, ep_step));
+            if (C.n_priv) {
+                float pv[NPRIV];
+                priv_vals(C, P, d, pv);
+#pragma unroll
+                for (int k = 0; k < NPRIV; ++k) rec[(23 + k) * ld] = pv[k];
+            }
+            if (term || trunc) {
+                float* sd = R.E.side + (size_t)slot * NS * ld + e;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) sd[i * ld] = s2[i];
+            }
+        }
+        for (int i = C.n_hist - 1; i >= 1; --i)
+            for (int c = 0; c < 4; ++c)
+                R.E.hist[(4 * i + c) * ld + e] = ldcg(R.E.hist + (4 * (i - 1) + c) * ld + e);
+        if (C.n_hist > 0)
+            for (int c = 0; c < 4; ++c) R.E.hist[c * ld + e] = a[c];
+        float ret = ldcg(R.E.ep_ret + e) + r;
+        uint32_t eps = ep_after;
+        if (term || trunc) {
+            R.E.n_done[e] = ldcg(R.E.n_done + e) + 1;
+            R.E.len_sum[e] = ldcg(R.E.len_sum + e) + ep_after;
+            R.E.ret_sum[e] = ldcg(R.E.ret_sum + e) + ret;
+            const uint32_t epi = ldcg(R.E.ep_index + e) + 1;
+            R.E.ep_index[e] = epi;
+            float prm7[7];
+            reset_env(C, (uint32_t)e, epi, s2, prm7, d);
+            for (int i = 0; i < 7; ++i) R.E.prm[i * ld + e] = prm7[i];
+            for (int i = 0; i < 6; ++i) R.E.dist[i * ld + e] = d[i];
+            for (int i = 0; i < 4 * HMAX; ++i) R.E.hist[i * ld + e] = 0.0f;
+            ret = 0.0f;
+            eps = 0;
+        }
+        R.E.ep_ret[e] = ret;
+        R.E.ep_step[e] = eps;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) R.E.state[i * ld + e] = s2[i];
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------------- TD3 update
+__device__ __forceinline__ int64_t pmod64(int64_t a, int64_t m) {
+    const int64_t r = a % m;
+    return r < 0 ? r + m : r;
+}
+
+// Gather one sample: rebuilds o_a, o_a', o_c (with stored action), o_c' (action slot
+// filled later), r and the termination flag from the compact replay records.
+__device__ void gather_sample(const RunDesc& R, int j, uint32_t u, int64_t head, int64_t size,
+                              int64_t t_now, const Scr& S, int jl) {
+    const EnvCfg& C = R.C;
+    const int ld = C.ld, F = C.F, NE = R.n_env, DA = R.DA, DC = R.DC;
+    const int64_t CAP = R.capacity;
+    const int64_t lost = size == CAP ? C.n_hist : 0;
+    const uint32_t nvalid = (uint32_t)((size - 1 - lost) * NE);
+    const uint4 rr = draw(C, (uint32_t)j >> 2, u, TAG_REPLAY, 0);
+    const uint32_t x = (j & 3) == 0 ? rr.x : ((j & 3) == 1 ? rr.y : ((j & 3) == 2 ? rr.z : rr.w));
+    const uint32_t idx = (uint32_t)(((uint64_t)x * (uint64_t)nvalid) >> 32);
+    const int64_t k = idx / (uint32_t)NE;
+    const int env = (int)(idx % (uint32_t)NE);
+    const int64_t slot = pmod64(head - size + lost + k, CAP);
+    const uint32_t t_rec = (uint32_t)(t_now - size + lost + k);
+    const float* rec = R.E.rec + (size_t)slot * F * ld + env;
+    const uint32_t fl = __float_as_uint(ldcg(rec + 22 * ld));
+    const bool done = (fl & 3u) != 0;
+    const uint32_t ep = fl >> 8;
+    float s[NS], s2[NS], a[4], pv[NPRIV];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) s[i] = ldcg(rec + i * ld);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = ldcg(rec + (17 + i) * ld);
+#pragma unroll
+    for (int k2 = 0; k2 < NPRIV; ++k2) pv[k2] = 0.0f;
+    if (C.n_priv) {
+#pragma unroll
+        for (int k2 = 0; k2 < NPRIV; ++k2) pv[k2] = ldcg(rec + (23 + k2) * ld);
+    }
+    const float* src2 = done ? R.E.side + (size_t)slot * NS * ld + env
+                             : R.E.rec + (size_t)pmod64(slot + 1, CAP) * F * ld + env;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) s2[i] = ldcg(src2 + i * ld);
+    float* oa = S.oa + (size_t)jl * DA;
+    float* oa2 = S.oa2 + (size_t)jl * DA;
+    float* oc = S.oc + (size_t)jl * DC;
+    float* oc2 = S.oc2 + (size_t)jl * DC;
+    float o[18], o2[18];
+    obs_state(s, o);
+    obs_state(s2, o2);
+    // critic observations (noise-free)
+    if (C.critic_layout == 2) {
+#pragma unroll
+        for (int q = 0; q < 18; ++q) { oc[q] = o[q]; oc2[q] = o2[q]; }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { oc[18 + i] = rpm_norm(C.veh, s[13 + i]); oc2[18 + i] = rpm_norm(C.veh, s2[13 + i]); }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) { oc[22 + q] = pv[q]; oc2[22 + q] = pv[q]; }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 18; ++q) { oc[q] = o[q]; oc2[q] = o2[q]; }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { oc[DA + i] = rpm_norm(C.veh, s[13 + i]); oc2[DA + i] = rpm_norm(C.veh, s2[13 + i]); }
+        if (C.critic_layout == 1)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) { oc[DA + 4 + q] = pv[q]; oc2[DA + 4 + q] = pv[q]; }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) oc[DC - 4 + i] = a[i];
+    // history: o_a has a_{t-1..t-NH}; o_a' has a_t, a_{t-1..t-NH+1}; zeros before the
+    // episode start
+    for (int i = 1; i <= C.n_hist; ++i) {
+        float h[4] = {0, 0, 0, 0}, h2[4] = {0, 0, 0, 0};
+        if ((uint32_t)i <= ep) {
+            const float* ap = R.E.rec + (size_t)pmod64(slot - i, CAP) * F * ld + env + 17 * ld;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) h[c] = ldcg(ap + c * ld);
+        }
+        if (i == 1) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) h2[c] = a[c];
+        } else if ((uint32_t)(i - 1) <= ep) {
+            const float* ap = R.E.rec + (size_t)pmod64(slot - (i - 1), CAP) * F * ld + env + 17 * ld;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) h2[c] = ldcg(ap + c * ld);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            oa[18 + 4 * (i - 1) + c] = h[c];
+            oa2[18 + 4 * (i - 1) + c] = h2[c];
+            if (C.critic_layout != 2) {
+                oc[18 + 4 * (i - 1) + c] = h[c];
+                oc2[18 + 4 * (i - 1) + c] = h2[c];
+            }
+        }
+    }
+    if (C.any_noise) {
+        float n1[18], n2[18];
+        obs_noise(C, (uint32_t)env, t_rec, n1);
+        obs_noise(C, (uint32_t)env, t_rec + 1, n2);
+#pragma unroll
+        for (int q = 0; q < 18; ++q) { o[q] += n1[q]; o2[q] += n2[q]; }
+    }
+#pragma unroll
+    for (int q = 0; q < 18; ++q) { oa[q] = o[q]; oa2[q] = o2[q]; }
+    S.r[jl] = ldcg(rec + 21 * ld);
+    S.term[jl] = (fl & 1u) ? 1.0f : 0.0f;
+}
+
+__device__ void adam_slice(float* th, const float* gpart_base, size_t part_stride, int S,
+                           int goff, float* m, float* v, int lo, int hi, int64_t t,
+                           const LearnHyper& hp, float gscale) {
+    const float bc1 = 1.0f - powf(hp.beta1, (float)t);
+    const float bc2 = 1.0f - powf(hp.beta2, (float)t);
+    for (int i = lo + threadIdx.x; i < hi; i += LT) {
+        float g = 0.0f;
+        for (int s = 0; s < S; ++s) g += ldcg(gpart_base + (size_t)s * part_stride + goff + i);
+        g *= gscale;
+        const float mi = fmaf(hp.beta1, m[i], (1.0f - hp.beta1) * g);
+        const float vi = fmaf(hp.beta2, v[i], (1.0f - hp.beta2) * g * g);
+        m[i] = mi;
+        v[i] = vi;
+        th[i] -= hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + hp.eps);
+    }
+}
+
+__device__ void polyak_slice(float* tg, const float* src, int lo, int hi, float tau) {
+    for (int i = lo + threadIdx.x; i < hi; i += LT) tg[i] = fmaf(tau, ldcg(src + i), (1.0f - tau) * tg[i]);
+}
+
+// Block-wide sum of v over threads (fixed order).
+__device__ float block_sum(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    float s = 0.0f;
+    for (int i = 0; i < LT / 32; ++i) s += red[i];
+    __syncthreads();
+    return s;
+}
+
+// One TD3 update of run R by the cluster (rank `rk` of S).
+__device__ void td3_update(RunDesc& R, int64_t head, int64_t size, int64_t t_now, uint32_t u,
+                           int64_t& t_a, int64_t& t_c, const Scr& S, float* scr_base,
+                           size_t scr_stride, int cl_base, int rk, int nS, float* sm) {
+    const int B = R.B, Bc = B / nS, H = R.H, DA = R.DA, DC = R.DC, PA = R.PA, PC = R.PC;
+    const LearnHyper& hp = R.hp;
+    const int j0 = rk * Bc;
+    // a9: gather
+    for (int jl = threadIdx.x; jl < Bc; jl += LT) gather_sample(R, j0 + jl, u, head, size, t_now, S, jl);
+    __syncthreads();
+    // a10: target actor + smoothing
+    mlp_fwd(R.actor_t, DA, H, 4, S.oa2, DA, Bc, S.X1, S.X2, S.mu, 4, true, sm);
+    for (int jl = threadIdx.x; jl < Bc; jl += LT) {
+        const uint32_t j = (uint32_t)(j0 + jl);
+        const uint4 r0 = draw(R.C, j, u, TAG_SMOOTH, 0), r1 = draw(R.C, j, u, TAG_SMOOTH, 1);
+        const float z[4] = {gauss(r0.x, r0.y), gauss(r0.z, r0.w), gauss(r1.x, r1.y), gauss(r1.z, r1.w)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float eps = clampf(hp.sigma_t * z[i], -hp.noise_clip, hp.noise_clip);
+            S.oc2[(size_t)jl * DC + DC - 4 + i] = clampf(S.mu[jl * 4 + i] + eps, -1.0f, 1.0f);
+        }
+    }
+    __syncthreads();
+    // a11: twin target critics, clipped double-Q target
+    mlp_fwd(R.c1_t, DC, H, 1, S.oc2, DC, Bc, S.X1, S.X2, S.q1, 1, false, sm);
+    mlp_fwd(R.c2_t, DC, H, 1, S.oc2, DC, Bc, S.X1, S.X2, S.q2, 1, false, sm);
+    for (int jl = threadIdx.x; jl < Bc; jl += LT) {
+        const float qmin = fminf(S.q1[jl], S.q2[jl]);
+        S.y[jl] = S.r[jl] + (S.term[jl] != 0.0f ? 0.0f : hp.gamma * qmin);
+    }
+    __syncthreads();
+    // a12: critic regression, forward + backward on this CTA's samples
+    mlp_fwd(R.c1, DC, H, 1, S.oc, DC, Bc, S.H1a, S.H2a, S.q1, 1, false, sm);
+    mlp_fwd(R.c2, DC, H, 1, S.oc, DC, Bc, S.H1b, S.H2b, S.q2, 1, false, sm);
+    float lsum = 0.0f;
+    for (int jl = threadIdx.x; jl < Bc; jl += LT) {
+        const float e1 = S.q1[jl] - S.y[jl], e2 = S.q2[jl] - S.y[jl];
+        S.dz3[jl] = 2.0f * e1 / (float)B;
+        S.da[jl] = 2.0f * e2 / (float)B;
+        lsum += (e1 * e1 + e2 * e2) / (float)B;
+    }
+    lsum = block_sum(lsum, sm);
+    if (threadIdx.x == 0) S.loss[0] = lsum;
+    __syncthreads();
+    mlp_bwd(R.c1, DC, H, 1, S.oc, DC, Bc, S.H1a, S.H2a, S.dz3, S.dZ2, S.dZ1, S.g1, nullptr, 0, sm);
+    mlp_bwd(R.c2, DC, H, 1, S.oc, DC, Bc, S.H1b, S.H2b, S.da, S.dZ2, S.dZ1, S.g2, nullptr, 0, sm);
+    cluster_sync_all(nS);
+    // a14 (critics): reduce the partials over the cluster and apply Adam to this slice
+    t_c += 1;
+    {
+        const size_t g1off = (size_t)(S.g1 - scr_base), g2off = (size_t)(S.g2 - scr_base);
+        const float* cl0 = scr_base - (size_t)rk * scr_stride;  // scratch of cluster rank 0
+        const int lo = (int)((int64_t)PC * rk / nS), hi = (int)((int64_t)PC * (rk + 1) / nS);
+        adam_slice(R.c1, cl0, scr_stride, nS, (int)g1off, R.m_c1, R.v_c1, lo, hi, t_c, hp, 1.0f);
+        adam_slice(R.c2, cl0, scr_stride, nS, (int)g2off, R.m_c2, R.v_c2, lo, hi, t_c, hp, 1.0f);
+        if (rk == 0 && threadIdx.x == 0) {
+            float l = 0.0f;
+            for (int s = 0; s < nS; ++s) l += ldcg(cl0 + (size_t)s * scr_stride + (S.loss - scr_base));
+            R.stats[0] = l;
+        }
+    }
+    cluster_sync_all(nS);
+    // a13: delayed actor update through the updated first critic
+    if ((int64_t)(u % (uint32_t)hp.policy_delay) != (int64_t)(hp.policy_delay - 1)) return;
+    mlp_fwd(R.actor, DA, H, 4, S.oa, DA, Bc, S.X1, S.X2, S.mu, 4, true, sm);
+    for (int i = threadIdx.x; i < Bc * 4; i += LT) {
+        const int jl = i >> 2, c = i & 3;
+        S.oc[(size_t)jl * DC + DC - 4 + c] = S.mu[i];
+    }
+    __syncthreads();
+    mlp_fwd(R.c1, DC, H, 1, S.oc, DC, Bc, S.H1a, S.H2a, S.q1, 1, false, sm);
+    float qs = 0.0f;
+    for (int jl = threadIdx.x; jl < Bc; jl += LT) {
+        S.dz3[jl] = -1.0f / (float)B;
+        qs += -S.q1[jl] / (float)B;
+    }
+    qs = block_sum(qs, sm);
+    if (threadIdx.x == 0) S.loss[1] = qs;
+    __syncthreads();
+    // dQ1/d(input) restricted to the action columns [DC-4, DC) -> dX stored in oc2 rows
+    mlp_bwd(R.c1, DC, H, 1, S.oc, DC, Bc, S.H1a, S.H2a, S.dz3, S.dZ2, S.dZ1, nullptr, S.oc2, DC - 4, sm);
+    for (int i = threadIdx.x; i < Bc * 4; i += LT) {
+        const int jl = i >> 2, c = i & 3;
+        const float m = S.mu[i];
+        S.da[i] = S.oc2[(size_t)jl * DC + DC - 4 + c] * (1.0f - m * m);
+    }
+    __syncthreads();
+    mlp_bwd(R.actor, DA, H, 4, S.oa, DA, Bc, S.X1, S.X2, S.da, S.dZ2, S.dZ1, S.ga, nullptr, 0, sm);
+    cluster_sync_all(nS);
+    t_a += 1;
+    {
+        const size_t gaoff = (size_t)(S.ga - scr_base);
+        const float* cl0 = scr_base - (size_t)rk * scr_stride;
+        const int lo = (int)((int64_t)PA * rk / nS), hi = (int)((int64_t)PA * (rk + 1) / nS);
+        adam_slice(R.actor, cl0, scr_stride, nS, (int)gaoff, R.m_a, R.v_a, lo, hi, t_a, hp, 1.0f);
+        if (rk == 0 && threadIdx.x == 0) {
+            float l = 0.0f;
+            for (int s = 0; s < nS; ++s) l += ldcg(cl0 + (size_t)s * scr_stride + (S.loss - scr_base) + 1);
+            R.stats[1] = l;
+        }
+        __syncthreads();
+        polyak_slice(R.actor_t, R.actor, lo, hi, hp.tau);
+        const int clo = (int)((int64_t)PC * rk / nS), chi = (int)((int64_t)PC * (rk + 1) / nS);
+        polyak_slice(R.c1_t, R.c1, clo, chi, hp.tau);
+        polyak_slice(R.c2_t, R.c2, clo, chi, hp.tau);
+    }
+    cluster_sync_all(nS);
+}
+
+// Curriculum change + reward recalculation over the run's buffer, split over the cluster.
+__device__ void curriculum_step(RunDesc& R, int64_t head, int64_t size, int rk, int nS) {
+    if (rk == 0 && threadIdx.x == 0) {
+        for (int i = 0; i < 7; ++i) {
+            const float c = R.E.rewardC[i], x = c * R.cf[i];
+            R.E.rewardC[i] = R.cf[i] >= 1.0f ? fminf(x, R.ct[i]) : fmaxf(x, R.ct[i]);
+        }
+        R.E.rewardC[7] = fmaxf(R.E.rewardC[7] * R.sig_f, R.sig_min);
+    }
+    cluster_sync_all(nS);
+    if (!R.recalc || R.capacity == 0) return;
+    const EnvCfg& C = R.C;
+    const int ld = C.ld, F = C.F;
+    float Cr[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Cr[i] = ldcg(R.E.rewardC + i);
+    const int64_t total = size * (int64_t)R.n_env;
+    for (int64_t idx = (int64_t)rk * LT + threadIdx.x; idx < total; idx += (int64_t)nS * LT) {
+        const int64_t k = idx / R.n_env;
+        const int e = (int)(idx - k * R.n_env);
+        const int64_t slot = pmod64(head - size + k, R.capacity);
+        float* rec = R.E.rec + (size_t)slot * F * ld + e;
+        const uint32_t fl = __float_as_uint(ldcg(rec + 22 * ld));
+        const float* src;
+        if (fl & 3u) src = R.E.side + (size_t)slot * NS * ld + e;
+        else if (k == size - 1) src = R.E.state + e;
+        else src = R.E.rec + (size_t)pmod64(slot + 1, R.capacity) * F * ld + e;
+        float s2[NS], a[4];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) s2[i] = ldcg(src + i * ld);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = ldcg(rec + (17 + i) * ld);
+        rec[21 * ld] = reward(Cr, s2, a);
+    }
+    cluster_sync_all(nS);
+}
+
+// Persistent training kernel.  Cluster c walks runs order[off[c] .. off[c+1]).
+__global__ void __launch_bounds__(LT) k_train(RunDesc* runs, const int* order, const int* off,
+                                              int n_iters, int do_env, float* scratch,
+                                              size_t scr_stride, int nS) {
+    extern __shared__ __align__(16) float sm[];
+    const int rk = nS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    const int cl = blockIdx.x / nS;
+    float* my = scratch + (size_t)blockIdx.x * scr_stride;
+    for (int oi = off[cl]; oi < off[cl + 1]; ++oi) {
+        RunDesc& R = runs[order[oi]];
+        int64_t head = R.head, size = R.size, t_now = R.t_now, t_a = R.t_a, t_c = R.t_c, u = R.u;
+        int64_t next_curr = R.next_curr;
+        const int Bc = R.B / nS;
+        const Scr S = carve(my, Bc, R.H, R.DA, R.DC, R.PA, R.PC, R.n_env);
+        for (int it = 0; it < n_iters; ++it) {
+            int n_upd = 1;
+            if (do_env) {
+                if (rk == 0) env_step_cta(R, S, (uint32_t)t_now, head, sm);
+                t_now += 1;
+                if (R.capacity > 0) {
+                    head = head + 1 == R.capacity ? 0 : head + 1;
+                    if (size < R.capacity) size += 1;
+                }
+                cluster_sync_all(nS);
+                if (R.curr_interval > 0 && t_now * (int64_t)R.n_env >= next_curr) {
+                    curriculum_step(R, head, size, rk, nS);
+                    next_curr += R.curr_interval;
+                }
+                n_upd = t_now >= R.start_updates ? R.hp.updates_per_step : 0;
+            }
+            for (int k = 0; k < n_upd; ++k) {
+                td3_update(R, head, size, t_now, (uint32_t)u, t_a, t_c, S, my, scr_stride,
+                           blockIdx.x - rk, rk, nS, sm);
+                u += 1;
+            }
+        }
+        cluster_sync_all(nS);
+        if (rk == 0 && threadIdx.x == 0) {
+            R.head = head; R.size = size; R.t_now = t_now; R.t_a = t_a; R.t_c = t_c; R.u = u;
+            R.next_curr = next_curr;
+        }
+        cluster_sync_all(nS);
+    }
+}
+
+// ------------------------------------------------------------------- initialisation
+__global__ void k_init_params(float* P, int in, int h, int out, uint32_t net_id, uint32_t k0,
+                              uint32_t k1, uint32_t run) {
+    const int total = psize(in, h, out);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int sizes[6] = {h * in, h, h * h, h, out * h, out};
+    const int fan[6] = {in, in, h, h, h, h};
+    int blk = 0, acc = 0;
+    while (blk < 5 && i >= acc + sizes[blk]) { acc += sizes[blk]; ++blk; }
+    const float bound = 1.0f / sqrtf((float)fan[blk]);
+    const uint4 r = philox((uint32_t)i >> 2, net_id, (TAG_INIT << 24), run, k0, k1);
+    const uint32_t x = (i & 3) == 0 ? r.x : ((i & 3) == 1 ? r.y : ((i & 3) == 2 ? r.z : r.w));
+    P[i] = bound * (2.0f * u01(x) - 1.0f);
+}
+
+static int grid_for(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+static size_t learner_smem() { return sizeof(float) * (size_t)GEMM_SMEM; }
+
+}  // namespace qsim
+
+using namespace qsim;
+
+// ---------------------------------------------------------------------------- ABI
+static qsim_status fill_desc(ac_handle* a, qsim_handle* e, RunDesc& R) {
+    memset(&R, 0, sizeof(R));
+    R.C = e->dc;
+    R.E = e->p;
+    R.capacity = e->capacity; R.head = e->head; R.size = e->size; R.t_now = e->t_now;
+    R.curr_interval = e->cfg.curriculum_interval;
+    R.next_curr = e->next_curriculum;
+    for (int i = 0; i < 7; ++i) { R.cf[i] = e->cfg.curriculum_factor[i]; R.ct[i] = e->cfg.curriculum_target[i]; }
+    R.sig_f = e->cfg.sigma_factor; R.sig_min = e->cfg.sigma_min; R.recalc = e->cfg.recalc_rewards;
+    R.n_env = e->n;
+    R.actor = a->actor; R.actor_t = a->actor_t; R.c1 = a->c1; R.c1_t = a->c1_t; R.c2 = a->c2; R.c2_t = a->c2_t;
+    R.m_a = a->m_a; R.v_a = a->v_a; R.m_c1 = a->m_c1; R.v_c1 = a->v_c1; R.m_c2 = a->m_c2; R.v_c2 = a->v_c2;
+    R.stats = a->stats;
+    R.H = a->hidden; R.B = a->batch; R.DA = a->obs_dim; R.DC = a->critic_in;
+    R.PA = a->n_actor; R.PC = a->n_critic;
+    R.t_a = a->t_actor; R.t_c = a->t_critic; R.u = a->updates;
+    const int64_t lost = e->cfg.n_hist;
+    R.start_updates = std::max<int64_t>((int64_t)e->cfg.learning_starts, 2 + lost);
+    const ac_config& c = a->cfg;
+    R.hp = LearnHyper{c.gamma, c.tau, c.lr, c.beta1, c.beta2, c.eps, c.sigma_target, c.noise_clip,
+                      c.policy_delay, c.updates_per_step};
+    return QSIM_OK;
+}
+
+static void read_back(ac_handle* a, qsim_handle* e, const RunDesc& R) {
+    e->head = R.head; e->size = R.size; e->t_now = R.t_now; e->next_curriculum = R.next_curr;
+    a->t_actor = R.t_a; a->t_critic = R.t_c; a->updates = R.u;
+}
+
+static int pick_cluster(const ac_handle* a, int n_runs) {
+    if (a->cfg.cluster > 0) return a->cfg.cluster;
+    if (n_runs >= 64) return 1;
+    const int b = a->batch;
+    int s = n_runs > 8 ? 2 : 8;
+    while (s > 1 && (b % s || b / s < 16)) s >>= 1;
+    return s;
+}
+
+struct TrainPlan {
+    RunDesc* d_runs = nullptr;
+    int* d_order = nullptr;
+    int* d_off = nullptr;
+    float* scratch = nullptr;
+    size_t stride = 0;
+    int n_clusters = 0, nS = 1, grid = 0;
+};
+
+static qsim_status validate_pair(const ac_handle* a, const qsim_handle* e) {
+    if (!a || !e) return fail(QSIM_EINVAL, "null handle");
+    if (e->capacity < 2) return fail(QSIM_ESTATE, "env set has no replay buffer");
+    if (e->capacity < e->cfg.n_hist + 2)
+        return fail(QSIM_EINVAL, "replay capacity %lld must exceed the history length + 1",
+                    (long long)e->capacity);
+    if (a->obs_dim != e->dc.obs_dim || a->critic_in != e->dc.cobs_dim + 4)
+        return fail(QSIM_EINVAL, "learner and env set have different observation layouts");
+    return QSIM_OK;
+}
+
+static qsim_status launch_train(std::vector<ac_handle*>& A, std::vector<qsim_handle*>& E,
+                                int n_iters, int do_env, int nS, cudaStream_t st,
+                                std::vector<int>* order_in, int n_clusters_in) {
+    const int n = (int)A.size();
+    std::vector<RunDesc> D(n);
+    size_t stride = 0;
+    for (int i = 0; i < n; ++i) {
+        fill_desc(A[i], E[i], D[i]);
+        if (A[i]->batch % nS) return fail(QSIM_EINVAL, "batch %d not divisible by cluster %d", A[i]->batch, nS);
+        stride = std::max(stride, scratch_floats(A[i]->batch / nS, A[i]->hidden, A[i]->obs_dim,
+                                                 A[i]->critic_in, A[i]->n_actor, A[i]->n_critic, E[i]->n));
+    }
+    // longest-processing-time-first assignment of runs to clusters
+    const int n_clusters = std::max(1, std::min(n, n_clusters_in));
+    std::vector<int> order(n), off(n_clusters + 1, 0);
+    {
+        std::vector<double> cost(n);
+        for (int i = 0; i < n; ++i) {
+            const double h = A[i]->hidden;
+            cost[i] = (double)A[i]->batch * (h * (A[i]->obs_dim + A[i]->critic_in) + 3 * h * h) + 1.0;
+        }
+        std::vector<int> idx(n);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        std::vector<double> load(n_clusters, 0.0);
+        std::vector<std::vector<int>> lists(n_clusters);
+        for (int i : idx) {
+            int best = 0;
+            for (int c = 1; c < n_clusters; ++c)
+                if (load[c] < load[best]) best = c;
+            load[best] += cost[i];
+            lists[best].push_back(i);
+        }
+        int k = 0;
+        for (int c = 0; c < n_clusters; ++c) {
+            off[c] = k;
+            for (int i : lists[c]) order[k++] = i;
+        }
+        off[n_clusters] = k;
+    }
+    if (order_in) *order_in = order;
+    // device copies (stream-ordered; freed after the launch completes)
+    RunDesc* d_runs;
+    int *d_order, *d_off;
+    float* scratch;
+    const size_t scr_bytes = sizeof(float) * stride * (size_t)n_clusters * nS;
+    QCHECK_CUDA(cudaMallocAsync((void**)&d_runs, sizeof(RunDesc) * n, st));
+    QCHECK_CUDA(cudaMallocAsync((void**)&d_order, sizeof(int) * n, st));
+    QCHECK_CUDA(cudaMallocAsync((void**)&d_off, sizeof(int) * (n_clusters + 1), st));
+    QCHECK_CUDA(cudaMallocAsync((void**)&scratch, scr_bytes, st));
+    QCHECK_CUDA(cudaMemcpyAsync(d_runs, D.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, st));
+    QCHECK_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    QCHECK_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (n_clusters + 1), cudaMemcpyHostToDevice, st));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(n_clusters * nS);
+    lc.blockDim = dim3(LT);
+    lc.dynamicSmemBytes = learner_smem();
+    lc.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (nS > 8) QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    QCHECK_CUDA(cudaLaunchKernelEx(&lc, k_train, d_runs, (const int*)d_order, (const int*)d_off,
+                                   n_iters, do_env, scratch, stride, nS));
+    // fetch the advanced counters
+    QCHECK_CUDA(cudaMemcpyAsync(D.data(), d_runs, sizeof(RunDesc) * n, cudaMemcpyDeviceToHost, st));
+    QCHECK_CUDA(cudaFreeAsync(scratch, st));
+    QCHECK_CUDA(cudaFreeAsync(d_off, st));
+    QCHECK_CUDA(cudaFreeAsync(d_order, st));
+    QCHECK_CUDA(cudaFreeAsync(d_runs, st));
+    QCHECK_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) read_back(A[i], E[i], D[i]);
+    return QSIM_OK;
+}
+
+extern "C" qsim_status ac_create(const ac_config* cfg, const qsim_handle* env, ac_handle** out) {
+    if (!cfg || !env || !out) return fail(QSIM_EINVAL, "ac_create: null pointer");
+    *out = nullptr;
+    if (cfg->hidden < 4 || cfg->hidden > 128 || (cfg->hidden % 4))
+        return fail(QSIM_EINVAL, "ac_create: hidden=%d must be a multiple of 4 in [4,128]", cfg->hidden);
+    if (cfg->batch < 1 || cfg->batch > 1024) return fail(QSIM_EINVAL, "ac_create: batch out of range");
+    if (cfg->policy_delay < 1) return fail(QSIM_EINVAL, "ac_create: policy_delay < 1");
+    if (cfg->cluster < 0 || cfg->cluster > 16 || (cfg->cluster & (cfg->cluster - 1)))
+        return fail(QSIM_EINVAL, "ac_create: cluster must be 0 or a power of two <= 16");
+    ac_handle* a = new ac_handle();
+    a->cfg = *cfg;
+    if (a->cfg.updates_per_step < 1) a->cfg.updates_per_step = 1;
+    cudaGetDevice(&a->device);
+    a->obs_dim = env->dc.obs_dim;
+    a->critic_in = env->dc.cobs_dim + 4;
+    a->hidden = cfg->hidden;
+    a->batch = cfg->batch;
+    a->n_actor = a->hidden * a->obs_dim + a->hidden + a->hidden * a->hidden + a->hidden + 4 * a->hidden + 4;
+    a->n_critic = a->hidden * a->critic_in + a->hidden + a->hidden * a->hidden + a->hidden + a->hidden + 1;
+    a->t_actor = a->t_critic = a->updates = 0;
+    const size_t PA = a->n_actor, PC = a->n_critic;
+    const size_t total = 4 * PA + 8 * PC + 8;
+    if (cudaMalloc((void**)&a->base, total * 4) != cudaSuccess ||
+        cudaMalloc((void**)&a->status, 4) != cudaSuccess) {
+        cudaGetLastError();
+        ac_destroy(a);
+        return fail(QSIM_ENOMEM, "ac_create: allocation failed");
+    }
+    cudaMemset(a->base, 0, total * 4);
+    cudaMemset(a->status, 0, 4);
+    float* p = a->base;
+    a->actor = p; p += PA; a->actor_t = p; p += PA;
+    a->c1 = p; p += PC; a->c1_t = p; p += PC; a->c2 = p; p += PC; a->c2_t = p; p += PC;
+    a->m_a = p; p += PA; a->v_a = p; p += PA;
+    a->m_c1 = p; p += PC; a->v_c1 = p; p += PC; a->m_c2 = p; p += PC; a->v_c2 = p; p += PC;
+    a->stats = p;
+    const uint32_t k0 = env->dc.key0, k1 = env->dc.key1, run = env->dc.run_id;
+    k_init_params<<<grid_for(PA, 256), 256>>>(a->actor, a->obs_dim, a->hidden, 4, 0, k0, k1, run);
+    k_init_params<<<grid_for(PC, 256), 256>>>(a->c1, a->critic_in, a->hidden, 1, 1, k0, k1, run);
+    k_init_params<<<grid_for(PC, 256), 256>>>(a->c2, a->critic_in, a->hidden, 1, 2, k0, k1, run);
+    cudaMemcpy(a->actor_t, a->actor, PA * 4, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(a->c1_t, a->c1, PC * 4, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(a->c2_t, a->c2, PC * 4, cudaMemcpyDeviceToDevice);
+    cudaError_t err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) {
+        ac_destroy(a);
+        return cuda_fail(err, "ac_create: init");
+    }
+    *out = a;
+    return QSIM_OK;
+}
+
+extern "C" qsim_status ac_destroy(ac_handle* a) {
+    if (!a) return QSIM_OK;
+    if (a->base) cudaFree(a->base);
+    if (a->status) cudaFree(a->status);
+    delete a;
+    return QSIM_OK;
+}
+
+extern "C" qsim_status ac_info_get(const ac_handle* a, ac_info* o) {
+    if (!a || !o) return fail(QSIM_EINVAL, "ac_info_get: null pointer");
+    o->obs_dim = a->obs_dim; o->critic_in = a->critic_in; o->hidden = a->hidden; o->batch = a->batch;
+    o->n_actor = a->n_actor; o->n_critic = a->n_critic;
+    o->t_actor = a->t_actor; o->t_critic = a->t_critic; o->updates = a->updates;
+    o->actor = a->actor; o->actor_t = a->actor_t; o->c1 = a->c1; o->c1_t = a->c1_t;
+    o->c2 = a->c2; o->c2_t = a->c2_t; o->m_a = a->m_a; o->v_a = a->v_a;
+    o->m_c1 = a->m_c1; o->v_c1 = a->v_c1; o->m_c2 = a->m_c2; o->v_c2 = a->v_c2;
+    o->stats = a->stats;
+    return QSIM_OK;
+}
+
+extern "C" qsim_status ac_set_counters(ac_handle* a, int64_t t_actor, int64_t t_critic, int64_t updates) {
+    if (!a || t_actor < 0 || t_critic < 0 || updates < 0 || (updates >> 32))
+        return fail(QSIM_EINVAL, "ac_set_counters: bad argument");
+    a->t_actor = t_actor; a->t_critic = t_critic; a->updates = updates;
+    return QSIM_OK;
+}
+
+extern "C" qsim_status ac_update(ac_handle* a, qsim_handle* env, int32_t n_updates, void* stream) {
+    qsim_status s = validate_pair(a, env);
+    if (s != QSIM_OK) return s;
+    if (n_updates < 0) return fail(QSIM_EINVAL, "ac_update: n_updates < 0");
+    if (n_updates == 0) return QSIM_OK;
+    const int64_t lost = env->size == env->capacity ? env->cfg.n_hist : 0;
+    if (env->size - 1 - lost < 1)
+        return fail(QSIM_ESTATE, "ac_update: replay buffer too small to sample (size=%lld)", (long long)env->size);
+    if ((uint64_t)(env->size - 1 - lost) * (uint64_t)env->n >= (1ull << 32))
+        return fail(QSIM_EINVAL, "ac_update: replay buffer exceeds 2^32 transitions");
+    std::vector<ac_handle*> A{a};
+    std::vector<qsim_handle*> E{env};
+    const int nS = pick_cluster(a, 1);
+    return launch_train(A, E, n_updates, 0, nS, (cudaStream_t)stream, nullptr, 1);
+}
+
+extern "C" qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
+                                int64_t steps_per_run, int32_t persistent, void* stream) {
+    if (!runs || !envs || n_runs < 1 || steps_per_run < 0)
+        return fail(QSIM_EINVAL, "ac_train: bad argument");
+    std::vector<ac_handle*> A(runs, runs + n_runs);
+    std::vector<qsim_handle*> E(envs, envs + n_runs);
+    for (int i = 0; i < n_runs; ++i) {
+        qsim_status s = validate_pair(A[i], E[i]);
+        if (s != QSIM_OK) return s;
+        if ((uint64_t)E[i]->capacity * (uint64_t)E[i]->n >= (1ull << 32))
+            return fail(QSIM_EINVAL, "ac_train: replay buffer exceeds 2^32 transitions");
+        if (((E[i]->t_now + steps_per_run) >> 32) != 0)
+            return fail(QSIM_ESTATE, "ac_train: step counter exhausted");
+    }
+    if (steps_per_run == 0) return QSIM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nS = pick_cluster(A[0], n_runs);
+    for (int i = 1; i < n_runs; ++i)
+        if (pick_cluster(A[i], n_runs) != nS) return fail(QSIM_EINVAL, "ac_train: runs need one cluster size");
+    if (!persistent) {
+        for (int64_t t = 0; t < steps_per_run; ++t)
+            for (int i = 0; i < n_runs; ++i) {
+                std::vector<ac_handle*> a1{A[i]};
+                std::vector<qsim_handle*> e1{E[i]};
+                qsim_status s = launch_train(a1, e1, 1, 1, nS, st, nullptr, 1);
+                if (s != QSIM_OK) return s;
+            }
+        return QSIM_OK;
+    }
+    int max_clusters = 1;
+    {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(nS * 1024);
+        lc.blockDim = dim3(LT);
+        lc.dynamicSmemBytes = learner_smem();
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = nS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        if (nS > 8) cudaFuncSetAttribute(k_train, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (cudaOccupancyMaxActiveClusters(&max_clusters, k_train, &lc) != cudaSuccess || max_clusters < 1) {
+            cudaGetLastError();
+            int sms = 152;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, A[0]->device);
+            max_clusters = std::max(1, sms / nS);
+        }
+    }
+    return launch_train(A, E, (int)steps_per_run, 1, nS, st, nullptr, max_clusters);
+}
+
+extern "C" qsim_status ac_sync(ac_handle* a) {
+    if (!a) return fail(QSIM_EINVAL, "ac_sync: null handle");
+    QCHECK_CUDA(cudaDeviceSynchronize());
+    return QSIM_OK;
+}
+
+// ------------------------------------------------------------------------ checkpoints
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t abi, obs_dim, critic_in, hidden, n_actor, n_critic, n_env, ld;
+    int64_t t_actor, t_critic, updates, t_now, head, size, next_curr;
+};
+}  // namespace
+
+extern "C" qsim_status ac_save(const ac_handle* a, const qsim_handle* e, const char* path) {
+    if (!a || !e || !path) return fail(QSIM_EINVAL, "ac_save: null pointer");
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "QSIMCKP1", 8);
+    h.abi = QSIM_ABI_VERSION; h.obs_dim = a->obs_dim; h.critic_in = a->critic_in; h.hidden = a->hidden;
+    h.n_actor = a->n_actor; h.n_critic = a->n_critic; h.n_env = e->n; h.ld = e->ld;
+    h.t_actor = a->t_actor; h.t_critic = a->t_critic; h.updates = a->updates;
+    h.t_now = e->t_now; h.head = e->head; h.size = e->size; h.next_curr = e->next_curriculum;
+    const size_t nparam = 4 * (size_t)a->n_actor + 8 * (size_t)a->n_critic;
+    std::vector<float> w(nparam);
+    QCHECK_CUDA(cudaDeviceSynchronize());
+    QCHECK_CUDA(cudaMemcpy(w.data(), a->base, nparam * 4, cudaMemcpyDeviceToHost));
+    const size_t ld = e->ld;
+    std::vector<float> env_f((NS + 8 + 6 + 4 * HMAX + 2) * ld + 8);
+    std::vector<uint32_t> env_u(4 * ld);
+    float* f = env_f.data();
+    QCHECK_CUDA(cudaMemcpy(f, e->p.state, NS * ld * 4, cudaMemcpyDeviceToHost)); f += NS * ld;
+    QCHECK_CUDA(cudaMemcpy(f, e->p.prm, 8 * ld * 4, cudaMemcpyDeviceToHost)); f += 8 * ld;
+    QCHECK_CUDA(cudaMemcpy(f, e->p.dist, 6 * ld * 4, cudaMemcpyDeviceToHost)); f += 6 * ld;
+    QCHECK_CUDA(cudaMemcpy(f, e->p.hist, 4 * HMAX * ld * 4, cudaMemcpyDeviceToHost)); f += 4 * HMAX * ld;
+    QCHECK_CUDA(cudaMemcpy(f, e->p.ep_ret, ld * 4, cudaMemcpyDeviceToHost)); f += ld;
+    QCHECK_CUDA(cudaMemcpy(f, e->p.ret_sum, ld * 4, cudaMemcpyDeviceToHost)); f += ld;
+    QCHECK_CUDA(cudaMemcpy(f, e->p.rewardC, 8 * 4, cudaMemcpyDeviceToHost));
+    QCHECK_CUDA(cudaMemcpy(env_u.data(), e->p.ep_index, ld * 4, cudaMemcpyDeviceToHost));
+    QCHECK_CUDA(cudaMemcpy(env_u.data() + ld, e->p.ep_step, ld * 4, cudaMemcpyDeviceToHost));
+    QCHECK_CUDA(cudaMemcpy(env_u.data() + 2 * ld, e->p.n_done, ld * 4, cudaMemcpyDeviceToHost));
+    QCHECK_CUDA(cudaMemcpy(env_u.data() + 3 * ld, e->p.len_sum, ld * 4, cudaMemcpyDeviceToHost));
+    std::ofstream os(path, std::ios::binary);
+    if (!os) return fail(QSIM_EINVAL, "ac_save: cannot open %s", path);
+    os.write((const char*)&h, sizeof(h));
+    os.write((const char*)w.data(), w.size() * 4);
+    os.write((const char*)env_f.data(), env_f.size() * 4);
+    os.write((const char*)env_u.data(), env_u.size() * 4);
+    if (!os) return fail(QSIM_EINVAL, "ac_save: write failed");
+    return QSIM_OK;
+}
+
+extern "C" qsim_status ac_load(ac_handle* a, qsim_handle* e, const char* path) {
+    if (!a || !e || !path) return fail(QSIM_EINVAL, "ac_load: null pointer");
+    std::ifstream is(path, std::ios::binary);
+    if (!is) return fail(QSIM_EINVAL, "ac_load: cannot open %s", path);
+    CkptHeader h;
+    is.read((char*)&h, sizeof(h));
+    if (!is || memcmp(h.magic, "QSIMCKP1", 8) != 0) return fail(QSIM_EVERSION, "ac_load: not a checkpoint");
+    if (h.abi != QSIM_ABI_VERSION || h.obs_dim != a->obs_dim || h.critic_in != a->critic_in ||
+        h.hidden != a->hidden || h.n_actor != a->n_actor || h.n_critic != a->n_critic ||
+        h.n_env != e->n || h.ld != e->ld)
+        return fail(QSIM_EVERSION, "ac_load: checkpoint layout does not match the handles");
+    const size_t nparam = 4 * (size_t)a->n_actor + 8 * (size_t)a->n_critic;
+    const size_t ld = e->ld;
+    std::vector<float> w(nparam), env_f((NS + 8 + 6 + 4 * HMAX + 2) * ld + 8);
+    std::vector<uint32_t> env_u(4 * ld);
+    is.read((char*)w.data(), w.size() * 4);
+    is.read((char*)env_f.data(), env_f.size() * 4);
+    is.read((char*)env_u.data(), env_u.size() * 4);
+    if (!is) return fail(QSIM_EVERSION, "ac_load: truncated checkpoint");
+    QCHECK_CUDA(cudaDeviceSynchronize());
+    QCHECK_CUDA(cudaMemcpy(a->base, w.data(), nparam * 4, cudaMemcpyHostToDevice));
+    const float* f = env_f.data();
+    QCHECK_CUDA(cudaMemcpy(e->p.state, f, NS * ld * 4, cudaMemcpyHostToDevice)); f += NS * ld;
+    QCHECK_CUDA(cudaMemcpy(e->p.prm, f, 8 * ld * 4, cudaMemcpyHostToDevice)); f += 8 * ld;
+    QCHECK_CUDA(cudaMemcpy(e->p.dist, f, 6 * ld * 4, cudaMemcpyHostToDevice)); f += 6 * ld;
+    QCHECK_CUDA(cudaMemcpy(e->p.hist, f, 4 * HMAX * ld * 4, cudaMemcpyHostToDevice)); f += 4 * HMAX * ld;
+    QCHECK_CUDA(cudaMemcpy(e->p.ep_ret, f, ld * 4, cudaMemcpyHostToDevice)); f += ld;
+    QCHECK_CUDA(cudaMemcpy(e->p.ret_sum, f, ld * 4, cudaMemcpyHostToDevice)); f += ld;
+    QCHECK_CUDA(cudaMemcpy(e->p.rewardC, f, 8 * 4, cudaMemcpyHostToDevice));
+    QCHECK_CUDA(cudaMemcpy(e->p.ep_index, env_u.data(), ld * 4, cudaMemcpyHostToDevice));
+    QCHECK_CUDA(cudaMemcpy(e->p.ep_step, env_u.data() + ld, ld * 4, cudaMemcpyHostToDevice));
+    QCHECK_CUDA(cudaMemcpy(e->p.n_done, env_u.data() + 2 * ld, ld * 4, cudaMemcpyHostToDevice));
+    QCHECK_CUDA(cudaMemcpy(e->p.len_sum, env_u.data() + 3 * ld, ld * 4, cudaMemcpyHostToDevice));
+    a->t_actor = h.t_actor; a->t_critic = h.t_critic; a->updates = h.updates;
+    e->t_now = h.t_now; e->head = h.head; e->size = h.size; e->next_curriculum = h.next_curr;
+    return QSIM_OK;
+}

@@ -1,0 +1,255 @@
+"""GPU parity of the env-side entry points against the FP64 oracle (teacher-forced: each
+call's FP32 inputs are read back and promoted to FP64 for the oracle)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from helpers import (STATE_SCALE, assert_close, compare_records, cpu, f64, gpu_records,
+                     lib_config, oracle_envs, u32)
+
+pytestmark = pytest.mark.gpu
+
+
+def test_philox_streams_bit_exact(gpu):
+    q = gpu
+    seed = 0x123456789ABCDEF0
+    for tag, sub, c1, run in ((0, 0, 0, 0), (3, 1, 777, 5), (4, 0, 2**31 + 3, 511)):
+        out = torch.empty(4 * 1000, dtype=torch.int32, device="cuda")
+        q.qsim_philox_fill(seed, run, tag, sub, c1, out, kind=0)
+        g = u32(out).reshape(-1, 4)
+        key = [seed & 0xFFFFFFFF, seed >> 32]
+        for i in list(range(0, 1000, 37)) + [999]:
+            ref = O.philox([i, c1, (tag << 24) | sub, run], key)
+            assert [int(x) for x in g[i]] == [int(x) for x in ref]
+        # uniforms: exact in float32
+        q.qsim_philox_fill(seed, run, tag, sub, c1, out, kind=1)
+        uf = cpu(out).view(np.float32).reshape(-1, 4)
+        ref_u = np.array([[O.uniform(int(x)) for x in row] for row in g], dtype=np.float64)
+        assert np.array_equal(uf.astype(np.float64), ref_u)
+        # Box-Muller normals: float32 vs float64
+        q.qsim_philox_fill(seed, run, tag, sub, c1, out, kind=2)
+        z = cpu(out).view(np.float32).reshape(-1, 4)[:, :2].astype(np.float64)
+        ref_z = np.array([[O.gauss(r[0], r[1]), O.gauss(r[2], r[3])] for r in g])
+        assert_close(z, ref_z, 1.0, rtol=1e-5, what="gauss")
+    # host-side Philox is the same stream
+    assert q.qsim_philox_host([1, 2, 3, 4], [5, 6]) == [int(x) for x in O.philox([1, 2, 3, 4], [5, 6])]
+
+
+@pytest.mark.parametrize("n,steps", [(1, 1), (1000, 1), (333, 25), (4096, 3)])
+def test_dynamics_step_parity(gpu, n, steps):
+    q = gpu
+    d = W.config("c1")
+    veh = q.make_params(d)
+    ld = q.padded(n)
+    s = W.random_states(7 + n, n)
+    prm = W.random_params(8 + n, n)
+    u = W.random_actions(9 + n, (n, 4), 0.0, 21702.0)
+    dist = W.random_actions(10 + n, (n, 6), -1e-3, 1e-3)
+
+    def dev(x, rows):
+        t = torch.zeros(rows, ld, dtype=torch.float32)
+        t[:, :n] = torch.tensor(x.T, dtype=torch.float32)
+        return t.cuda()
+
+    S, Pm, U, D = dev(s, 17), dev(prm, 8), dev(u, 4), dev(dist, 6)
+    out = torch.empty_like(S)
+    q.qsim_dynamics_step(veh, Pm, D, S, U, 0.01, 1, n, ld, steps, out)
+    torch.cuda.synchronize()
+    ref = O.dynamics_batch(d, f64(S)[:, :n].T, f64(U)[:, :n].T, f64(Pm)[:, :n].T,
+                           f64(D)[:, :n].T, dt=np.float64(np.float32(0.01)), renorm=1,
+                           n_steps=steps)
+    assert_close(f64(out)[:, :n].T, ref, STATE_SCALE, what="state")
+
+
+def test_dynamics_rejects_bad_arguments(gpu):
+    q = gpu
+    veh = q.make_params(W.config("c1"))
+    S = torch.zeros(17, 32, device="cuda")
+    with pytest.raises(q.QsimError):
+        q.qsim_dynamics_step(veh, S, None, S, S, 0.01, 1, 40, 32, 1, S)  # ld < n
+    with pytest.raises(q.QsimError):
+        q.qsim_dynamics_step(veh, S, None, S, S, -0.01, 1, 8, 32, 1, S)  # dt <= 0
+    with pytest.raises(q.QsimError):
+        q.qsim_dynamics_step(veh, S[:, 1:], None, S, S, 0.01, 1, 8, 32, 1, S)  # misaligned
+
+
+def test_create_resets_like_oracle(gpu):
+    q = gpu
+    d, cfg, veh = lib_config(q, "c2", n_envs=200, capacity=0)
+    h = q.qsim_create(cfg, veh)
+    try:
+        info = q.qsim_info_get(h)
+        st, prm = f64(info["state"]), f64(info["params"])
+        for e in (0, 1, 17, 199):
+            s_ref, p_ref, _ = O.reset_env(d, e, 0)
+            assert_close(st[:, e], s_ref, STATE_SCALE, what="reset state")
+            assert_close(prm[:7, e], p_ref[:7], np.abs(p_ref[:7]) + 1e-30, what="reset params")
+        assert np.all(f64(info["hist"]) == 0)
+    finally:
+        q.qsim_destroy(h)
+
+
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_step_and_observe_parity(gpu, layout):
+    q = gpu
+    n = 70
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=16, critic_layout=layout,
+                             episode_len=9, sig_p=0.01, sig_R=0.02, sig_v=0.03, sig_w=0.04,
+                             dist_f=0.01, dist_tau=1e-4)
+    h = q.qsim_create(cfg, veh)
+    try:
+        info = q.qsim_info_get(h)
+        ld = info["ld"]
+        da, dc = info["obs_dim"], info["critic_obs_dim"]
+        for step in range(12):
+            acts = torch.tensor(W.random_actions(100 + step, (4, ld), -1.3, 1.3), dtype=torch.float32,
+                                device="cuda")
+            info = q.qsim_info_get(h)
+            ids = np.arange(n)
+            e = oracle_envs(info, ids)
+            t0, head0 = info["t_now"], info["head"]
+            oa = torch.zeros(da, ld, device="cuda")
+            oc = torch.zeros(dc, ld, device="cuda")
+            rw = torch.zeros(ld, device="cuda")
+            te = torch.zeros(ld, dtype=torch.uint8, device="cuda")
+            tr = torch.zeros(ld, dtype=torch.uint8, device="cuda")
+            q.qsim_step(h, acts, oa, oc, rw, te, tr)
+            torch.cuda.synchronize()
+            ref = O.rollout(d, W.REWARD, e, 1, t0, ext_actions=f64(acts)[:, :n].T[None])
+            info = q.qsim_info_get(h)
+            compare_records(gpu_records(info, [head0], ids), ref, what=f"step{step}")
+            assert_close(f64(info["state"])[:, :n].T, e["s"], STATE_SCALE, what="next state")
+            assert np.array_equal(u32(info["ep_index"])[:n], e["ep_index"])
+            assert np.array_equal(u32(info["ep_step"])[:n], e["ep_step"])
+            assert_close(f64(rw)[:n], ref["rec_r"][0], 1.0, what="reward out")
+            assert np.array_equal(cpu(te)[:n], (ref["rec_flags"][0] & 1).astype(np.uint8))
+            assert np.array_equal(cpu(tr)[:n], ((ref["rec_flags"][0] >> 1) & 1).astype(np.uint8))
+            # observations of the next step
+            for k in range(0, n, 7):
+                o_ref = O.obs_actor(d, e["s"][k], e["hist"][k], O.obs_noise(d, k, t0 + 1))
+                assert_close(f64(oa)[:, k], o_ref, 1.0, what="obs_a")
+                pv = O.priv(d, e["prm"][k], e["dist"][k])
+                c_ref = O.obs_critic(d, e["s"][k], e["hist"][k], pv)
+                assert_close(f64(oc)[:, k], c_ref, 1.0, what="obs_c")
+        st = q.qsim_stats_get(h)
+        assert st["episodes"] > 0 and st["mean_length"] <= 9
+    finally:
+        q.qsim_destroy(h)
+
+
+def _actor(d, hidden, seed=0):
+    dd = dict(d)
+    dd["seed"] = seed
+    return O.init_params(dd, 0, O.actor_in(d), hidden, 4).astype(np.float32)
+
+
+@pytest.mark.parametrize("hidden,n,warps", [(64, 300, 0), (64, 1000, 4), (32, 100, 0),
+                                            (128, 200, 2), (64, 64, 10)])
+def test_rollout_parity(gpu, hidden, n, warps):
+    q = gpu
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=6, learning_starts=3, episode_len=40,
+                             sig_p=0.005, sig_R=0.01, sig_v=0.02, sig_w=0.02)
+    h = q.qsim_create(cfg, veh)
+    try:
+        if warps:
+            q.qsim_rollout_tune(h, warps)
+        actor = _actor(d, hidden)
+        A = torch.tensor(actor, device="cuda")
+        ids = np.arange(n)
+        for call, T in enumerate((2, 1, 3, 1)):
+            info = q.qsim_info_get(h)
+            e = oracle_envs(info, ids)
+            t0, head0 = info["t_now"], info["head"]
+            q.qsim_rollout(h, A, hidden, T, 0.1)
+            torch.cuda.synchronize()
+            ref = O.rollout(d, W.REWARD, e, T, t0, actor=actor.astype(np.float64), hidden=hidden,
+                            sigma_e=0.1, n_threads=8)
+            info = q.qsim_info_get(h)
+            slots = [(head0 + k) % 6 for k in range(T)]
+            if T == 1:
+                compare_records(gpu_records(info, slots, ids), ref, what=f"rollout{call}")
+                assert_close(f64(info["state"])[:, :n].T, e["s"], STATE_SCALE, what="state")
+                assert_close(f64(info["hist"])[:, :n].T, e["hist"], 1.0, what="hist")
+                assert np.array_equal(u32(info["ep_step"])[:n], e["ep_step"])
+            else:
+                # several steps in one call: first step strictly, later steps where the
+                # trajectories have not been separated by a termination decision
+                g = gpu_records(info, slots, ids)
+                compare_records({k: v[:1] for k, v in g.items()}, {k: v[:1] for k, v in ref.items()},
+                                what=f"rollout{call}.0")
+                same = np.all(g["rec_flags"] == ref["rec_flags"], axis=0)
+                assert same.mean() > 0.99
+                assert_close(g["rec_s"][:, same], ref["rec_s"][:, same], STATE_SCALE, what="multi s")
+    finally:
+        q.qsim_destroy(h)
+
+
+def test_rollout_full_size_sampled(gpu):
+    """65,536 envs in the benchmark's launch configuration; 256 sampled envs checked."""
+    q = gpu
+    n = 65536
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=4, learning_starts=0)
+    h = q.qsim_create(cfg, veh)
+    try:
+        actor = _actor(d, 64)
+        A = torch.tensor(actor, device="cuda")
+        q.qsim_rollout(h, A, 64, 3, 0.1)
+        ids = np.unique([O.replay_index(int(O.philox([i, 0, 4 << 24, 0], [0, 0])[0]), n)
+                         for i in range(256)])
+        info = q.qsim_info_get(h)
+        e = oracle_envs(info, ids)
+        t0, head0 = info["t_now"], info["head"]
+        q.qsim_rollout(h, A, 64, 1, 0.1)
+        torch.cuda.synchronize()
+        ref = O.rollout(d, W.REWARD, e, 1, t0, actor=actor.astype(np.float64), hidden=64,
+                        sigma_e=0.1, n_threads=8)
+        info = q.qsim_info_get(h)
+        compare_records(gpu_records(info, [head0], ids), ref, what="c2 sampled")
+        assert_close(f64(info["state"])[:, ids].T, e["s"], STATE_SCALE, what="c2 state")
+    finally:
+        q.qsim_destroy(h)
+
+
+def test_rollout_deterministic(gpu):
+    q = gpu
+    d, cfg, veh = lib_config(q, "c2", n_envs=500, capacity=20, learning_starts=0)
+    A = torch.tensor(_actor(d, 64), device="cuda")
+    outs = []
+    for _ in range(2):
+        h = q.qsim_create(cfg, veh)
+        q.qsim_rollout(h, A, 64, 17, 0.1)
+        info = q.qsim_info_get(h)
+        outs.append((cpu(info["records"]).copy(), cpu(info["state"]).copy()))
+        q.qsim_destroy(h)
+    assert np.array_equal(outs[0][0].view(np.uint32), outs[1][0].view(np.uint32))
+    assert np.array_equal(outs[0][1].view(np.uint32), outs[1][1].view(np.uint32))
+
+
+def test_recalc_rewards_parity(gpu):
+    q = gpu
+    n = 40
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=30, episode_len=7, learning_starts=0)
+    h = q.qsim_create(cfg, veh)
+    try:
+        A = torch.tensor(_actor(d, 64), device="cuda")
+        q.qsim_rollout(h, A, 64, 45, 0.3)  # wraps the ring
+        C2 = list(W.REWARD)
+        C2[4] = 0.37
+        C2[0] = 2.0
+        q.qsim_set_reward(h, C2, 0.1)
+        q.qsim_recalc_rewards(h)
+        torch.cuda.synchronize()
+        info = q.qsim_info_get(h)
+        cap = info["capacity"]
+        rec = f64(info["records"])
+        raw = cpu(info["records"]).view(np.uint32)
+        buf = dict(s=rec[:, 0:17, :n].transpose(0, 2, 1), a=rec[:, 17:21, :n].transpose(0, 2, 1),
+                   r=np.zeros((cap, n)), flags=raw[:, 22, :n], priv=np.zeros((cap, n, 6)),
+                   side=np.nan_to_num(f64(info["side"])[:, :, :n].transpose(0, 2, 1)),
+                   head=info["head"], size=info["size"], t_now=info["t_now"])
+        O.recalc_rewards(C2, buf, f64(info["state"])[:, :n].T)
+        assert_close(rec[:, 21, :n], buf["r"], 1.0, what="recalc")
+    finally:
+        q.qsim_destroy(h)
