@@ -1,0 +1,446 @@
+"""Benchmark of the quadrotor training hot path on GB300.
+
+Default workload (one bench step): the fused env step of 65,536 domain-randomised
+quadrotors for 1,000 steps each (actor MLP 82-64-64-4 with Gaussian exploration, RK4
+dynamics with motor lag, reward, termination, reset) writing every transition into a
+65,536 x 1,000 device replay ring -- 65.5 M env-steps per bench step.
+
+Printed as ONE JSON line (rank 0).  Besides the headline env-steps/s it carries the
+roofline of the dominant kernel (FP32 FMA bound), the end-to-end number through the C ABI
+with host buffers, the FP64 oracle timed on this host's cores, and secondary measurements
+of the other hot-path pieces: the learner (wall time to N actor-critic updates, batched
+persistent launch vs the plain one-run-per-launch form), reward recalculation bandwidth,
+the dynamics-only benchmark in the paper's shape, and reverse-mode gradients.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank simulates its own 65,536 envs (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("env-steps/s (sim+policy) and wall time to N actor-critic updates on 1 GB300, "
+          "vs plain")
+FLOP_ACTOR = lambda da, h: 2 * (da * h + h * h + 4 * h)  # noqa: E731
+FLOP_DYN = 672        # RK4 (4 derivative evaluations + stage/accumulation arithmetic)
+FLOP_MISC = 60        # observation rotation matrix, reward, termination, action map
+BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, flags)
+# DRAM bytes per env-step of k_rollout<64,*> measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum, 32,768 envs x 100 steps; profiles/k_rollout_c2_65536x1000.md).
+# Set to None whenever the kernel changes until it is captured again.
+NCU_DRAM_BYTES_PER_ENV_STEP = (46.935808e6 + 289.2096e6) / (32768 * 100)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--envs", type=int, default=65536)
+    ap.add_argument("--horizon", type=int, default=1000)
+    ap.add_argument("--no-extras", action="store_true", help="headline measurement only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.zero_()
+
+
+def device_peaks(torch, q):
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    max_mhz = 2070.0
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        max_mhz = float(mp.get("sm_max_mhz", max_mhz))
+        hbm = float(mp["hbm_gbs"])
+        hbm_src = "measured"
+    except Exception:
+        hbm, hbm_src = 6800.0, "fallback"
+    fp32 = sms * 128 * 2 * max_mhz * 1e6 / 1e12
+    return sms, max_mhz, fp32, hbm, hbm_src
+
+
+# -------------------------------------------------------------------------- measurements
+def measure_ffma(torch, q):
+    out = torch.zeros(4, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks, iters = sms * 8, 4096
+    q.qsim_ffma_probe(blocks, 64, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    q.qsim_ffma_probe(blocks, iters, out)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    flops = blocks * 256 * iters * 8 * 16 * 2
+    return flops / (ms * 1e-3) / 1e12
+
+
+def measure_dynamics(torch, q, veh):
+    """Paper's simulator benchmark shape: 8,192 envs x 1e6 RK4 steps, no policy."""
+    res = {}
+    for n, steps, tag in ((8192, 1_000_000, "paper_shape_8192x1e6"),
+                          (155_648, 50_000, "saturating_155648x5e4")):
+        ld = (n + 31) // 32 * 32
+        out = torch.empty(17, ld, device="cuda")
+        q.qsim_dynamics_bench(veh, n, ld, 1000, 0.01, out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        q.qsim_dynamics_bench(veh, n, ld, steps, 0.01, out)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        res[tag] = {"env_steps_per_s": n * steps / (ms * 1e-3), "ms": ms,
+                    "tflops": n * steps * FLOP_DYN / (ms * 1e-3) / 1e12,
+                    "finite": bool(torch.isfinite(out[:, :n]).all())}
+    return res
+
+
+def measure_recalc(torch, q, h, n, horizon, hbm):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q.qsim_recalc_rewards(h)
+    st.synchronize()
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        q.qsim_recalc_rewards(h)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    records = n * horizon
+    byts = records * (17 * 4 + 4 * 4 + 4 + 4)  # read s', a, flags; write r
+    return {"records": records, "ms": ms, "gbs": byts / (ms * 1e-3) / 1e9,
+            "frac_of_measured_hbm": byts / (ms * 1e-3) / 1e9 / hbm, "bytes_per_record": 92}
+
+
+def measure_training(torch, q, W, n_runs=512, steps=20, prefill=20):
+    """Batched training sample: n_runs independent runs (widths {32,64,128}, batches
+    {128,256,512} drawn per run from Philox, 8 envs each).  Wall time to n_runs x steps
+    updates, persistent batched launch vs the plain one-run-per-launch form."""
+    res = {}
+    widths, batches = (32, 64, 128), (128, 256, 512)
+    for mode in ("persistent", "plain"):
+        runs, envs = [], []
+        flops = 0.0
+        for r in range(n_runs):
+            x = q.qsim_philox_host([0, 0, 9 << 24, r], [r, 0])
+            hid, B = widths[x[0] % 3], batches[x[1] % 3]
+            d = W.config("c2")
+            d.update(seed=r, run_id=r, learning_starts=0)
+            cfg = q.make_config(d, 8, 2048, reward=W.REWARD, sigma_e=0.1)
+            h = q.qsim_create(cfg, q.make_params(d))
+            hp = dict(W.TD3)
+            hp.update(hidden=hid, batch=B)
+            a = q.ac_create(q.make_ac_config(hp, cluster=1), h)
+            runs.append(a)
+            envs.append(h)
+            da, dc = 82, 90
+            mac = (da * hid + hid * hid + 4 * hid) * 1.5 + (dc * hid + hid * hid + hid) * 6 \
+                + 0.5 * ((dc * hid + hid * hid + hid) * 2)
+            flops += 2 * mac * B * steps
+        q.ac_train(runs, envs, prefill, persistent=1)  # fills buffers past the history window
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.ac_train(runs, envs, steps, persistent=1 if mode == "persistent" else 0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[mode] = {"s": dt, "updates": n_runs * steps, "updates_per_s": n_runs * steps / dt,
+                     "tflops": flops / dt / 1e12}
+        for a, h in zip(runs, envs):
+            q.ac_destroy(a)
+            q.qsim_destroy(h)
+    res["speedup_vs_plain"] = res["plain"]["s"] / res["persistent"]["s"]
+    res["config"] = {"runs": n_runs, "steps_per_run": steps, "envs_per_run": 8,
+                     "updates_per_step": 1}
+    return res
+
+
+def measure_c1(torch, q, W, steps=2000):
+    """Plain single run (1 env, batch 256): wall time per env step + update."""
+    d = W.config("c1")
+    d.update(learning_starts=0)
+    cfg = q.make_config(d, 1, 10_000, reward=W.REWARD, sigma_e=0.1)
+    h = q.qsim_create(cfg, q.make_params(d))
+    hp = dict(W.TD3)
+    a = q.ac_create(q.make_ac_config(hp), h)
+    q.ac_train([a], [h], 100, persistent=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q.ac_train([a], [h], steps, persistent=1)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    q.ac_destroy(a)
+    q.qsim_destroy(h)
+    return {"steps": steps, "s": dt, "updates_per_s": steps / dt,
+            "projected_9000_updates_s": 9000 * dt / steps}
+
+
+def cpu_baseline(n_envs=4096, horizon=1000, chunk=50):
+    """The FP64 oracle (as it stands) on this host's cores: a bounded sample of the
+    rollout workload (n_envs x horizon env-steps, all cores)."""
+    import numpy as np
+
+    import oracle as O
+    import workloads as W
+    O.build()
+    cores = os.cpu_count() or 1
+    d = W.config("c2")
+    d.update(learning_starts=0)
+    actor = O.init_params(d, 0, 82, 64, 4)
+    e = O.new_envs(d, np.arange(n_envs))
+    t0 = time.perf_counter()
+    for c in range(0, horizon, chunk):
+        O.rollout(d, W.REWARD, e, min(chunk, horizon - c), c, actor=actor, hidden=64,
+                  sigma_e=0.1, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n_envs * horizon / dt, "unit": "env-steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{n_envs} envs x {horizon} steps of the same rollout workload "
+                      f"(FP64 C oracle, {cores} threads), {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------------------ main arms
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle as O
+    import workloads as W
+    O.build()
+    cores = os.cpu_count() or 1
+    d = W.config("c2")
+    d.update(learning_starts=0)
+    actor = O.init_params(d, 0, 82, 64, 4)
+    n, T = 4096, 40
+    e = O.new_envs(d, np.arange(n))
+    t = 0
+    for _ in range(args.warmup):
+        O.rollout(d, W.REWARD, e, T, t, actor=actor, hidden=64, sigma_e=0.1, n_threads=cores)
+        t += T
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.rollout(d, W.REWARD, e, T, t, actor=actor, hidden=64, sigma_e=0.1, n_threads=cores)
+        t += T
+    dt = time.perf_counter() - t0
+    v = n * T * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "env-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "c2 rollout sample: 4096 domain-randomised envs x 40 steps "
+                       "per bench step (of 65,536 x 1,000)", "envs": n, "steps_per_bench_step": T},
+            "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{n} envs x {T} steps per bench step, {cores} threads"},
+            "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2311_13081_gb300 as q
+    import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    q.load()
+    n, horizon = args.envs, args.horizon
+    d = W.config("c2")
+    d.update(learning_starts=0, seed=0, run_id=rank)
+    veh = q.make_params(d)
+    cfg = q.make_config(d, n, horizon, reward=W.REWARD, sigma_e=0.1)
+    h = q.qsim_create(cfg, veh)
+    hp = dict(W.TD3)
+    a = q.ac_create(q.make_ac_config(hp), h)  # random-init actor (Philox tag 7, seed 0)
+    actor = q.ac_info_get(a)["actor"]
+    hidden = 64
+    info = q.qsim_info_get(h)
+    l2 = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
+    tuned = q.qsim_rollout_autotune(h, actor, hidden, 100)
+    for _ in range(args.warmup):
+        q.qsim_rollout(h, actor, hidden, horizon)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        time.sleep(0.3)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush_l2(l2)
+            starts[k].record()
+            q.qsim_rollout(h, actor, hidden, horizon)
+            ends[k].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_dev = sum(ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_dev], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+        dist.barrier()
+    env_steps = n * horizon * args.steps * world
+    value = env_steps / t_dev
+    sms, max_mhz, fp32_peak, hbm, hbm_src = device_peaks(torch, q)
+    flop_step = FLOP_ACTOR(82, hidden) + FLOP_DYN + FLOP_MISC
+    achieved = n * horizon * flop_step / (sum(ms) / args.steps * 1e-3) / 1e12
+    clocks = clk.summary()
+
+    # end to end through the C ABI with host buffers: pinned actor weights in, episode
+    # statistics out, every step
+    host_actor = actor.detach().cpu().pin_memory()
+    dev_actor = torch.empty_like(actor)
+    host_stats = torch.empty(3, info["ld"], dtype=torch.int32).pin_memory()
+    stats_dev = torch.stack([info["n_done"], info["len_sum"], info["ret_sum"].view(torch.int32)])
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(args.steps):
+        dev_actor.copy_(host_actor, non_blocking=True)
+        q.qsim_rollout(h, dev_actor, hidden, horizon)
+        stats_dev = torch.stack([info["n_done"], info["len_sum"], info["ret_sum"].view(torch.int32)])
+        host_stats.copy_(stats_dev, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - w0
+    e2e = {"value": env_steps / max(e2e_t, 1e-9) if world == 1 else None, "unit": "env-steps/s",
+           "h2d_bytes_per_step": host_actor.numel() * 4,
+           "d2h_bytes_per_step": host_stats.numel() * 4}
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["fp32_ffma_probe_tflops"] = measure_ffma(torch, q)
+        extras["reward_recalc"] = measure_recalc(torch, q, h, n, horizon, hbm)
+        st = q.qsim_stats_get(h)
+        extras["episodes"] = st
+    q.ac_destroy(a)
+    q.qsim_destroy(h)
+    del l2
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extras:
+        extras["dynamics_only"] = measure_dynamics(torch, q, veh)
+        extras["learner_batched"] = measure_training(torch, q, W)
+        extras["learner_single_run_c1"] = measure_c1(torch, q, W)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "env-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"c2 batched rollout: {n} domain-randomised quadrotors x "
+                                   f"{horizon} steps per bench step, actor 82-64-64-4, "
+                                   f"replay {n}x{horizon} in HBM",
+                       "envs_per_gpu": n, "steps_per_bench_step": horizon,
+                       "l2": "flushed before every timed step (512 MB write)",
+                       "rollout_warps_per_block": tuned},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "traffic": (None if NCU_DRAM_BYTES_PER_ENV_STEP is None
+                                     else NCU_DRAM_BYTES_PER_ENV_STEP * n * horizon),
+                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                         "flop_per_env_step": flop_step,
+                         "hbm_gbs_achieved": n * horizon * BYTES_STEP / (sum(ms) / args.steps * 1e-3) / 1e9,
+                         "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
+            "cpu_baseline": cpu, "step_ms": ms, "wall_s": wall,
+        }
+        line.update(extras)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

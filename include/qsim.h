@@ -210,6 +210,18 @@ qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t hidden, int
  * effect. */
 int32_t qsim_rollout_tune(qsim_handle* h, int32_t warps_per_block);
 
+/* Autotuner: times every warps-per-block variant of the rollout kernel that fits on this
+ * device with n_steps-step rollouts (CUDA events on `stream`; these are real env steps
+ * that advance the env set), keeps the fastest for this handle and returns its warps
+ * per block (negative qsim_status on error).  Synchronises the stream. */
+int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int32_t hidden,
+                              int32_t n_steps, void* stream);
+
+/* FP32 FMA throughput probe: every thread of n_blocks x 256 runs `iters` iterations of 16
+ * independent FMA chains; out[0] receives a checksum (device).  Used to confirm the FP32
+ * roofline peak. */
+qsim_status qsim_ffma_probe(int32_t n_blocks, int32_t iters, float* out, void* stream);
+
 /* Recompute every stored reward from (s', a) with the current reward constants (Sec. VI
  * reward recalculation). */
 qsim_status qsim_recalc_rewards(qsim_handle* h, void* stream);

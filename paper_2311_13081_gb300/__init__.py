@@ -117,6 +117,8 @@ _SIGS = {
     "qsim_step": (C.c_int, [P, P, P, P, P, P, P, P]),
     "qsim_rollout": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_float, P]),
     "qsim_rollout_tune": (C.c_int32, [P, C.c_int32]),
+    "qsim_rollout_autotune": (C.c_int32, [P, P, C.c_int32, C.c_int32, P]),
+    "qsim_ffma_probe": (C.c_int, [C.c_int32, C.c_int32, P, P]),
     "qsim_recalc_rewards": (C.c_int, [P, P]),
     "qsim_set_reward": (C.c_int, [P, P, C.c_float, P]),
     "qsim_stats_get": (C.c_int, [P, C.POINTER(QsimStats), P]),
@@ -334,6 +336,18 @@ def qsim_rollout(h, actor, hidden, n_steps, sigma_e=-1.0, stream=None):
 
 def qsim_rollout_tune(h, warps_per_block=0) -> int:
     return _lib.qsim_rollout_tune(h, warps_per_block)
+
+
+def qsim_rollout_autotune(h, actor, hidden, n_steps, stream=None) -> int:
+    r = _lib.qsim_rollout_autotune(h, _ptr(actor), hidden, n_steps, _stream(stream))
+    if r < 0:
+        _chk(r)
+    return int(r)
+
+
+def qsim_ffma_probe(n_blocks, iters, out, stream=None):
+    load()
+    _chk(_lib.qsim_ffma_probe(n_blocks, iters, _ptr(out), _stream(stream)))
 
 
 def qsim_recalc_rewards(h, stream=None):

@@ -336,6 +336,24 @@ __global__ void k_set_reward(float* rewardC, float c0, float c1, float c2, float
     rewardC[4] = c4; rewardC[5] = c5; rewardC[6] = c6; rewardC[7] = sigma;
 }
 
+// 16 independent FMA chains per thread: issue-bound on the FP32 pipe.
+__global__ void __launch_bounds__(256) k_ffma_probe(int iters, float* out) {
+    float a[16];
+    const float x = 1.0f + 1e-7f * (float)threadIdx.x, y = 0.999999f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = (float)(i + blockIdx.x);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[i] = fmaf(a[i], y, x);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += a[i];
+    if (s == 12345.678f) out[0] = s;  // keeps the chains live
+}
+
 static int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
 
 }  // namespace qsim
@@ -608,5 +626,12 @@ extern "C" qsim_status qsim_stats_get(qsim_handle* h, qsim_stats* out, void* str
     out->episodes = ep;
     out->mean_length = ep ? len / (double)ep : 0.0;
     out->mean_return = ep ? ret / (double)ep : 0.0;
+    return QSIM_OK;
+}
+
+extern "C" qsim_status qsim_ffma_probe(int32_t n_blocks, int32_t iters, float* out, void* stream) {
+    if (n_blocks <= 0 || iters <= 0 || !out) return fail(QSIM_EINVAL, "qsim_ffma_probe: bad argument");
+    k_ffma_probe<<<n_blocks, 256, 0, (cudaStream_t)stream>>>(iters, out);
+    QCHECK_LAUNCH("k_ffma_probe");
     return QSIM_OK;
 }

@@ -471,3 +471,40 @@ extern "C" qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t 
     }
     return QSIM_OK;
 }
+
+extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int32_t hidden,
+                                         int32_t n_steps, void* stream) {
+    if (!h || !actor || n_steps <= 0) return fail(QSIM_EINVAL, "qsim_rollout_autotune: bad argument");
+    if (hidden != 32 && hidden != 64 && hidden != 128)
+        return fail(QSIM_EINVAL, "qsim_rollout_autotune: hidden=%d not in {32,64,128}", hidden);
+    int smem_blk = 227 * 1024;
+    cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    QCHECK_CUDA(cudaEventCreate(&e0));
+    QCHECK_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_nw = 0;
+    for (int nw : kWarpChoices) {
+        if (roll_smem(hidden, nw) > (size_t)smem_blk) continue;
+        if (((h->t_now + n_steps) >> 32) != 0) break;
+        cudaEventRecord(e0, st);
+        qsim_status s = launch_rollout(h, actor, hidden, n_steps, -1.0f, st, nw);
+        cudaEventRecord(e1, st);
+        if (s != QSIM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+        h->t_now += n_steps;
+        if (h->capacity > 0) {
+            h->head = (h->head + n_steps) % h->capacity;
+            h->size = std::min<int64_t>(h->capacity, h->size + n_steps);
+        }
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_nw = nw; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    QCHECK_LAUNCH("qsim_rollout_autotune");
+    if (best_nw) h->rollout_warps = best_nw;
+    return best_nw;
+}
