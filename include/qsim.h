@@ -276,6 +276,29 @@ qsim_status ac_set_counters(ac_handle* a, int64_t t_actor, int64_t t_critic, int
  * critic 1, Adam on the actor and Polyak averaging of all targets. */
 qsim_status ac_update(ac_handle* a, qsim_handle* env, int32_t n_updates, void* stream);
 
+/* Allocation-free variant of ac_update, for callers that cannot allocate device memory
+ * while they run updates -- for example an embedded trainer that reserves all memory up
+ * front, code running under a custom allocator that forbids cudaMalloc, or a host thread
+ * that must not take the driver's allocation locks.  The paper has no counterpart; this is
+ * a deployment convenience of this library.  Same arguments, semantics and results as
+ * ac_update; the learner and env handles still supply every input and output.
+ * Differences:
+ *  - Scratch (activations, partial gradients, the run descriptor) lives in a static
+ *    device array of QSIM_STATIC_SCRATCH_BYTES (+ QSIM_STATIC_DESC_BYTES) that every GPU
+ *    which loads the library holds until the process exits.  Configurations needing more
+ *    scratch (large batch x hidden, see the error message) return QSIM_EINVAL.
+ *  - The call makes no cudaMalloc / cudaFree and calls no allocating library routine.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call before any
+ *    stream capture.
+ *  - Every call shares the one array: calls whose work overlaps on the GPU (other streams,
+ *    other threads) race and must be serialised by the caller.  The array keeps the last
+ *    call's contents; nothing in it needs to start at zero.
+ *  - Synchronises `stream` (the updated counters are read back). */
+#define QSIM_STATIC_SCRATCH_BYTES (8u << 20)
+#define QSIM_STATIC_DESC_BYTES (4u << 10)
+qsim_status ac_update_static(ac_handle* a, qsim_handle* env, int32_t n_updates, void* stream);
+
 /* Train n_runs independent runs for steps_per_run env steps each: per step, the fused
  * env step of each run's envs (actor, exploration, dynamics, reward, reset, transition
  * write) followed by updates_per_step updates once the buffer allows sampling, plus the

@@ -127,6 +127,7 @@ _SIGS = {
     "ac_info_get": (C.c_int, [P, C.POINTER(AcInfo)]),
     "ac_set_counters": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64]),
     "ac_update": (C.c_int, [P, P, C.c_int32, P]),
+    "ac_update_static": (C.c_int, [P, P, C.c_int32, P]),
     "ac_train": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int32, P]),
     "ac_sync": (C.c_int, [P]),
     "ac_save": (C.c_int, [P, P, C.c_char_p]),
@@ -398,6 +399,11 @@ def ac_set_counters(a, t_actor, t_critic, updates):
 
 def ac_update(a, env, n_updates, stream=None):
     _chk(_lib.ac_update(a, env, n_updates, _stream(stream)))
+
+
+def ac_update_static(a, env, n_updates, stream=None):
+    """ac_update without any device allocation (library-owned static scratch)."""
+    _chk(_lib.ac_update_static(a, env, n_updates, _stream(stream)))
 
 
 def ac_train(runs, envs, steps_per_run, persistent=1, stream=None):

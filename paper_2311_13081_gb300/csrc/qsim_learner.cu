@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <fstream>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -974,6 +975,109 @@ extern "C" qsim_status ac_update(ac_handle* a, qsim_handle* env, int32_t n_updat
     std::vector<qsim_handle*> E{env};
     const int nS = pick_cluster(a, 1);
     return launch_train(A, E, n_updates, 0, nS, (cudaStream_t)stream, nullptr, 1);
+}
+
+// ------------------------------------------------- allocation-free learner update
+// Scratch for ac_update_static(): a library-owned array in every device's global memory
+// (held from library load until process exit), plus room for the run descriptor.
+// Host code must not pass the symbol itself to a kernel (in host code it names a host-side
+// stand-in); the device address comes from cudaGetSymbolAddress, looked up once per device.
+static __device__ __align__(256) float g_static_scratch[QSIM_STATIC_SCRATCH_BYTES / sizeof(float)];
+static __device__ __align__(256) unsigned char g_static_desc[QSIM_STATIC_DESC_BYTES];
+
+namespace {
+struct StaticSlot {
+    float* scratch = nullptr;
+    unsigned char* desc = nullptr;
+    bool ready = false;
+};
+constexpr int kMaxDevices = 64;
+StaticSlot g_static_slots[kMaxDevices];
+std::mutex g_static_mutex;
+
+// Resolves the device addresses of the static arrays for the current device (first call
+// on each device only).
+qsim_status static_slot(int device, StaticSlot** out) {
+    if (device < 0 || device >= kMaxDevices) return fail(QSIM_EINVAL, "ac_update_static: device id %d", device);
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    StaticSlot& s = g_static_slots[device];
+    if (!s.ready) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "ac_update_static: cudaGetSymbolAddress(scratch)");
+        s.scratch = static_cast<float*>(p);
+        e = cudaGetSymbolAddress(&p, g_static_desc);
+        if (e != cudaSuccess) return cuda_fail(e, "ac_update_static: cudaGetSymbolAddress(desc)");
+        s.desc = static_cast<unsigned char*>(p);
+        s.ready = true;
+    }
+    *out = &s;
+    return QSIM_OK;
+}
+}  // namespace
+
+extern "C" qsim_status ac_update_static(ac_handle* a, qsim_handle* env, int32_t n_updates,
+                                        void* stream) {
+    qsim_status st = validate_pair(a, env);
+    if (st != QSIM_OK) return st;
+    if (n_updates < 0) return fail(QSIM_EINVAL, "ac_update_static: n_updates < 0");
+    if (n_updates == 0) return QSIM_OK;
+    const int64_t lost = env->size == env->capacity ? env->cfg.n_hist : 0;
+    if (env->size - 1 - lost < 1)
+        return fail(QSIM_ESTATE, "ac_update_static: replay buffer too small to sample (size=%lld)",
+                    (long long)env->size);
+    if ((uint64_t)(env->size - 1 - lost) * (uint64_t)env->n >= (1ull << 32))
+        return fail(QSIM_EINVAL, "ac_update_static: replay buffer exceeds 2^32 transitions");
+    const int nS = pick_cluster(a, 1);
+    if (a->batch % nS) return fail(QSIM_EINVAL, "ac_update_static: batch %d not divisible by cluster %d", a->batch, nS);
+    const size_t stride = scratch_floats(a->batch / nS, a->hidden, a->obs_dim, a->critic_in,
+                                         a->n_actor, a->n_critic, env->n);
+    const size_t need = stride * sizeof(float) * (size_t)nS;
+    if (need > QSIM_STATIC_SCRATCH_BYTES)
+        return fail(QSIM_EINVAL,
+                    "ac_update_static: needs %zu bytes of scratch (batch %d, hidden %d, cluster %d), "
+                    "more than the static maximum of %d bytes; use ac_update",
+                    need, a->batch, a->hidden, nS, (int)QSIM_STATIC_SCRATCH_BYTES);
+    int device = 0;
+    QCHECK_CUDA(cudaGetDevice(&device));
+    StaticSlot* slot = nullptr;
+    st = static_slot(device, &slot);
+    if (st != QSIM_OK) return st;
+    struct Packed {
+        RunDesc run;
+        int order[1];
+        int off[2];
+    };
+    static_assert(sizeof(Packed) <= QSIM_STATIC_DESC_BYTES, "run descriptor exceeds its static area");
+    Packed pk;
+    memset(&pk, 0, sizeof(pk));
+    fill_desc(a, env, pk.run);
+    pk.order[0] = 0;
+    pk.off[0] = 0;
+    pk.off[1] = 1;
+    cudaStream_t cs = (cudaStream_t)stream;
+    Packed* d_pk = reinterpret_cast<Packed*>(slot->desc);
+    QCHECK_CUDA(cudaMemcpyAsync(d_pk, &pk, sizeof(pk), cudaMemcpyHostToDevice, cs));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(nS);
+    lc.blockDim = dim3(LT);
+    lc.dynamicSmemBytes = learner_smem();
+    lc.stream = cs;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (nS > 8) QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    QCHECK_CUDA(cudaLaunchKernelEx(&lc, k_train, &d_pk->run, (const int*)d_pk->order,
+                                   (const int*)d_pk->off, (int)n_updates, 0, slot->scratch,
+                                   stride, nS));
+    QCHECK_CUDA(cudaMemcpyAsync(&pk, d_pk, sizeof(pk), cudaMemcpyDeviceToHost, cs));
+    QCHECK_CUDA(cudaStreamSynchronize(cs));
+    read_back(a, env, pk.run);
+    return QSIM_OK;
 }
 
 extern "C" qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
