@@ -315,16 +315,23 @@ qsim_status ac_save(const ac_handle* a, const qsim_handle* env, const char* path
 qsim_status ac_load(ac_handle* a, qsim_handle* env, const char* path);
 
 /* ------------------------------------------------------------------ differentiation
- * Reverse-mode gradient through an H-step RK4 rollout of n envs without resets:
+ * Reverse-mode gradient through an H-step RK4 rollout of n envs without resets or
+ * disturbances (differentiable form of the Sec. IV dynamics):
  *   loss_e = sum_{t=1..H} [w_p |p_t|^2 + w_q (1 - q_w,t^2) + w_v |v_t|^2]
  *            + w_a sum_{t=0..H-1} |a_t|^2
- * mode 0 (open loop): actions [H][4][ld] given; returns d loss_e / d a_t in g_actions.
- * mode 1 (closed loop): a_t = actor(o_a,t) with o_a built from the state and the
- * history of the rollout's own actions (zeros before t = 0, no noise); returns
- * d sum_e loss_e / d actor in g_actor.
- * Both modes return d loss_e / d (m, Jx, Jy, Jz) in g_params [4][ld] and loss [ld].
- * States are checkpointed every `ckpt` steps and recomputed inside each segment.
- * s0 [17][ld], params [8][ld]; workspace: device scratch of qsim_vjp_workspace() bytes. */
+ * mode 0 (open loop): actions [H][4][ld] given (normalised, mapped linearly to RPM and
+ * clipped to the RPM range); g_actions [H][4][ld] receives d L / d a_t.
+ * mode 1 (closed loop): a_t = actor(o_a,t), o_a built from the state and the rollout's
+ * own previous n_hist actions (zeros before t = 0, no noise); g_actor [P_actor] receives
+ * d L / d actor (summed over envs; overwritten).
+ * L = sum_e seed_e loss_e with seed [ld] (device; NULL = all ones), so a caller can pass
+ * the upstream gradient of each env's loss.  Both modes write loss [ld] (unweighted),
+ * d L / d (m, Jx, Jy, Jz) into g_params [4][ld], and the actions used into actions_out
+ * [H][4][ld] (either may be NULL).  If g_actions, g_actor and g_params are all NULL only
+ * the forward pass runs.
+ * States are checkpointed every `ckpt` steps and recomputed inside each segment, so the
+ * workspace (device, 16-byte aligned, qsim_vjp_workspace() bytes, caller-owned) grows with
+ * H/ckpt + ckpt, not H.  s0 [17][ld], params [8][ld] (m Jx Jy Jz kf km T_m -). */
 typedef struct qsim_vjp_desc {
     int32_t n, ld, H, ckpt, mode, n_hist, hidden, reserved0;
     float w_p, w_q, w_v, w_a;
@@ -334,8 +341,8 @@ typedef struct qsim_vjp_desc {
 size_t qsim_vjp_workspace(const qsim_vjp_desc* d);
 qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_params* veh, const float* s0,
                              const float* params, const float* actions, const float* actor,
-                             float* loss, float* g_actions, float* g_actor, float* g_params,
-                             float* actions_out, void* workspace, void* stream);
+                             const float* seed, float* loss, float* g_actions, float* g_actor,
+                             float* g_params, float* actions_out, void* workspace, void* stream);
 
 #ifdef __cplusplus
 }

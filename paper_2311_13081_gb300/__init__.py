@@ -134,7 +134,7 @@ _SIGS = {
     "ac_load": (C.c_int, [P, P, C.c_char_p]),
     "qsim_vjp_workspace": (C.c_size_t, [C.POINTER(QsimVjpDesc)]),
     "qsim_rollout_vjp": (C.c_int, [C.POINTER(QsimVjpDesc), C.POINTER(QsimParams), P, P, P, P,
-                                   P, P, P, P, P, P, P]),
+                                   P, P, P, P, P, P, P, P]),
 }
 
 
@@ -431,13 +431,13 @@ def qsim_vjp_workspace(desc: QsimVjpDesc) -> int:
     return int(_lib.qsim_vjp_workspace(C.byref(desc)))
 
 
-def qsim_rollout_vjp(desc: QsimVjpDesc, veh: QsimParams, s0, params, actions, actor, loss,
-                     g_actions, g_actor, g_params, actions_out, workspace, stream=None):
+def qsim_rollout_vjp(desc: QsimVjpDesc, veh: QsimParams, s0, params, actions, actor, seed,
+                     loss, g_actions, g_actor, g_params, actions_out, workspace, stream=None):
     load()
     _chk(_lib.qsim_rollout_vjp(C.byref(desc), C.byref(veh), _ptr(s0), _ptr(params),
-                               _ptr(actions), _ptr(actor), _ptr(loss), _ptr(g_actions),
-                               _ptr(g_actor), _ptr(g_params), _ptr(actions_out),
-                               _ptr(workspace), _stream(stream)))
+                               _ptr(actions), _ptr(actor), _ptr(seed), _ptr(loss),
+                               _ptr(g_actions), _ptr(g_actor), _ptr(g_params),
+                               _ptr(actions_out), _ptr(workspace), _stream(stream)))
 
 
 def param_count(inp: int, hid: int, out: int) -> int:

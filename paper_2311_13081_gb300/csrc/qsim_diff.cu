@@ -1,20 +1,601 @@
-// qsim_diff.cu -- reverse-mode gradients through the RK4 simulator (placeholder entry
-// points; the adjoint kernels are added in the differentiation unit).
+// qsim_diff.cu -- reverse-mode gradients through an H-step RK4 rollout (differentiable
+// simulation of the Sec. IV dynamics, with or without the actor in the loop).
+//
+// Schedule (thread per env, state in registers):
+//   forward   : integrate H steps, store the state every `ckpt` steps and the actions,
+//               accumulate the loss.
+//   backward  : for each segment, last to first: recompute the segment's states from its
+//               checkpoint, then sweep it in reverse -- vector-Jacobian product of RK4
+//               (four stage derivatives recomputed, quaternion renormalisation included),
+//               of the action -> RPM map, and in closed loop of the actor (per-thread
+//               backprop with weights in shared memory; history inputs pass their adjoint
+//               to earlier actions).  The adjoint state and parameter gradients carry over
+//               between segments in the workspace.
+//   weights   : closed loop only -- the per-(step, env) activations and deltas of a
+//               segment are reduced into the actor gradient by CTA-wide GEMMs over env
+//               chunks, then summed over chunks in a fixed order (deterministic).
+// Memory: O(H/ckpt + ckpt) states per env instead of O(H).
+#include <algorithm>
+#include <cstring>
+
+#include "qsim_gemm.cuh"
 #include "qsim_internal.h"
+
+namespace qsim {
+
+struct VjpArgs {
+    Vehicle V;
+    int n, ld, H, ckpt, mode, nh, hid, DA, PA, nseg, nchunk, chunk;
+    float w_p, w_q, w_v, w_a, dt;
+    int renorm;
+    const float *s0, *prm, *actions, *actor, *seed;
+    float *loss, *g_actions, *g_actor, *g_params, *actions_out;
+    // workspace
+    float *ck, *A, *la, *segs, *lam, *gp, *rec, *fo, *part;
+};
+
+constexpr int VT = 128;  // threads per CTA of the per-env kernels
+
+__device__ __forceinline__ void load_vehicle_prm(const VjpArgs& a, int e, Prm& P) {
+    const float* p = a.prm;
+    const int ld = a.ld;
+    P = make_prm(p[e], p[ld + e], p[2 * ld + e], p[3 * ld + e], p[4 * ld + e], p[5 * ld + e],
+                 p[6 * ld + e]);
+}
+
+__device__ __forceinline__ float state_loss(const VjpArgs& a, const float* s) {
+    return a.w_p * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]) + a.w_q * (1.0f - s[3] * s[3]) +
+           a.w_v * (s[7] * s[7] + s[8] * s[8] + s[9] * s[9]);
+}
+
+__device__ __forceinline__ void state_loss_grad(const VjpArgs& a, const float* s, float* g) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] += 2.0f * a.w_p * s[k];
+    g[3] += -2.0f * a.w_q * s[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[7 + k] += 2.0f * a.w_v * s[7 + k];
+}
+
+// d(derivative)^T lam, added into gs (state), gu (unclipped set-point) and gp (m, Jx, Jy,
+// Jz, kf, km, T_m).  No disturbance in the differentiable rollout.
+__device__ __forceinline__ void deriv_vjp(const Vehicle& V, const float* s, const float* u,
+                                          const Prm& P, const float* lam, float* gs, float* gu,
+                                          float* gp) {
+    const float qw = s[3], qx = s[4], qy = s[5], qz = s[6];
+    const float wx = s[10], wy = s[11], wz = s[12];
+    float f[4], F = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) { f[i] = P.kf * s[13 + i] * s[13 + i]; F += f[i]; }
+    const float r02 = 2.0f * (qx * qz + qw * qy);
+    const float r12 = 2.0f * (qy * qz - qw * qx);
+    const float r22 = 1.0f - 2.0f * (qx * qx + qy * qy);
+    // p' = v
+    gs[7] += lam[0]; gs[8] += lam[1]; gs[9] += lam[2];
+    // v' = R e_z F / m - g e_z
+    const float lv0 = lam[7], lv1 = lam[8], lv2 = lam[9];
+    const float gF = (lv0 * r02 + lv1 * r12 + lv2 * r22) * P.im;
+    gp[0] += -(lv0 * r02 + lv1 * r12 + lv2 * r22) * F * P.im * P.im;
+    const float G2 = lv0 * F * P.im, G5 = lv1 * F * P.im, G8 = lv2 * F * P.im;
+    gs[3] += 2.0f * (qy * G2 - qx * G5);
+    gs[4] += 2.0f * (qz * G2 - qw * G5 - 2.0f * qx * G8);
+    gs[5] += 2.0f * (qw * G2 + qz * G5 - 2.0f * qy * G8);
+    gs[6] += 2.0f * (qx * G2 + qy * G5);
+    // q' = 1/2 q (x) (0, w)
+    const float l0 = lam[3], l1 = lam[4], l2 = lam[5], l3 = lam[6];
+    gs[3] += 0.5f * (l1 * wx + l2 * wy + l3 * wz);
+    gs[4] += 0.5f * (-l0 * wx - l2 * wz + l3 * wy);
+    gs[5] += 0.5f * (-l0 * wy + l1 * wz - l3 * wx);
+    gs[6] += 0.5f * (-l0 * wz - l1 * wy + l2 * wx);
+    gs[10] += 0.5f * (-qx * l0 + qw * l1 + qz * l2 - qy * l3);
+    gs[11] += 0.5f * (-qy * l0 - qz * l1 + qw * l2 + qx * l3);
+    gs[12] += 0.5f * (-qz * l0 + qy * l1 - qx * l2 + qw * l3);
+    // w' = J^-1 (tau - w x J w)
+    const float mx = lam[10] * P.iJx, my = lam[11] * P.iJy, mz = lam[12] * P.iJz;
+    float tx = 0.0f, ty = 0.0f, tz = 0.0f, sdf = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        tx = fmaf(V.ry[i], f[i], tx);
+        ty = fmaf(-V.rx[i], f[i], ty);
+        sdf = fmaf(V.dir[i], f[i], sdf);
+    }
+    tz = P.km * sdf;
+    const float wdx = (tx - (P.Jz - P.Jy) * wy * wz) * P.iJx;
+    const float wdy = (ty - (P.Jx - P.Jz) * wz * wx) * P.iJy;
+    const float wdz = (tz - (P.Jy - P.Jx) * wx * wy) * P.iJz;
+    gs[10] += -my * (P.Jx - P.Jz) * wz - mz * (P.Jy - P.Jx) * wy;
+    gs[11] += -mx * (P.Jz - P.Jy) * wz - mz * (P.Jy - P.Jx) * wx;
+    gs[12] += -mx * (P.Jz - P.Jy) * wy - my * (P.Jx - P.Jz) * wx;
+    gp[1] += -mx * wdx - my * wz * wx + mz * wx * wy;
+    gp[2] += -my * wdy + mx * wy * wz - mz * wx * wy;
+    gp[3] += -mz * wdz - mx * wy * wz + my * wz * wx;
+    // rotor forces
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float gf = gF + mx * V.ry[i] - my * V.rx[i] + mz * V.dir[i] * P.km;
+        gs[13 + i] += gf * 2.0f * P.kf * s[13 + i];
+        gp[4] += gf * s[13 + i] * s[13 + i];
+    }
+    gp[5] += mz * sdf;
+    // motor lag
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float uc = clampf(u[i], V.rpm_min, V.rpm_max);
+        const float lm = lam[13 + i];
+        gs[13 + i] += -lm * P.itm;
+        if (u[i] > V.rpm_min && u[i] < V.rpm_max) gu[i] += lm * P.itm;
+        gp[6] += -lm * (uc - s[13 + i]) * P.itm * P.itm;
+    }
+}
+
+// Reverse of one RK4 step: lam_out = dL/ds'; gs receives dL/ds (overwritten), gu and gp
+// are accumulated.
+__device__ __forceinline__ void rk4_vjp(const Vehicle& V, float dt, int renorm, const float* s,
+                                        const float* u, const Prm& P, const float* lam_out,
+                                        float* gs, float* gu, float* gp) {
+    float uc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) uc[i] = clampf(u[i], V.rpm_min, V.rpm_max);
+    const float d0[6] = {0, 0, 0, 0, 0, 0};
+    float k1[NS], k2[NS], k3[NS], y2[NS], y3[NS], y4[NS];
+    deriv(V, s, uc, P, d0, k1);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) y2[i] = fmaf(0.5f * dt, k1[i], s[i]);
+    deriv(V, y2, uc, P, d0, k2);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) y3[i] = fmaf(0.5f * dt, k2[i], s[i]);
+    deriv(V, y3, uc, P, d0, k3);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) y4[i] = fmaf(dt, k3[i], s[i]);
+    float lam[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) lam[i] = lam_out[i];
+    if (renorm) {
+        float k4[NS];
+        deriv(V, y4, uc, P, d0, k4);
+        float pre[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            pre[i] = s[3 + i] + dt * (1.0f / 6.0f) * (k1[3 + i] + 2.0f * k2[3 + i] + 2.0f * k3[3 + i] + k4[3 + i]);
+        const float inv = rsqrtf(pre[0] * pre[0] + pre[1] * pre[1] + pre[2] * pre[2] + pre[3] * pre[3]);
+        float dot = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dot += pre[i] * inv * lam_out[3 + i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) lam[3 + i] = (lam_out[3 + i] - pre[i] * inv * dot) * inv;
+    }
+    float lk[NS], ly[NS], lk2[NS], lk3[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        gs[i] = lam[i];
+        lk[i] = dt * (1.0f / 6.0f) * lam[i];   // k4 and k1 weight
+        lk2[i] = dt * (1.0f / 3.0f) * lam[i];  // k2 weight
+        lk3[i] = lk2[i];                       // k3 weight
+        ly[i] = 0.0f;
+    }
+    deriv_vjp(V, y4, u, P, lk, ly, gu, gp);       // k4 = f(y4), y4 = s + dt k3
+#pragma unroll
+    for (int i = 0; i < NS; ++i) { gs[i] += ly[i]; lk3[i] = fmaf(dt, ly[i], lk3[i]); ly[i] = 0.0f; }
+    deriv_vjp(V, y3, u, P, lk3, ly, gu, gp);      // k3 = f(y3), y3 = s + dt/2 k2
+#pragma unroll
+    for (int i = 0; i < NS; ++i) { gs[i] += ly[i]; lk2[i] = fmaf(0.5f * dt, ly[i], lk2[i]); ly[i] = 0.0f; }
+    deriv_vjp(V, y2, u, P, lk2, ly, gu, gp);      // k2 = f(y2), y2 = s + dt/2 k1
+#pragma unroll
+    for (int i = 0; i < NS; ++i) { gs[i] += ly[i]; lk[i] = fmaf(0.5f * dt, ly[i], lk[i]); ly[i] = 0.0f; }
+    deriv_vjp(V, s, u, P, lk, ly, gu, gp);        // k1 = f(s)
+#pragma unroll
+    for (int i = 0; i < NS; ++i) gs[i] += ly[i];
+}
+
+// Reverse of the observation's state entries {p, R(q) row-major, v, omega}.
+__device__ __forceinline__ void obs_vjp(const float* s, const float* go, float* gs) {
+    const float qw = s[3], qx = s[4], qy = s[5], qz = s[6];
+    const float* G = go + 3;
+    gs[0] += go[0]; gs[1] += go[1]; gs[2] += go[2];
+    gs[3] += 2.0f * (-qz * G[1] + qy * G[2] + qz * G[3] - qx * G[5] - qy * G[6] + qx * G[7]);
+    gs[4] += 2.0f * (qy * G[1] + qz * G[2] + qy * G[3] - 2.0f * qx * G[4] - qw * G[5] + qz * G[6] +
+                     qw * G[7] - 2.0f * qx * G[8]);
+    gs[5] += 2.0f * (-2.0f * qy * G[0] + qx * G[1] + qw * G[2] + qx * G[3] + qz * G[5] - qw * G[6] +
+                     qz * G[7] - 2.0f * qy * G[8]);
+    gs[6] += 2.0f * (-2.0f * qz * G[0] - qw * G[1] + qx * G[2] + qw * G[3] - 2.0f * qz * G[4] +
+                     qy * G[5] + qx * G[6] + qy * G[7]);
+    gs[7] += go[12]; gs[8] += go[13]; gs[9] += go[14];
+    gs[10] += go[15]; gs[11] += go[16]; gs[12] += go[17];
+}
+
+// Actor observation of env e at step t into O [DA][ld] column e: state part from s, then
+// the rollout's own previous actions (zeros before t = 0).
+__device__ __forceinline__ void build_obs(const VjpArgs& a, int e, int t, const float* s, float* O) {
+    const int ld = a.ld;
+    float o[18];
+    obs_state(s, o);
+#pragma unroll
+    for (int k = 0; k < 18; ++k) O[k * ld] = o[k];
+    for (int i = 1; i <= a.nh; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            O[(18 + 4 * (i - 1) + c) * ld] = (t - i >= 0) ? a.A[((size_t)(t - i) * 4 + c) * ld + e] : 0.0f;
+}
+
+// Per-thread actor forward with weights in shared memory; vectors live in column e of
+// field-major global arrays (coalesced across the warp, L1-resident).
+__device__ __forceinline__ void actor_fwd_thread(const float* sW, int DA, int H, const float* O,
+                                                 float* H1, float* H2, int ld, float* mu) {
+    const float* W1 = sW;
+    const float* b1 = W1 + H * DA;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + 4 * H;
+    for (int j = 0; j < H; ++j) {
+        float acc = b1[j];
+        for (int k = 0; k < DA; ++k) acc = fmaf(W1[j * DA + k], O[k * ld], acc);
+        H1[j * ld] = fmaxf(acc, 0.0f);
+    }
+    for (int j = 0; j < H; ++j) {
+        float acc = b2[j];
+        for (int k = 0; k < H; ++k) acc = fmaf(W2[j * H + k], H1[k * ld], acc);
+        H2[j * ld] = fmaxf(acc, 0.0f);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float acc = b3[j];
+        for (int k = 0; k < H; ++k) acc = fmaf(W3[j * H + k], H2[k * ld], acc);
+        mu[j] = tanhf(acc);
+    }
+}
+
+__global__ void __launch_bounds__(VT) k_vjp_forward(VjpArgs a) {
+    extern __shared__ __align__(16) float sW[];
+    if (a.mode == 1) {
+        for (int i = threadIdx.x; i < a.PA; i += VT) sW[i] = a.actor[i];
+        __syncthreads();
+    }
+    const int e = blockIdx.x * VT + threadIdx.x;
+    if (e >= a.n) return;
+    const int ld = a.ld;
+    float s[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) s[i] = a.s0[i * ld + e];
+    Prm P;
+    load_vehicle_prm(a, e, P);
+    const float d0[6] = {0, 0, 0, 0, 0, 0};
+    const float half = 0.5f * (a.V.rpm_max - a.V.rpm_min);
+    float loss = 0.0f;
+    for (int t = 0; t < a.H; ++t) {
+        if (t % a.ckpt == 0) {
+            float* c = a.ck + (size_t)(t / a.ckpt) * NS * ld + e;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) c[i * ld] = s[i];
+        }
+        float act[4];
+        if (a.mode == 0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) act[c] = a.actions[((size_t)t * 4 + c) * ld + e];
+        } else {
+            float* O = a.fo + e;
+            build_obs(a, e, t, s, O);
+            actor_fwd_thread(sW, a.DA, a.hid, O, O + (size_t)a.DA * ld, O + (size_t)(a.DA + a.hid) * ld,
+                             ld, act);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            a.A[((size_t)t * 4 + c) * ld + e] = act[c];
+            if (a.actions_out) a.actions_out[((size_t)t * 4 + c) * ld + e] = act[c];
+        }
+        float u[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) u[c] = fmaf(act[c] + 1.0f, half, a.V.rpm_min);
+        rk4(a.V, a.dt, a.renorm, s, u, P, d0);
+        loss += state_loss(a, s) + a.w_a * (act[0] * act[0] + act[1] * act[1] + act[2] * act[2] + act[3] * act[3]);
+    }
+    if (a.loss) a.loss[e] = loss;
+}
+
+// Reverse sweep over segment g.
+__global__ void __launch_bounds__(VT) k_vjp_backward(VjpArgs a, int g) {
+    extern __shared__ __align__(16) float sW[];
+    if (a.mode == 1) {
+        for (int i = threadIdx.x; i < a.PA; i += VT) sW[i] = a.actor[i];
+        __syncthreads();
+    }
+    const int e = blockIdx.x * VT + threadIdx.x;
+    if (e >= a.n) return;
+    const int ld = a.ld, DA = a.DA, H = a.hid;
+    const int t0 = g * a.ckpt, t1 = min(a.H, t0 + a.ckpt);
+    const bool last = (t1 == a.H);
+    const float seed = a.seed ? a.seed[e] : 1.0f;
+    Prm P;
+    load_vehicle_prm(a, e, P);
+    const float d0[6] = {0, 0, 0, 0, 0, 0};
+    const float half = 0.5f * (a.V.rpm_max - a.V.rpm_min);
+    // recompute the segment's states from its checkpoint
+    float s[NS];
+    {
+        const float* c = a.ck + (size_t)g * NS * ld + e;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) s[i] = c[i * ld];
+    }
+    float lam[NS], gp[7];
+    for (int t = t0; t < t1; ++t) {
+        float* ss = a.segs + (size_t)(t - t0) * NS * ld + e;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) ss[i * ld] = s[i];
+        float u[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) u[c] = fmaf(a.A[((size_t)t * 4 + c) * ld + e] + 1.0f, half, a.V.rpm_min);
+        rk4(a.V, a.dt, a.renorm, s, u, P, d0);
+    }
+    if (last) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) lam[i] = 0.0f;
+        state_loss_grad(a, s, lam);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) lam[i] *= seed;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) gp[i] = 0.0f;
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) lam[i] = a.lam[i * ld + e];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) gp[i] = a.gp[i * ld + e];
+    }
+    const size_t NR = (size_t)DA + 4 * H + 4;  // O, H1, H2, dZ1, dZ2, dZ3 per (step, env)
+    for (int t = t1 - 1; t >= t0; --t) {
+        float st[NS];
+        const float* ss = a.segs + (size_t)(t - t0) * NS * ld + e;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) st[i] = ss[i * ld];
+        float act[4], u[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            act[c] = a.A[((size_t)t * 4 + c) * ld + e];
+            u[c] = fmaf(act[c] + 1.0f, half, a.V.rpm_min);
+        }
+        float gs[NS], gu[4] = {0, 0, 0, 0};
+        rk4_vjp(a.V, a.dt, a.renorm, st, u, P, lam, gs, gu, gp);
+        float ga[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ga[c] = gu[c] * half + seed * 2.0f * a.w_a * act[c];
+        if (a.mode == 0) {
+            if (a.g_actions)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) a.g_actions[((size_t)t * 4 + c) * ld + e] = ga[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ga[c] += a.la[((size_t)t * 4 + c) * ld + e];
+            float* R = a.rec + (size_t)(t - t0) * NR * ld + e;
+            float* O = R;
+            float* H1 = R + (size_t)DA * ld;
+            float* H2 = H1 + (size_t)H * ld;
+            float* dZ1 = H2 + (size_t)H * ld;
+            float* dZ2 = dZ1 + (size_t)H * ld;
+            float* dZ3 = dZ2 + (size_t)H * ld;
+            build_obs(a, e, t, st, O);
+            float mu[4];
+            actor_fwd_thread(sW, DA, H, O, H1, H2, ld, mu);
+            const float* W1 = sW;
+            const float* W2 = W1 + H * DA + H;
+            const float* W3 = W2 + H * H + H;
+            float z3[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                z3[c] = ga[c] * (1.0f - mu[c] * mu[c]);
+                dZ3[c * ld] = z3[c];
+            }
+            for (int k = 0; k < H; ++k) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc = fmaf(W3[c * H + k], z3[c], acc);
+                dZ2[k * ld] = H2[k * ld] > 0.0f ? acc : 0.0f;
+            }
+            for (int k = 0; k < H; ++k) {
+                float acc = 0.0f;
+                for (int j = 0; j < H; ++j) acc = fmaf(W2[j * H + k], dZ2[j * ld], acc);
+                dZ1[k * ld] = H1[k * ld] > 0.0f ? acc : 0.0f;
+            }
+            float go[18];
+            for (int k = 0; k < 18; ++k) {
+                float acc = 0.0f;
+                for (int j = 0; j < H; ++j) acc = fmaf(W1[j * DA + k], dZ1[j * ld], acc);
+                go[k] = acc;
+            }
+            obs_vjp(st, go, gs);
+            for (int i = 1; i <= a.nh && t - i >= 0; ++i)
+                for (int c = 0; c < 4; ++c) {
+                    const int k = 18 + 4 * (i - 1) + c;
+                    float acc = 0.0f;
+                    for (int j = 0; j < H; ++j) acc = fmaf(W1[j * DA + k], dZ1[j * ld], acc);
+                    a.la[((size_t)(t - i) * 4 + c) * ld + e] += acc;
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < NS; ++i) lam[i] = gs[i];
+        if (t >= 1) {
+            float lg[NS];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) lg[i] = 0.0f;
+            state_loss_grad(a, st, lg);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) lam[i] = fmaf(seed, lg[i], lam[i]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) a.lam[i * ld + e] = lam[i];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) a.gp[i * ld + e] = gp[i];
+    if (g == 0 && a.g_params)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a.g_params[i * ld + e] = gp[i];
+}
+
+// Partial actor-weight gradient of segment g over env chunk blockIdx.x (closed loop).
+__global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g) {
+    extern __shared__ __align__(16) float sm[];
+    const int ld = a.ld, DA = a.DA, H = a.hid;
+    const int t0 = g * a.ckpt, t1 = min(a.H, t0 + a.ckpt);
+    const int e0 = blockIdx.x * a.chunk;
+    const int ne = min(a.chunk, a.n - e0);
+    if (ne <= 0) return;
+    const size_t NR = (size_t)DA + 4 * H + 4;
+    float* P = a.part + (size_t)blockIdx.x * a.PA;
+    float* gW1 = P;
+    float* gb1 = gW1 + H * DA;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + H * H;
+    float* gW3 = gb2 + H;
+    float* gb3 = gW3 + 4 * H;
+    for (int t = t0; t < t1; ++t) {
+        const float* R = a.rec + (size_t)(t - t0) * NR * ld + e0;
+        const float* O = R;
+        const float* H1 = R + (size_t)DA * ld;
+        const float* H2 = H1 + (size_t)H * ld;
+        const float* dZ1 = H2 + (size_t)H * ld;
+        const float* dZ2 = dZ1 + (size_t)H * ld;
+        const float* dZ3 = dZ2 + (size_t)H * ld;
+        const bool first = (t == t0);
+        cta_gemm(H, DA, ne, Mat{dZ1, ld, 1}, Mat{O, 1, ld}, sm, [&](int m, int n, float v) {
+            float* p = gW1 + m * DA + n;
+            *p = first ? v : *p + v;
+        });
+        cta_gemm(H, H, ne, Mat{dZ2, ld, 1}, Mat{H1, 1, ld}, sm, [&](int m, int n, float v) {
+            float* p = gW2 + m * H + n;
+            *p = first ? v : *p + v;
+        });
+        cta_gemm(4, H, ne, Mat{dZ3, ld, 1}, Mat{H2, 1, ld}, sm, [&](int m, int n, float v) {
+            float* p = gW3 + m * H + n;
+            *p = first ? v : *p + v;
+        });
+        for (int j = threadIdx.x; j < 2 * H + 4; j += LT) {
+            const float* src = j < H ? dZ1 + (size_t)j * ld : (j < 2 * H ? dZ2 + (size_t)(j - H) * ld
+                                                                         : dZ3 + (size_t)(j - 2 * H) * ld);
+            float* dst = j < H ? gb1 + j : (j < 2 * H ? gb2 + (j - H) : gb3 + (j - 2 * H));
+            float s = 0.0f;
+            for (int q = 0; q < ne; ++q) s += ldcg(src + q);
+            *dst = first ? s : *dst + s;
+        }
+        __syncthreads();
+    }
+}
+
+// g_actor += sum over chunks (fixed order).
+__global__ void k_vjp_wreduce(VjpArgs a) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.PA) return;
+    float s = 0.0f;
+    for (int c = 0; c < a.nchunk; ++c) s += a.part[(size_t)c * a.PA + p];
+    a.g_actor[p] += s;
+}
+
+static size_t align_up(size_t x) { return (x + 63) & ~(size_t)63; }
+
+struct WsLayout {
+    size_t ck, A, la, segs, lam, gp, rec, fo, part, total;
+};
+
+static WsLayout ws_layout(const qsim_vjp_desc& d, int DA, int PA, int nchunk) {
+    WsLayout w;
+    const size_t ld = d.ld, nseg = (d.H + d.ckpt - 1) / d.ckpt;
+    size_t off = 0;
+    auto take = [&](size_t floats) { size_t o = off; off += align_up(floats); return o; };
+    w.ck = take(nseg * NS * ld);
+    w.A = take((size_t)d.H * 4 * ld);
+    w.la = take(d.mode == 1 ? (size_t)d.H * 4 * ld : 0);
+    w.segs = take((size_t)d.ckpt * NS * ld);
+    w.lam = take(NS * ld);
+    w.gp = take(8 * ld);
+    const size_t NR = (size_t)DA + 4 * (size_t)d.hidden + 4;
+    w.rec = take(d.mode == 1 ? (size_t)d.ckpt * NR * ld : 0);
+    w.fo = take(d.mode == 1 ? ((size_t)DA + 2 * (size_t)d.hidden) * ld : 0);
+    w.part = take(d.mode == 1 ? (size_t)nchunk * PA : 0);
+    w.total = off;
+    return w;
+}
+
+static constexpr int kChunk = 64;
+
+}  // namespace qsim
 
 using namespace qsim;
 
+static qsim_status check_desc(const qsim_vjp_desc* d) {
+    if (!d) return fail(QSIM_EINVAL, "qsim_rollout_vjp: null descriptor");
+    if (d->n < 1 || d->ld < d->n || (d->ld & 3) || d->H < 1 || d->ckpt < 1 || d->mode < 0 ||
+        d->mode > 1 || !(d->dt > 0.0f))
+        return fail(QSIM_EINVAL, "qsim_rollout_vjp: bad sizes (n=%d ld=%d H=%d ckpt=%d mode=%d)",
+                    d->n, d->ld, d->H, d->ckpt, d->mode);
+    if (d->mode == 1 && (d->n_hist < 0 || d->n_hist > HMAX || d->hidden < 4 || d->hidden > 128))
+        return fail(QSIM_EINVAL, "qsim_rollout_vjp: bad actor shape (n_hist=%d hidden=%d)", d->n_hist,
+                    d->hidden);
+    return QSIM_OK;
+}
+
 extern "C" size_t qsim_vjp_workspace(const qsim_vjp_desc* d) {
-    (void)d;
-    return 0;
+    if (check_desc(d) != QSIM_OK) return 0;
+    const int DA = 18 + 4 * d->n_hist;
+    const int PA = d->hidden * DA + d->hidden + d->hidden * d->hidden + d->hidden + 4 * d->hidden + 4;
+    const int nchunk = (d->n + kChunk - 1) / kChunk;
+    return ws_layout(*d, DA, PA, nchunk).total * sizeof(float);
 }
 
 extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_params* veh,
                                         const float* s0, const float* params, const float* actions,
-                                        const float* actor, float* loss, float* g_actions,
-                                        float* g_actor, float* g_params, float* actions_out,
-                                        void* workspace, void* stream) {
-    (void)d; (void)veh; (void)s0; (void)params; (void)actions; (void)actor; (void)loss;
-    (void)g_actions; (void)g_actor; (void)g_params; (void)actions_out; (void)workspace; (void)stream;
-    return fail(QSIM_ESTATE, "qsim_rollout_vjp: not available in this build");
+                                        const float* actor, const float* seed, float* loss,
+                                        float* g_actions, float* g_actor, float* g_params,
+                                        float* actions_out, void* workspace, void* stream) {
+    qsim_status st = check_desc(d);
+    if (st != QSIM_OK) return st;
+    if (!veh || !s0 || !params || !workspace) return fail(QSIM_EINVAL, "qsim_rollout_vjp: null pointer");
+    if (d->mode == 0 && !actions) return fail(QSIM_EINVAL, "qsim_rollout_vjp: open loop needs actions");
+    if (d->mode == 1 && !actor) return fail(QSIM_EINVAL, "qsim_rollout_vjp: closed loop needs actor");
+    if (!aligned16(s0) || !aligned16(params) || !aligned16(workspace))
+        return fail(QSIM_EINVAL, "qsim_rollout_vjp: pointers must be 16-byte aligned");
+    VjpArgs a;
+    memset(&a, 0, sizeof(a));
+    a.V = make_vehicle(*veh);
+    a.n = d->n; a.ld = d->ld; a.H = d->H; a.ckpt = d->ckpt; a.mode = d->mode;
+    a.nh = d->mode == 1 ? d->n_hist : 0;
+    a.hid = d->hidden;
+    a.DA = 18 + 4 * a.nh;
+    a.PA = a.hid * a.DA + a.hid + a.hid * a.hid + a.hid + 4 * a.hid + 4;
+    a.nseg = (d->H + d->ckpt - 1) / d->ckpt;
+    a.chunk = kChunk;
+    a.nchunk = (d->n + kChunk - 1) / kChunk;
+    a.w_p = d->w_p; a.w_q = d->w_q; a.w_v = d->w_v; a.w_a = d->w_a; a.dt = d->dt;
+    a.renorm = d->renorm;
+    a.s0 = s0; a.prm = params; a.actions = actions; a.actor = actor; a.seed = seed;
+    a.loss = loss; a.g_actions = g_actions; a.g_actor = g_actor; a.g_params = g_params;
+    a.actions_out = actions_out;
+    qsim_vjp_desc dd = *d;
+    dd.n_hist = a.nh;
+    const WsLayout w = ws_layout(dd, a.DA, a.PA, a.nchunk);
+    float* base = static_cast<float*>(workspace);
+    a.ck = base + w.ck; a.A = base + w.A; a.la = base + w.la; a.segs = base + w.segs;
+    a.lam = base + w.lam; a.gp = base + w.gp; a.rec = base + w.rec; a.fo = base + w.fo;
+    a.part = base + w.part;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const size_t smem = d->mode == 1 ? sizeof(float) * (size_t)a.PA : 0;
+    if (smem > 48 * 1024) {
+        QCHECK_CUDA(cudaFuncSetAttribute(k_vjp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        QCHECK_CUDA(cudaFuncSetAttribute(k_vjp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    const int grid = (d->n + VT - 1) / VT;
+    k_vjp_forward<<<grid, VT, smem, cs>>>(a);
+    QCHECK_LAUNCH("k_vjp_forward");
+    const bool want_grad = g_actions || g_actor || g_params;
+    if (!want_grad) return QSIM_OK;
+    if (d->mode == 1) {
+        QCHECK_CUDA(cudaMemsetAsync(a.la, 0, sizeof(float) * (size_t)d->H * 4 * d->ld, cs));
+        if (g_actor) QCHECK_CUDA(cudaMemsetAsync(g_actor, 0, sizeof(float) * (size_t)a.PA, cs));
+    }
+    for (int g = a.nseg - 1; g >= 0; --g) {
+        k_vjp_backward<<<grid, VT, smem, cs>>>(a, g);
+        QCHECK_LAUNCH("k_vjp_backward");
+        if (d->mode == 1 && g_actor) {
+            k_vjp_wgrad<<<a.nchunk, LT, sizeof(float) * GEMM_SMEM, cs>>>(a, g);
+            QCHECK_LAUNCH("k_vjp_wgrad");
+            k_vjp_wreduce<<<(a.PA + 255) / 256, 256, 0, cs>>>(a);
+            QCHECK_LAUNCH("k_vjp_wreduce");
+        }
+    }
+    return QSIM_OK;
 }
