@@ -210,9 +210,17 @@ qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t hidden, int
  * effect. */
 int32_t qsim_rollout_tune(qsim_handle* h, int32_t warps_per_block);
 
-/* Autotuner: times every warps-per-block variant of the rollout kernel that fits on this
- * device with n_steps-step rollouts (CUDA events on `stream`; these are real env steps
- * that advance the env set), keeps the fastest for this handle and returns its warps
+/* Rollout schedule: split the envs into `parts` partitions (1..4) run on internal streams,
+ * each advancing in chunks of `chunk` steps (0 = whole call), joined on the caller's stream
+ * at the end of every qsim_rollout call.  Partitions keep the SMs busy while another
+ * partition's last blocks finish.  parts 0 = automatic (2 partitions in 100-step chunks
+ * when the env set needs more than one wave of resident warps).  Returns the parts in
+ * effect; a negative argument leaves that setting unchanged. */
+int32_t qsim_rollout_schedule(qsim_handle* h, int32_t parts, int32_t chunk);
+
+/* Autotuner: times every (warps-per-block, schedule) variant of the rollout kernel that fits
+ * on this device with n_steps-step rollouts (CUDA events on `stream`; these are real env
+ * steps that advance the env set), keeps the fastest for this handle and returns its warps
  * per block (negative qsim_status on error).  Synchronises the stream. */
 int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int32_t hidden,
                               int32_t n_steps, void* stream);

@@ -118,6 +118,7 @@ _SIGS = {
     "qsim_rollout": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_float, P]),
     "qsim_rollout_tune": (C.c_int32, [P, C.c_int32]),
     "qsim_rollout_autotune": (C.c_int32, [P, P, C.c_int32, C.c_int32, P]),
+    "qsim_rollout_schedule": (C.c_int32, [P, C.c_int32, C.c_int32]),
     "qsim_ffma_probe": (C.c_int, [C.c_int32, C.c_int32, P, P]),
     "qsim_recalc_rewards": (C.c_int, [P, P]),
     "qsim_set_reward": (C.c_int, [P, P, C.c_float, P]),
@@ -344,6 +345,10 @@ def qsim_rollout_autotune(h, actor, hidden, n_steps, stream=None) -> int:
     if r < 0:
         _chk(r)
     return int(r)
+
+
+def qsim_rollout_schedule(h, parts=-1, chunk=-1) -> int:
+    return int(_lib.qsim_rollout_schedule(h, parts, chunk))
 
 
 def qsim_ffma_probe(n_blocks, iters, out, stream=None):

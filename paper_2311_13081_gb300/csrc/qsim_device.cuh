@@ -76,6 +76,23 @@ __device__ __forceinline__ uint4 draw(const EnvCfg& C, uint32_t c0, uint32_t c1,
     return philox(c0, c1, (tag << 24) | sub, C.run_id, C.key0, C.key1);
 }
 
+// Same stream with the rounds kept as a loop: for cold paths (resets, observation noise)
+// whose unrolled copies would only bloat the hot loop's instruction footprint.
+__device__ __forceinline__ uint4 draw_rolled(const EnvCfg& C, uint32_t c0, uint32_t c1,
+                                             uint32_t tag, uint32_t sub) {
+    uint32_t x0 = c0, x1 = c1, x2 = (tag << 24) | sub, x3 = C.run_id, k0 = C.key0, k1 = C.key1;
+#pragma unroll 1
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+        const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+        const uint32_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
+        x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
 // ((x >> 9) + 1/2) * 2^-23: exact in float, strictly inside (0, 1).
 __device__ __forceinline__ float u01(uint32_t x) {
     return ((float)(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
@@ -183,9 +200,9 @@ __device__ __forceinline__ void obs_state(const float* s, float* o) {
 
 // Observation noise of env `env` at global step t: 18 normals, two per Philox block.
 __device__ __forceinline__ void obs_noise(const EnvCfg& C, uint32_t env, uint32_t t, float* nz) {
-#pragma unroll
+#pragma unroll 1
     for (int b = 0; b < 9; ++b) {
-        const uint4 r = draw(C, env, t, TAG_OBS, (uint32_t)b);
+        const uint4 r = draw_rolled(C, env, t, TAG_OBS, (uint32_t)b);
         const int k = 2 * b;
         const float s0 = k < 3 ? C.sig[0] : (k < 12 ? C.sig[1] : (k < 15 ? C.sig[2] : C.sig[3]));
         const float s1 = (k + 1) < 3 ? C.sig[0]
@@ -251,7 +268,7 @@ __device__ __forceinline__ void reset_env(const EnvCfg& C, uint32_t env, uint32_
     float U[16];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        const uint4 r = draw(C, env, ep, TAG_RESET, (uint32_t)b);
+        const uint4 r = draw_rolled(C, env, ep, TAG_RESET, (uint32_t)b);
         U[4 * b] = u01(r.x); U[4 * b + 1] = u01(r.y); U[4 * b + 2] = u01(r.z); U[4 * b + 3] = u01(r.w);
     }
 #pragma unroll
@@ -270,7 +287,7 @@ __device__ __forceinline__ void reset_env(const EnvCfg& C, uint32_t env, uint32_
     for (int k = 0; k < 3; ++k) s[10 + k] = C.init_w * (2.0f * U[9 + k] - 1.0f);
 #pragma unroll
     for (int i = 0; i < 4; ++i) s[13 + i] = fmaf(C.init_rpm_hi - C.init_rpm_lo, U[12 + i], C.init_rpm_lo);
-    const uint4 a = draw(C, env, ep, TAG_DR, 0), b = draw(C, env, ep, TAG_DR, 1);
+    const uint4 a = draw_rolled(C, env, ep, TAG_DR, 0), b = draw_rolled(C, env, ep, TAG_DR, 1);
     prm7[0] = C.m0 * (1.0f + C.dr_mass * (2.0f * u01(a.x) - 1.0f));
     prm7[1] = C.Jx0 * (1.0f + C.dr_J * (2.0f * u01(a.y) - 1.0f));
     prm7[2] = C.Jy0 * (1.0f + C.dr_J * (2.0f * u01(a.z) - 1.0f));
@@ -279,7 +296,7 @@ __device__ __forceinline__ void reset_env(const EnvCfg& C, uint32_t env, uint32_
     prm7[5] = C.km0;
     prm7[6] = fmaf(C.tm_hi - C.tm_lo, u01(b.y), C.tm_lo);
     if (C.dist_f > 0.0f || C.dist_tau > 0.0f) {
-        const uint4 x = draw(C, env, ep, TAG_DIST, 0), y = draw(C, env, ep, TAG_DIST, 1);
+        const uint4 x = draw_rolled(C, env, ep, TAG_DIST, 0), y = draw_rolled(C, env, ep, TAG_DIST, 1);
         d[0] = C.dist_f * (2.0f * u01(x.x) - 1.0f);
         d[1] = C.dist_f * (2.0f * u01(x.y) - 1.0f);
         d[2] = C.dist_f * (2.0f * u01(x.z) - 1.0f);

@@ -476,6 +476,9 @@ extern "C" qsim_status qsim_create(const qsim_config* cfg, const qsim_params* ve
     h->t_now = h->head = h->size = 0;
     h->next_curriculum = cfg->curriculum_interval > 0 ? cfg->curriculum_interval : -1;
     h->rollout_warps = 0;
+    h->rollout_parts = 0;
+    h->rollout_chunk = 0;
+    h->streams_ready = false;
     cudaGetDevice(&h->device);
     const size_t ld = (size_t)h->ld;
     auto alloc = [&](void** p, size_t bytes) -> bool {
@@ -518,6 +521,13 @@ extern "C" qsim_status qsim_destroy(qsim_handle* h) {
                     h->p.side, h->p.rewardC, h->p.status};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (h->streams_ready) {
+        for (int i = 0; i < 4; ++i) {
+            cudaStreamDestroy(h->part_stream[i]);
+            cudaEventDestroy(h->ev_join[i]);
+        }
+        cudaEventDestroy(h->ev_fork);
+    }
     delete h;
     return QSIM_OK;
 }

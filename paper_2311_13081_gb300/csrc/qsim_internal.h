@@ -50,6 +50,12 @@ struct qsim_handle {
     int64_t next_curriculum;  // interaction count of the next curriculum change
     qsim::EnvPtrs p;
     int rollout_warps;
+    // rollout scheduling: env partitions on internal streams, launched in time chunks so
+    // that one partition's next chunk fills SMs the other leaves idle
+    int rollout_parts, rollout_chunk;
+    cudaStream_t part_stream[4];
+    cudaEvent_t ev_fork, ev_join[4];
+    bool streams_ready;
 };
 
 struct ac_handle {

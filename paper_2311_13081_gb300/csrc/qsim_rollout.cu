@@ -56,7 +56,8 @@ template <int H, int NW>
 __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
                                                      const float* __restrict__ actor, int T,
                                                      uint32_t t0, int64_t head0,
-                                                     int64_t capacity, float sigma_in) {
+                                                     int64_t capacity, float sigma_in,
+                                                     int warp0, int warp_end) {
     using L = RollLayout<H>;
     constexpr int OP = H / 8;  // outputs per lane
     constexpr int NQ = OP / 4; // float4 chunks per lane per weight row
@@ -95,8 +96,9 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = (blockIdx.x * NW + warp) * 32 + lane;  // global env index
-    if ((blockIdx.x * NW + warp) * 32 >= ld) return;      // warp-uniform
+    const int gw = warp0 + blockIdx.x * NW + warp;  // global warp (32 envs)
+    const int g = gw * 32 + lane;                      // global env index
+    if (gw >= warp_end) return;                        // warp-uniform
     const int tx = lane >> 3, ty = lane & 7;
     float* sObs = smem + L::WEIGHTS + warp * L::PER_WARP;
     float* sHid = sObs + L::OBS;
@@ -363,7 +365,8 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
     p.n_done[g] = n_done; p.len_sum[g] = len_sum; p.ret_sum[g] = ret_sum;
 }
 
-using RollFn = void (*)(EnvCfg, EnvPtrs, const float*, int, uint32_t, int64_t, int64_t, float);
+using RollFn = void (*)(EnvCfg, EnvPtrs, const float*, int, uint32_t, int64_t, int64_t, float,
+                        int, int);
 
 template <int H>
 static RollFn pick(int nw) {
@@ -421,8 +424,34 @@ static int default_warps(int hidden, int ld, int device) {
     return best_nw;
 }
 
+static int resident_warps(int hidden, int nw, int device) {
+    RollFn fn = roll_fn(hidden, nw);
+    int blocks = 0, sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, nw * 32, roll_smem(hidden, nw)) != cudaSuccess) {
+        cudaGetLastError();
+        blocks = 1;
+    }
+    return std::max(1, blocks) * nw * sms;
+}
+
+static qsim_status ensure_streams(qsim_handle* h) {
+    if (h->streams_ready) return QSIM_OK;
+    for (int p = 0; p < 4; ++p) {
+        QCHECK_CUDA(cudaStreamCreateWithFlags(&h->part_stream[p], cudaStreamNonBlocking));
+        QCHECK_CUDA(cudaEventCreateWithFlags(&h->ev_join[p], cudaEventDisableTiming));
+    }
+    QCHECK_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    h->streams_ready = true;
+    return QSIM_OK;
+}
+
+// Launches T steps of the rollout as `parts` env partitions x chunks of `chunk` steps.
+// Partition p owns warps [W p / parts, W (p+1) / parts); its chunks run in order on its
+// own stream, chunks of different partitions are issued interleaved, and the caller's
+// stream joins all partitions at the end.
 qsim_status launch_rollout(qsim_handle* h, const float* actor, int hidden, int T, float sigma,
-                           cudaStream_t st, int nw) {
+                           cudaStream_t st, int nw, int parts, int chunk) {
     RollFn fn = roll_fn(hidden, nw);
     if (!fn) return fail(QSIM_EINVAL, "qsim_rollout: no kernel for hidden=%d warps=%d", hidden, nw);
     const size_t smem = roll_smem(hidden, nw);
@@ -433,10 +462,35 @@ qsim_status launch_rollout(qsim_handle* h, const float* actor, int hidden, int T
         configured[hi][nw] = true;
     }
     const int warps = h->ld / 32;
-    const int grid = (warps + nw - 1) / nw;
-    fn<<<grid, nw * 32, smem, st>>>(h->dc, h->p, actor, T, (uint32_t)h->t_now, h->head,
-                                     h->capacity, sigma);
-    QCHECK_LAUNCH("k_rollout");
+    parts = std::max(1, std::min(parts, std::min(4, warps)));
+    if (chunk <= 0 || chunk > T) chunk = T;
+    const uint32_t t0 = (uint32_t)h->t_now;
+    if (parts == 1 && chunk == T) {
+        const int grid = (warps + nw - 1) / nw;
+        fn<<<grid, nw * 32, smem, st>>>(h->dc, h->p, actor, T, t0, h->head, h->capacity, sigma, 0,
+                                         warps);
+        QCHECK_LAUNCH("k_rollout");
+        return QSIM_OK;
+    }
+    qsim_status s = ensure_streams(h);
+    if (s != QSIM_OK) return s;
+    QCHECK_CUDA(cudaEventRecord(h->ev_fork, st));
+    for (int p = 0; p < parts; ++p) QCHECK_CUDA(cudaStreamWaitEvent(h->part_stream[p], h->ev_fork, 0));
+    for (int t = 0; t < T; t += chunk) {
+        const int tc = std::min(chunk, T - t);
+        for (int p = 0; p < parts; ++p) {
+            const int w0 = (int)((int64_t)warps * p / parts), w1 = (int)((int64_t)warps * (p + 1) / parts);
+            if (w1 <= w0) continue;
+            const int grid = (w1 - w0 + nw - 1) / nw;
+            fn<<<grid, nw * 32, smem, h->part_stream[p]>>>(h->dc, h->p, actor, tc, t0 + (uint32_t)t,
+                                                            h->head + t, h->capacity, sigma, w0, w1);
+            QCHECK_LAUNCH("k_rollout");
+        }
+    }
+    for (int p = 0; p < parts; ++p) {
+        QCHECK_CUDA(cudaEventRecord(h->ev_join[p], h->part_stream[p]));
+        QCHECK_CUDA(cudaStreamWaitEvent(st, h->ev_join[p], 0));
+    }
     return QSIM_OK;
 }
 
@@ -462,7 +516,14 @@ extern "C" qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t 
     if (n_steps == 0) return QSIM_OK;
     int nw = h->rollout_warps ? h->rollout_warps : default_warps(hidden, h->ld, h->device);
     if (roll_smem(hidden, nw) > 227 * 1024) nw = 2;
-    qsim_status s = launch_rollout(h, actor, hidden, n_steps, sigma_e, (cudaStream_t)stream, nw);
+    int parts = h->rollout_parts, chunk = h->rollout_chunk;
+    if (parts <= 0) {
+        // more than one wave of warps: pipeline two partitions in 100-step chunks
+        parts = (h->ld / 32 > resident_warps(hidden, nw, h->device)) ? 2 : 1;
+        chunk = parts > 1 ? 100 : 0;
+    }
+    qsim_status s = launch_rollout(h, actor, hidden, n_steps, sigma_e, (cudaStream_t)stream, nw,
+                                   parts, chunk);
     if (s != QSIM_OK) return s;
     h->t_now += n_steps;
     if (h->capacity > 0) {
@@ -484,27 +545,45 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
     QCHECK_CUDA(cudaEventCreate(&e0));
     QCHECK_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_nw = 0;
+    int best_nw = 0, best_parts = 1, best_chunk = 0;
+    struct Sched { int parts, chunk; };
+    const int tc = std::max(1, std::min(100, n_steps / 4));
+    const Sched scheds[] = {{1, 0}, {2, tc}, {3, tc}, {4, tc}};
     for (int nw : kWarpChoices) {
         if (roll_smem(hidden, nw) > (size_t)smem_blk) continue;
-        if (((h->t_now + n_steps) >> 32) != 0) break;
-        cudaEventRecord(e0, st);
-        qsim_status s = launch_rollout(h, actor, hidden, n_steps, -1.0f, st, nw);
-        cudaEventRecord(e1, st);
-        if (s != QSIM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
-        h->t_now += n_steps;
-        if (h->capacity > 0) {
-            h->head = (h->head + n_steps) % h->capacity;
-            h->size = std::min<int64_t>(h->capacity, h->size + n_steps);
+        for (const Sched& sc : scheds) {
+            if (((h->t_now + n_steps) >> 32) != 0) break;
+            if (sc.parts > 1 && h->ld / 32 <= resident_warps(hidden, nw, h->device)) continue;
+            cudaEventRecord(e0, st);
+            qsim_status s = launch_rollout(h, actor, hidden, n_steps, -1.0f, st, nw, sc.parts, sc.chunk);
+            cudaEventRecord(e1, st);
+            if (s != QSIM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+            h->t_now += n_steps;
+            if (h->capacity > 0) {
+                h->head = (h->head + n_steps) % h->capacity;
+                h->size = std::min<int64_t>(h->capacity, h->size + n_steps);
+            }
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_nw = nw; best_parts = sc.parts; best_chunk = sc.chunk; }
         }
-        cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; best_nw = nw; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     QCHECK_LAUNCH("qsim_rollout_autotune");
-    if (best_nw) h->rollout_warps = best_nw;
+    if (best_nw) {
+        h->rollout_warps = best_nw;
+        h->rollout_parts = best_parts;
+        h->rollout_chunk = best_parts > 1 ? 100 : 0;
+        (void)best_chunk;
+    }
     return best_nw;
+}
+
+extern "C" int32_t qsim_rollout_schedule(qsim_handle* h, int32_t parts, int32_t chunk) {
+    if (!h) return 0;
+    if (parts >= 0 && parts <= 4) h->rollout_parts = parts;
+    if (chunk >= 0) h->rollout_chunk = chunk;
+    return h->rollout_parts;
 }

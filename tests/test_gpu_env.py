@@ -253,3 +253,24 @@ def test_recalc_rewards_parity(gpu):
         assert_close(rec[:, 21, :n], buf["r"], 1.0, what="recalc")
     finally:
         q.qsim_destroy(h)
+
+
+def test_partitioned_schedule_is_bitwise_identical(gpu):
+    """Env partitions on internal streams, advanced in time chunks, give exactly the
+    single-launch results (same per-env arithmetic, different launch grouping)."""
+    q = gpu
+    n = 65536
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=8, learning_starts=2)
+    A = torch.tensor(_actor(d, 64), device="cuda")
+    outs = []
+    for parts, chunk in ((1, 0), (3, 2), (2, 1)):
+        h = q.qsim_create(cfg, veh)
+        q.qsim_rollout_schedule(h, parts, chunk)
+        q.qsim_rollout(h, A, 64, 5, 0.1)
+        torch.cuda.synchronize()
+        info = q.qsim_info_get(h)
+        outs.append([cpu(info[k]).copy() for k in ("records", "side", "state", "hist", "ep_step")])
+        q.qsim_destroy(h)
+    for o in outs[1:]:
+        for x, y in zip(o, outs[0]):
+            assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
