@@ -52,6 +52,13 @@ def parse():
     ap.add_argument("--horizon", type=int, default=1000)
     ap.add_argument("--no-extras", action="store_true", help="headline measurement only")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--only-learner", type=int, default=0, metavar="RUNS",
+                    help="only the batched-learner sample with RUNS runs (for profiling)")
+    ap.add_argument("--learner-steps", type=int, default=20)
+    ap.add_argument("--warps", type=int, default=0,
+                    help="pin the rollout's warps per block and skip the autotuner (profiling)")
+    ap.add_argument("--parts", type=int, default=1, help="with --warps: env partitions")
+    ap.add_argument("--chunk", type=int, default=100, help="with --warps: steps per chunk")
     return ap.parse_args()
 
 
@@ -215,10 +222,19 @@ def measure_training(torch, q, W, n_runs=512, steps=20, prefill=20):
             flops += 2 * mac * B * steps
         q.ac_train(runs, envs, prefill, persistent=1)  # fills buffers past the history window
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        q.ac_train(runs, envs, steps, persistent=1 if mode == "persistent" else 0)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        if mode == "persistent":
+            plan = q.ac_plan_create(runs, envs, steps)  # persistent launch captured in a graph
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            q.ac_plan_run(plan, 1)
+            q.ac_plan_sync(plan)
+            dt = time.perf_counter() - t0
+            q.ac_plan_destroy(plan)
+        else:
+            t0 = time.perf_counter()
+            q.ac_train(runs, envs, steps, persistent=0)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
         res[mode] = {"s": dt, "updates": n_runs * steps, "updates_per_s": n_runs * steps / dt,
                      "tflops": flops / dt / 1e12}
         for a, h in zip(runs, envs):
@@ -248,6 +264,94 @@ def measure_c1(torch, q, W, steps=2000):
     q.qsim_destroy(h)
     return {"steps": steps, "s": dt, "updates_per_s": steps / dt,
             "projected_9000_updates_s": 9000 * dt / steps}
+
+
+def measure_diff(torch, q, W, n=4096, H=200, ckpt=20):
+    """Differentiation workload: gradients of the H-step loss w.r.t. the actor weights and
+    (m, J) of n envs, closed loop with the 82-64-64-4 actor, checkpoint every ckpt steps;
+    and w.r.t. the action sequence in open loop."""
+    import numpy as np
+    from paper_2311_13081_gb300 import diff
+    d = W.config("c1")
+    veh = q.make_params(d)
+    ld = (n + 31) // 32 * 32
+    s0 = torch.tensor(W.random_states(0, ld, p=0.1, v=0.5, w=0.5, rpm=(12000.0, 17000.0)).T.copy(),
+                      dtype=torch.float32, device="cuda")
+    prm = torch.tensor(W.random_params(1, ld).T.copy(), dtype=torch.float32, device="cuda")
+    res = {}
+    for mode in (1, 0):
+        desc = diff.make_desc(n, ld, H, ckpt, mode, (1.0, 0.5, 0.2, 0.05), n_hist=16, hidden=64)
+        ws = torch.empty(q.qsim_vjp_workspace(desc) // 4 + 1, device="cuda")
+        loss = torch.zeros(ld, device="cuda")
+        gp = torch.zeros(4, ld, device="cuda")
+        if mode == 1:
+            hp = dict(W.TD3)
+            cfg = q.make_config(d, 1, 32, reward=W.REWARD)
+            h = q.qsim_create(cfg, veh)
+            a = q.ac_create(q.make_ac_config(hp), h)
+            x = q.ac_info_get(a)["actor"].clone()
+            q.ac_destroy(a)
+            q.qsim_destroy(h)
+            gx = torch.zeros_like(x)
+            args = (None, x, None, loss, None, gx, gp, None, ws)
+        else:
+            x = torch.tensor(W.random_actions(2, (H, 4, ld), -0.3, 0.4), dtype=torch.float32,
+                             device="cuda")
+            gx = torch.zeros_like(x)
+            args = (x, None, None, loss, gx, None, gp, None, ws)
+        q.qsim_rollout_vjp(desc, veh, s0, prm, *args)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        q.qsim_rollout_vjp(desc, veh, s0, prm, *args)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        tag = "closed_loop_actor" if mode == 1 else "open_loop_actions"
+        res[tag] = {"ms": ms, "env_steps_per_s": n * H / (ms * 1e-3),
+                    "finite": bool(torch.isfinite(gx).all() and torch.isfinite(gp).all())}
+    res["config"] = {"envs": n, "horizon": H, "ckpt": ckpt,
+                     "workspace_mb": q.qsim_vjp_workspace(desc) / 1e6}
+    return res
+
+
+def measure_c5(torch, q, W, n_runs=128, n_envs=64, iters=40, updates_per_step=64):
+    """Asymmetric privileged critic + curriculum at scale (bounded sample): 128 runs x 64
+    envs, replay 1,000,000 transitions per run, curriculum interval shortened so that the
+    sample contains changes with full-buffer reward recalculation."""
+    runs, envs = [], []
+    cur = dict(W.CURRICULUM)
+    cur["interval"] = 1024
+    for r in range(n_runs):
+        d = W.config("c5")
+        d.update(seed=r, run_id=r, learning_starts=0)
+        cfg = q.make_config(d, n_envs, 1_000_000 // n_envs, reward=W.REWARD, sigma_e=0.1,
+                            curriculum=cur)
+        h = q.qsim_create(cfg, q.make_params(d))
+        hp = dict(W.TD3)
+        hp.update(hidden=64, batch=256)
+        runs.append(q.ac_create(q.make_ac_config(hp, cluster=1, updates_per_step=updates_per_step), h))
+        envs.append(h)
+    q.ac_train(runs, envs, 20, persistent=1)
+    torch.cuda.synchronize()
+    plan = q.ac_plan_create(runs, envs, iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    q.ac_plan_run(plan, 1)
+    q.ac_plan_sync(plan)
+    dt = time.perf_counter() - t0
+    q.ac_plan_destroy(plan)
+    rc = q.qsim_info_get(envs[0])["reward_c"].tolist()
+    for a, h in zip(runs, envs):
+        q.ac_destroy(a)
+        q.qsim_destroy(h)
+    upd = n_runs * iters * updates_per_step
+    return {"s": dt, "env_steps": n_runs * n_envs * iters, "updates": upd,
+            "updates_per_s": upd / dt, "env_steps_per_s": n_runs * n_envs * iters / dt,
+            "C_ra_after": rc[4], "sigma_e_after": rc[7],
+            "config": {"runs": n_runs, "envs_per_run": n_envs, "iters": iters,
+                       "updates_per_step": updates_per_step, "replay_per_run": 1_000_000,
+                       "curriculum_interval": 1024, "critic": "privileged (96 inputs)"}}
 
 
 def cpu_baseline(n_envs=4096, horizon=1000, chunk=50):
@@ -325,6 +429,12 @@ def main():
     import paper_2311_13081_gb300 as q
     import workloads as W
 
+    if args.only_learner:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        q.load()
+        print(json.dumps({"learner_batched": measure_training(torch, q, W, n_runs=args.only_learner,
+                                                              steps=args.learner_steps)}))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -344,7 +454,11 @@ def main():
     hidden = 64
     info = q.qsim_info_get(h)
     l2 = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
-    tuned = q.qsim_rollout_autotune(h, actor, hidden, 100)
+    if args.warps:
+        tuned = q.qsim_rollout_tune(h, args.warps)
+        q.qsim_rollout_schedule(h, args.parts, args.chunk if args.parts > 1 else 0)
+    else:
+        tuned = q.qsim_rollout_autotune(h, actor, hidden, 100)
     for _ in range(args.warmup):
         q.qsim_rollout(h, actor, hidden, horizon)
     torch.cuda.synchronize()
@@ -410,6 +524,8 @@ def main():
         extras["dynamics_only"] = measure_dynamics(torch, q, veh)
         extras["learner_batched"] = measure_training(torch, q, W)
         extras["learner_single_run_c1"] = measure_c1(torch, q, W)
+        extras["differentiation_c3"] = measure_diff(torch, q, W)
+        extras["asymmetric_curriculum_c5"] = measure_c5(torch, q, W)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline()

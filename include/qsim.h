@@ -317,6 +317,22 @@ qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs, int32_t n
                      int64_t steps_per_run, int32_t persistent, void* stream);
 qsim_status ac_sync(ac_handle* a);
 
+/* Graph-captured batched training.  ac_plan_create builds, once, everything ac_train's
+ * persistent form builds per call (run descriptors, per-cluster scratch, the longest-
+ * processing-time-first run schedule) and captures one persistent launch of
+ * steps_per_chunk steps for all runs into a CUDA graph (synchronous).  ac_plan_run replays
+ * it n_chunks times on `stream` (asynchronous); the runs' counters advance in device memory,
+ * so consecutive replays continue where the last one stopped.  ac_plan_sync copies the
+ * counters back into the handles (synchronises `stream`); call it before using the handles
+ * with any other entry point.  The handles must outlive the plan and must not be used by
+ * other calls between ac_plan_create and ac_plan_sync. */
+typedef struct ac_plan ac_plan;
+qsim_status ac_plan_create(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
+                           int32_t steps_per_chunk, ac_plan** out);
+qsim_status ac_plan_run(ac_plan* p, int32_t n_chunks, void* stream);
+qsim_status ac_plan_sync(ac_plan* p, void* stream);
+qsim_status ac_plan_destroy(ac_plan* p);
+
 /* Checkpoint: weights, targets, Adam moments and counters, the env set's states and
  * counters and current reward constants (not the replay buffer).  Versioned binary. */
 qsim_status ac_save(const ac_handle* a, const qsim_handle* env, const char* path);

@@ -131,6 +131,10 @@ _SIGS = {
     "ac_update_static": (C.c_int, [P, P, C.c_int32, P]),
     "ac_train": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int32, P]),
     "ac_sync": (C.c_int, [P]),
+    "ac_plan_create": (C.c_int, [P, P, C.c_int32, C.c_int32, C.POINTER(P)]),
+    "ac_plan_run": (C.c_int, [P, C.c_int32, P]),
+    "ac_plan_sync": (C.c_int, [P, P]),
+    "ac_plan_destroy": (C.c_int, [P]),
     "ac_save": (C.c_int, [P, P, C.c_char_p]),
     "ac_load": (C.c_int, [P, P, C.c_char_p]),
     "qsim_vjp_workspace": (C.c_size_t, [C.POINTER(QsimVjpDesc)]),
@@ -417,6 +421,28 @@ def ac_train(runs, envs, steps_per_run, persistent=1, stream=None):
     ea = (P * n)(*[e.value if isinstance(e, P) else e for e in envs])
     _chk(_lib.ac_train(C.cast(ra, P), C.cast(ea, P), n, steps_per_run, persistent,
                        _stream(stream)))
+
+
+def ac_plan_create(runs, envs, steps_per_chunk):
+    n = len(runs)
+    ra = (P * n)(*[r.value if isinstance(r, P) else r for r in runs])
+    ea = (P * n)(*[e.value if isinstance(e, P) else e for e in envs])
+    p = P()
+    _chk(_lib.ac_plan_create(C.cast(ra, P), C.cast(ea, P), n, steps_per_chunk, C.byref(p)))
+    return p
+
+
+def ac_plan_run(plan, n_chunks, stream=None):
+    _chk(_lib.ac_plan_run(plan, n_chunks, _stream(stream)))
+
+
+def ac_plan_sync(plan, stream=None):
+    _chk(_lib.ac_plan_sync(plan, _stream(stream)))
+
+
+def ac_plan_destroy(plan):
+    if plan:
+        _chk(_lib.ac_plan_destroy(plan))
 
 
 def ac_sync(a):

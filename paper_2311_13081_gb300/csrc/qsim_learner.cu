@@ -58,7 +58,7 @@ struct RunDesc {
 };
 
 // Forward of in -> H (ReLU) -> H (ReLU) -> out (tanh or linear) for M rows of X [M][ldx].
-__device__ void mlp_fwd(const float* W, int in, int H, int out, const float* X, int ldx, int M,
+__device__ __noinline__ void mlp_fwd(const float* W, int in, int H, int out, const float* X, int ldx, int M,
                         float* H1, float* H2, float* Y, int ldy, bool tanh_out, float* sm) {
     const float* W1 = W;
     const float* b1 = W1 + H * in;
@@ -67,19 +67,18 @@ __device__ void mlp_fwd(const float* W, int in, int H, int out, const float* X, 
     const float* W3 = b2 + H;
     const float* b3 = W3 + out * H;
     cta_gemm(M, H, in, Mat{X, ldx, 1}, Mat{W1, 1, in}, sm,
-             [&](int m, int n, float v) { H1[m * H + n] = fmaxf(v + ldcg(b1 + n), 0.0f); });
+             [&](int m, int n, float v) { H1[m * H + n] = fmaxf(v, 0.0f); }, b1);
     cta_gemm(M, H, H, Mat{H1, H, 1}, Mat{W2, 1, H}, sm,
-             [&](int m, int n, float v) { H2[m * H + n] = fmaxf(v + ldcg(b2 + n), 0.0f); });
+             [&](int m, int n, float v) { H2[m * H + n] = fmaxf(v, 0.0f); }, b2);
     cta_gemm(M, out, H, Mat{H2, H, 1}, Mat{W3, 1, H}, sm, [&](int m, int n, float v) {
-        const float z = v + ldcg(b3 + n);
-        Y[m * ldy + n] = tanh_out ? tanhf(z) : z;
-    });
+        Y[m * ldy + n] = tanh_out ? tanhf(v) : v;
+    }, b3);
 }
 
 // Reverse through the MLP for M rows.  dZ3 [M][out] holds dLoss/d(pre-activation of the
 // output layer).  Writes the parameter gradient (this CTA's partial) into G (layout of
 // W) and, if dX != nullptr, dLoss/dX [M][in] (only columns [x_lo, in) are needed).
-__device__ void mlp_bwd(const float* W, int in, int H, int out, const float* X, int ldx, int M,
+__device__ __noinline__ void mlp_bwd(const float* W, int in, int H, int out, const float* X, int ldx, int M,
                         const float* H1, const float* H2, const float* dZ3, float* dZ2,
                         float* dZ1, float* G, float* dX, int x_lo, float* sm) {
     const float* W2 = W + H * in + H;
@@ -102,7 +101,7 @@ __device__ void mlp_bwd(const float* W, int in, int H, int out, const float* X, 
     }
     // dZ2 = (dZ3 W3) * (H2 > 0)
     cta_gemm(M, H, out, Mat{dZ3, out, 1}, Mat{W3, H, 1}, sm, [&](int m, int n, float v) {
-        dZ2[m * H + n] = ldcg(H2 + m * H + n) > 0.0f ? v : 0.0f;
+        dZ2[m * H + n] = H2[m * H + n] > 0.0f ? v : 0.0f;  // written by this CTA
     });
     if (G) {
         cta_gemm(H, H, M, Mat{dZ2, 1, H}, Mat{H1, H, 1}, sm,
@@ -115,7 +114,7 @@ __device__ void mlp_bwd(const float* W, int in, int H, int out, const float* X, 
     }
     // dZ1 = (dZ2 W2) * (H1 > 0)
     cta_gemm(M, H, H, Mat{dZ2, H, 1}, Mat{W2, H, 1}, sm, [&](int m, int n, float v) {
-        dZ1[m * H + n] = ldcg(H1 + m * H + n) > 0.0f ? v : 0.0f;
+        dZ1[m * H + n] = H1[m * H + n] > 0.0f ? v : 0.0f;  // written by this CTA
     });
     if (G) {
         cta_gemm(H, in, M, Mat{dZ1, 1, H}, Mat{X, ldx, 1}, sm,
@@ -195,7 +194,7 @@ __device__ __forceinline__ void load_env(const RunDesc& R, int e, float* s, floa
 // One env step of all envs of run R (executed by one CTA): observation, actor forward
 // (generic GEMM path), warm-up / exploration, RK4, reward, termination, record write,
 // history update and reset.
-__device__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, int64_t slot, float* sm) {
+__device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, int64_t slot, float* sm) {
     const EnvCfg& C = R.C;
     const int ld = C.ld, n = R.n_env, DA = R.DA, H = R.H;
     const bool warm = (int64_t)t < (int64_t)C.learning_starts;
@@ -314,7 +313,7 @@ __device__ __forceinline__ int64_t pmod64(int64_t a, int64_t m) {
 
 // Gather one sample: rebuilds o_a, o_a', o_c (with stored action), o_c' (action slot
 // filled later), r and the termination flag from the compact replay records.
-__device__ void gather_sample(const RunDesc& R, int j, uint32_t u, int64_t head, int64_t size,
+__device__ __noinline__ void gather_sample(const RunDesc& R, int j, uint32_t u, int64_t head, int64_t size,
                               int64_t t_now, const Scr& S, int jl) {
     const EnvCfg& C = R.C;
     const int ld = C.ld, F = C.F, NE = R.n_env, DA = R.DA, DC = R.DC;
@@ -448,7 +447,7 @@ __device__ float block_sum(float v, float* red) {
 }
 
 // One TD3 update of run R by the cluster (rank `rk` of S).
-__device__ void td3_update(RunDesc& R, int64_t head, int64_t size, int64_t t_now, uint32_t u,
+__device__ __noinline__ void td3_update(RunDesc& R, int64_t head, int64_t size, int64_t t_now, uint32_t u,
                            int64_t& t_a, int64_t& t_c, const Scr& S, float* scr_base,
                            size_t scr_stride, int cl_base, int rk, int nS, float* sm) {
     const int B = R.B, Bc = B / nS, H = R.H, DA = R.DA, DC = R.DC, PA = R.PA, PC = R.PC;
@@ -557,7 +556,7 @@ __device__ void td3_update(RunDesc& R, int64_t head, int64_t size, int64_t t_now
 }
 
 // Curriculum change + reward recalculation over the run's buffer, split over the cluster.
-__device__ void curriculum_step(RunDesc& R, int64_t head, int64_t size, int rk, int nS) {
+__device__ __noinline__ void curriculum_step(RunDesc& R, int64_t head, int64_t size, int rk, int nS) {
     if (rk == 0 && threadIdx.x == 0) {
         for (int i = 0; i < 7; ++i) {
             const float c = R.E.rewardC[i], x = c * R.cf[i];
@@ -1049,6 +1048,179 @@ extern "C" qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs
         }
     }
     return launch_train(A, E, (int)steps_per_run, 1, nS, st, nullptr, max_clusters);
+}
+
+// ------------------------------------------------------------ graph-captured plans
+struct ac_plan {
+    std::vector<ac_handle*> A;
+    std::vector<qsim_handle*> E;
+    RunDesc* d_runs = nullptr;
+    int* d_order = nullptr;
+    int* d_off = nullptr;
+    float* scratch = nullptr;
+    size_t stride = 0;
+    int nS = 1, n_clusters = 1, chunk = 1;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t steps_run = 0;
+};
+
+extern "C" qsim_status ac_plan_destroy(ac_plan* p) {
+    if (!p) return QSIM_OK;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->d_runs) cudaFree(p->d_runs);
+    if (p->d_order) cudaFree(p->d_order);
+    if (p->d_off) cudaFree(p->d_off);
+    if (p->scratch) cudaFree(p->scratch);
+    delete p;
+    return QSIM_OK;
+}
+
+extern "C" qsim_status ac_plan_create(ac_handle* const* runs, qsim_handle* const* envs,
+                                      int32_t n_runs, int32_t steps_per_chunk, ac_plan** out) {
+    if (!runs || !envs || !out || n_runs < 1 || steps_per_chunk < 1)
+        return fail(QSIM_EINVAL, "ac_plan_create: bad argument");
+    *out = nullptr;
+    ac_plan* p = new ac_plan();
+    p->A.assign(runs, runs + n_runs);
+    p->E.assign(envs, envs + n_runs);
+    p->chunk = steps_per_chunk;
+    for (int i = 0; i < n_runs; ++i) {
+        qsim_status s = validate_pair(p->A[i], p->E[i]);
+        if (s != QSIM_OK) { ac_plan_destroy(p); return s; }
+        if ((uint64_t)p->E[i]->capacity * (uint64_t)p->E[i]->n >= (1ull << 32)) {
+            ac_plan_destroy(p);
+            return fail(QSIM_EINVAL, "ac_plan_create: replay buffer exceeds 2^32 transitions");
+        }
+    }
+    p->nS = pick_cluster(p->A[0], n_runs);
+    for (int i = 0; i < n_runs; ++i)
+        if (pick_cluster(p->A[i], n_runs) != p->nS || p->A[i]->batch % p->nS) {
+            ac_plan_destroy(p);
+            return fail(QSIM_EINVAL, "ac_plan_create: runs need one cluster size dividing every batch");
+        }
+    const int nS = p->nS;
+    int max_clusters = 1;
+    {
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(nS * 1024);
+        lc.blockDim = dim3(LT);
+        lc.dynamicSmemBytes = learner_smem();
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = nS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        if (nS > 8) cudaFuncSetAttribute(k_train, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (cudaOccupancyMaxActiveClusters(&max_clusters, k_train, &lc) != cudaSuccess || max_clusters < 1) {
+            cudaGetLastError();
+            int sms = 152;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->A[0]->device);
+            max_clusters = std::max(1, sms / nS);
+        }
+    }
+    const int n = n_runs;
+    p->n_clusters = std::max(1, std::min(n, max_clusters));
+    std::vector<RunDesc> D(n);
+    for (int i = 0; i < n; ++i) {
+        fill_desc(p->A[i], p->E[i], D[i]);
+        p->stride = std::max(p->stride, scratch_floats(p->A[i]->batch / nS, p->A[i]->hidden,
+                                                       p->A[i]->obs_dim, p->A[i]->critic_in,
+                                                       p->A[i]->n_actor, p->A[i]->n_critic, p->E[i]->n));
+    }
+    // longest-processing-time-first assignment of runs to clusters
+    std::vector<int> order(n), off(p->n_clusters + 1, 0);
+    {
+        std::vector<double> cost(n);
+        for (int i = 0; i < n; ++i) {
+            const double h = p->A[i]->hidden;
+            cost[i] = (double)p->A[i]->batch * (h * (p->A[i]->obs_dim + p->A[i]->critic_in) + 3 * h * h) + 1.0;
+        }
+        std::vector<int> idx(n);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        std::vector<double> load(p->n_clusters, 0.0);
+        std::vector<std::vector<int>> lists(p->n_clusters);
+        for (int i : idx) {
+            int best = 0;
+            for (int c = 1; c < p->n_clusters; ++c)
+                if (load[c] < load[best]) best = c;
+            load[best] += cost[i];
+            lists[best].push_back(i);
+        }
+        int k = 0;
+        for (int c = 0; c < p->n_clusters; ++c) {
+            off[c] = k;
+            for (int i : lists[c]) order[k++] = i;
+        }
+        off[p->n_clusters] = k;
+    }
+    const size_t scr_bytes = sizeof(float) * p->stride * (size_t)p->n_clusters * nS;
+    if (cudaMalloc((void**)&p->d_runs, sizeof(RunDesc) * n) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_order, sizeof(int) * n) != cudaSuccess ||
+        cudaMalloc((void**)&p->d_off, sizeof(int) * (p->n_clusters + 1)) != cudaSuccess ||
+        cudaMalloc((void**)&p->scratch, scr_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ac_plan_destroy(p);
+        return fail(QSIM_ENOMEM, "ac_plan_create: allocation failed");
+    }
+    cudaMemcpy(p->d_runs, D.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_off, off.data(), sizeof(int) * (p->n_clusters + 1), cudaMemcpyHostToDevice);
+    // capture one chunk of the persistent launch
+    cudaStream_t cs;
+    QCHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(p->n_clusters * nS);
+    lc.blockDim = dim3(LT);
+    lc.dynamicSmemBytes = learner_smem();
+    lc.stream = cs;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess)
+        e = cudaLaunchKernelEx(&lc, k_train, p->d_runs, (const int*)p->d_order, (const int*)p->d_off,
+                               steps_per_chunk, 1, p->scratch, p->stride, nS);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        ac_plan_destroy(p);
+        return cuda_fail(e, "ac_plan_create: graph capture");
+    }
+    *out = p;
+    return QSIM_OK;
+}
+
+extern "C" qsim_status ac_plan_run(ac_plan* p, int32_t n_chunks, void* stream) {
+    if (!p || n_chunks < 0) return fail(QSIM_EINVAL, "ac_plan_run: bad argument");
+    for (size_t i = 0; i < p->E.size(); ++i)
+        if (((p->E[i]->t_now + p->steps_run + (int64_t)n_chunks * p->chunk) >> 32) != 0)
+            return fail(QSIM_ESTATE, "ac_plan_run: step counter exhausted");
+    for (int c = 0; c < n_chunks; ++c) QCHECK_CUDA(cudaGraphLaunch(p->exec, (cudaStream_t)stream));
+    p->steps_run += (int64_t)n_chunks * p->chunk;
+    return QSIM_OK;
+}
+
+extern "C" qsim_status ac_plan_sync(ac_plan* p, void* stream) {
+    if (!p) return fail(QSIM_EINVAL, "ac_plan_sync: null plan");
+    const size_t n = p->A.size();
+    std::vector<RunDesc> D(n);
+    QCHECK_CUDA(cudaMemcpyAsync(D.data(), p->d_runs, sizeof(RunDesc) * n, cudaMemcpyDeviceToHost,
+                                (cudaStream_t)stream));
+    QCHECK_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    for (size_t i = 0; i < n; ++i) read_back(p->A[i], p->E[i], D[i]);
+    p->steps_run = 0;
+    return QSIM_OK;
 }
 
 extern "C" qsim_status ac_sync(ac_handle* a) {

@@ -257,3 +257,43 @@ def test_update_rejects_empty_buffer(gpu):
     finally:
         q.ac_destroy(a)
         q.qsim_destroy(h)
+
+
+def test_graph_plan_equals_persistent_training(gpu):
+    """A captured plan replayed in chunks gives bitwise the single persistent launch."""
+    q = gpu
+
+    def make():
+        runs, envs = [], []
+        for r in range(4):
+            d, cfg, veh = lib_config(q, "c1", n_envs=3, capacity=40, learning_starts=5,
+                                     episode_len=15, seed=10 + r, run_id=r)
+            h = q.qsim_create(cfg, veh)
+            hp = dict(W.TD3)
+            hp.update(hidden=[32, 16][r % 2], batch=32)
+            runs.append(q.ac_create(q.make_ac_config(hp, cluster=1), h))
+            envs.append(h)
+        return runs, envs
+
+    r1, e1 = make()
+    q.ac_train(r1, e1, 24, persistent=1)
+    r2, e2 = make()
+    plan = q.ac_plan_create(r2, e2, 8)
+    q.ac_plan_run(plan, 3)
+    q.ac_plan_sync(plan)
+    torch.cuda.synchronize()
+    try:
+        for a, b, ha, hb in zip(r1, r2, e1, e2):
+            A, B = q.ac_info_get(a), q.ac_info_get(b)
+            assert A["updates"] == B["updates"] and A["t_actor"] == B["t_actor"]
+            for k in NETS:
+                assert np.array_equal(cpu(A[k]).view(np.uint32), cpu(B[k]).view(np.uint32)), k
+            IA, IB = q.qsim_info_get(ha), q.qsim_info_get(hb)
+            assert IA["t_now"] == IB["t_now"] == 24 and IA["head"] == IB["head"]
+            for k in ("state", "records"):
+                assert np.array_equal(cpu(IA[k]).view(np.uint32), cpu(IB[k]).view(np.uint32)), k
+    finally:
+        q.ac_plan_destroy(plan)
+        for a, h in zip(r1 + r2, e1 + e2):
+            q.ac_destroy(a)
+            q.qsim_destroy(h)
