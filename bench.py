@@ -59,6 +59,7 @@ def parse():
                     help="pin the rollout's warps per block and skip the autotuner (profiling)")
     ap.add_argument("--parts", type=int, default=1, help="with --warps: env partitions")
     ap.add_argument("--chunk", type=int, default=100, help="with --warps: steps per chunk")
+    ap.add_argument("--packed", type=int, default=1, help="with --warps: paired-FMA variant")
     return ap.parse_args()
 
 
@@ -153,7 +154,12 @@ def measure_ffma(torch, q):
     e1.synchronize()
     ms = e0.elapsed_time(e1)
     flops = blocks * 256 * iters * 8 * 16 * 2
-    return flops / (ms * 1e-3) / 1e12
+    e0.record()
+    q.qsim_ffma_probe(blocks, -iters // 2, out)  # paired f32x2 FMAs, same FMA count
+    e1.record()
+    e1.synchronize()
+    ms2 = e0.elapsed_time(e1)
+    return {"ffma": flops / (ms * 1e-3) / 1e12, "ffma2": flops / (ms2 * 1e-3) / 1e12}
 
 
 def measure_dynamics(torch, q, veh):
@@ -457,6 +463,7 @@ def main():
     if args.warps:
         tuned = q.qsim_rollout_tune(h, args.warps)
         q.qsim_rollout_schedule(h, args.parts, args.chunk if args.parts > 1 else 0)
+        q.qsim_rollout_packed(h, args.packed)
     else:
         tuned = q.qsim_rollout_autotune(h, actor, hidden, 100)
     for _ in range(args.warmup):
@@ -478,6 +485,8 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    packed_used = q.qsim_rollout_packed(h, -2)
+    parts_used = q.qsim_rollout_schedule(h, -1, -1)
     t_dev = sum(ms) / 1e3
     if world > 1:
         tt = torch.tensor([t_dev], device="cuda")
@@ -512,7 +521,7 @@ def main():
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras["fp32_ffma_probe_tflops"] = measure_ffma(torch, q)
+        extras["fp32_fma_probe_tflops"] = measure_ffma(torch, q)
         extras["reward_recalc"] = measure_recalc(torch, q, h, n, horizon, hbm)
         st = q.qsim_stats_get(h)
         extras["episodes"] = st
@@ -540,7 +549,9 @@ def main():
                                    f"replay {n}x{horizon} in HBM",
                        "envs_per_gpu": n, "steps_per_bench_step": horizon,
                        "l2": "flushed before every timed step (512 MB write)",
-                       "rollout_warps_per_block": tuned},
+                       "rollout_warps_per_block": tuned,
+                       "rollout_packed_fma": packed_used,
+                       "rollout_partitions": parts_used},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                          "traffic": (None if NCU_DRAM_BYTES_PER_ENV_STEP is None

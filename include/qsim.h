@@ -218,6 +218,12 @@ int32_t qsim_rollout_tune(qsim_handle* h, int32_t warps_per_block);
  * effect; a negative argument leaves that setting unchanged. */
 int32_t qsim_rollout_schedule(qsim_handle* h, int32_t parts, int32_t chunk);
 
+/* Rollout kernel variant: packed = 1 uses Blackwell's paired FP32 FMA (fma.rn.f32x2: two
+ * single-precision FMAs per instruction, results identical to the scalar kernel), 0 the
+ * scalar kernel, -1 automatic (the autotuner decides; scalar until it has run).  Returns the
+ * setting in effect. */
+int32_t qsim_rollout_packed(qsim_handle* h, int32_t packed);
+
 /* Autotuner: times every (warps-per-block, schedule) variant of the rollout kernel that fits
  * on this device with n_steps-step rollouts (CUDA events on `stream`; these are real env
  * steps that advance the env set), keeps the fastest for this handle and returns its warps
@@ -225,9 +231,9 @@ int32_t qsim_rollout_schedule(qsim_handle* h, int32_t parts, int32_t chunk);
 int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int32_t hidden,
                               int32_t n_steps, void* stream);
 
-/* FP32 FMA throughput probe: every thread of n_blocks x 256 runs `iters` iterations of 16
- * independent FMA chains; out[0] receives a checksum (device).  Used to confirm the FP32
- * roofline peak. */
+/* FP32 FMA throughput probe: every thread of n_blocks x 256 runs |iters| iterations of 16
+ * independent FMA chains (iters < 0: paired f32x2 FMAs, 2 per instruction); out is a
+ * device scratch word.  Used to confirm the FP32 roofline peak. */
 qsim_status qsim_ffma_probe(int32_t n_blocks, int32_t iters, float* out, void* stream);
 
 /* Recompute every stored reward from (s', a) with the current reward constants (Sec. VI

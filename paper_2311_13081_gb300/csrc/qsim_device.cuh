@@ -320,6 +320,24 @@ __device__ __forceinline__ uint32_t pack_flags(bool term, bool trunc, uint32_t e
     return (term ? 1u : 0u) | (trunc ? 2u : 0u) | (ep_step << 8);
 }
 
+// ------------------------------------------------------------- packed FP32 (f32x2) ops
+// Blackwell's paired FP32 FMA: two IEEE single-precision FMAs (round to nearest) per
+// instruction on a 64-bit register pair; element results equal fmaf's.
+__device__ __forceinline__ unsigned long long f2pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2unpack(unsigned long long v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Device status codes (first error wins).
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADSIZE = 2 };
 

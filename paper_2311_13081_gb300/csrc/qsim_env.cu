@@ -354,6 +354,29 @@ __global__ void __launch_bounds__(256) k_ffma_probe(int iters, float* out) {
     if (s == 12345.678f) out[0] = s;  // keeps the chains live
 }
 
+// Same with paired FMAs: 16 independent f32x2 chains (32 FMAs per 16 instructions).
+__global__ void __launch_bounds__(256) k_ffma2_probe(int iters, float* out) {
+    unsigned long long a[16];
+    const unsigned long long x = f2pack(1.0f + 1e-7f * (float)threadIdx.x, 1.0f),
+                             y = f2pack(0.999999f, 0.999999f);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = f2pack((float)(i + blockIdx.x), (float)i);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) a[i] = f2fma(a[i], y, x);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        float lo, hi;
+        f2unpack(a[i], lo, hi);
+        s += lo + hi;
+    }
+    if (s == 12345.678f) out[0] = s;
+}
+
 static int grid_for(int64_t n, int block) { return (int)((n + block - 1) / block); }
 
 }  // namespace qsim
@@ -478,6 +501,7 @@ extern "C" qsim_status qsim_create(const qsim_config* cfg, const qsim_params* ve
     h->rollout_warps = 0;
     h->rollout_parts = 0;
     h->rollout_chunk = 0;
+    h->rollout_packed = -1;
     h->streams_ready = false;
     cudaGetDevice(&h->device);
     const size_t ld = (size_t)h->ld;
@@ -640,8 +664,9 @@ extern "C" qsim_status qsim_stats_get(qsim_handle* h, qsim_stats* out, void* str
 }
 
 extern "C" qsim_status qsim_ffma_probe(int32_t n_blocks, int32_t iters, float* out, void* stream) {
-    if (n_blocks <= 0 || iters <= 0 || !out) return fail(QSIM_EINVAL, "qsim_ffma_probe: bad argument");
-    k_ffma_probe<<<n_blocks, 256, 0, (cudaStream_t)stream>>>(iters, out);
+    if (n_blocks <= 0 || !out || iters == 0) return fail(QSIM_EINVAL, "qsim_ffma_probe: bad argument");
+    if (iters < 0) k_ffma2_probe<<<n_blocks, 256, 0, (cudaStream_t)stream>>>(-iters, out);
+    else k_ffma_probe<<<n_blocks, 256, 0, (cudaStream_t)stream>>>(iters, out);
     QCHECK_LAUNCH("k_ffma_probe");
     return QSIM_OK;
 }

@@ -52,7 +52,7 @@ __device__ __forceinline__ int wpos(int o) {
     return (r >> 2) * 32 + ty * 4 + (r & 3);
 }
 
-template <int H, int NW>
+template <int H, int NW, bool PK>
 __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
                                                      const float* __restrict__ actor, int T,
                                                      uint32_t t0, int64_t head0,
@@ -158,6 +158,48 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
         } else {
             // ---------------- layer 1: obs (DA) -> H, ReLU
             float acc[OP][8];
+            if constexpr (PK) {
+                // paired FMAs: acc2[q][e] holds outputs (2q, 2q+1) of env e; weight pairs come
+                // straight from the 128-bit shared loads, activations are duplicated
+                unsigned long long acc2[OP / 2][8];
+#pragma unroll
+                for (int q = 0; q < OP / 2; ++q) {
+                    const unsigned long long b = f2pack(smem[L::B1 + ty * OP + 2 * q],
+                                                        smem[L::B1 + ty * OP + 2 * q + 1]);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc2[q][e] = b;
+                }
+                auto fma_row2 = [&](const float* wrow, const float* xrow) {
+                    unsigned long long w2[OP / 2];
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const float4 v = *reinterpret_cast<const float4*>(wrow + q * 32 + ty * 4);
+                        w2[2 * q] = f2pack(v.x, v.y);
+                        w2[2 * q + 1] = f2pack(v.z, v.w);
+                    }
+                    const float4 x0 = *reinterpret_cast<const float4*>(xrow + 8 * tx);
+                    const float4 x1 = *reinterpret_cast<const float4*>(xrow + 8 * tx + 4);
+                    const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const unsigned long long xb = f2pack(x[e], x[e]);
+#pragma unroll
+                        for (int q = 0; q < OP / 2; ++q) acc2[q][e] = f2fma(w2[q], xb, acc2[q][e]);
+                    }
+                };
+#pragma unroll 2
+                for (int k = 0; k < 18; ++k) fma_row2(sW1 + k * H, sObs + k * 32);
+                for (int i = 1; i <= nh; ++i) {
+                    const int base = 18 + 4 * (int)((t - (uint32_t)i) & 15u);
+                    const int kw = 18 + 4 * (i - 1);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) fma_row2(sW1 + (kw + c) * H, sObs + (base + c) * 32);
+                }
+#pragma unroll
+                for (int q = 0; q < OP / 2; ++q)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) f2unpack(acc2[q][e], acc[2 * q][e], acc[2 * q + 1][e]);
+            } else {
 #pragma unroll
             for (int i = 0; i < OP; ++i) {
                 const float b = smem[L::B1 + ty * OP + i];
@@ -187,6 +229,7 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
 #pragma unroll
                 for (int c = 0; c < 4; ++c) fma_row(sW1 + (kw + c) * H, sObs + (base + c) * 32);
             }
+            }
 #pragma unroll
             for (int i = 0; i < OP; ++i) {
                 const int o = ty * OP + i;
@@ -200,6 +243,42 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
             }
             __syncwarp();
             // ---------------- layer 2: H -> H, ReLU (in registers)
+            if constexpr (PK) {
+                unsigned long long acc2[OP / 2][8];
+#pragma unroll
+                for (int q = 0; q < OP / 2; ++q) {
+                    const unsigned long long b = f2pack(smem[L::B2 + ty * OP + 2 * q],
+                                                        smem[L::B2 + ty * OP + 2 * q + 1]);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc2[q][e] = b;
+                }
+#pragma unroll 2
+                for (int k = 0; k < H; ++k) {
+                    const float* wrow = sW2 + k * H;
+                    const float* xrow = sHid + k * 32;
+                    const int sw = (k / OP) & 7;
+                    unsigned long long w2[OP / 2];
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const float4 v = *reinterpret_cast<const float4*>(wrow + q * 32 + ty * 4);
+                        w2[2 * q] = f2pack(v.x, v.y);
+                        w2[2 * q + 1] = f2pack(v.z, v.w);
+                    }
+                    const float4 x0 = *reinterpret_cast<const float4*>(xrow + 4 * ((2 * tx) ^ sw));
+                    const float4 x1 = *reinterpret_cast<const float4*>(xrow + 4 * ((2 * tx + 1) ^ sw));
+                    const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const unsigned long long xb = f2pack(x[e], x[e]);
+#pragma unroll
+                        for (int q = 0; q < OP / 2; ++q) acc2[q][e] = f2fma(w2[q], xb, acc2[q][e]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < OP / 2; ++q)
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) f2unpack(acc2[q][e], acc[2 * q][e], acc[2 * q + 1][e]);
+            } else {
 #pragma unroll
             for (int i = 0; i < OP; ++i) {
                 const float b = smem[L::B2 + ty * OP + i];
@@ -224,6 +303,7 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
                 for (int i = 0; i < OP; ++i)
 #pragma unroll
                     for (int e = 0; e < 8; ++e) acc[i][e] = fmaf(w[i], x[e], acc[i][e]);
+            }
             }
             // ---------------- layer 3: H -> 4, partial over this lane's H/8 units
             float pp[4][8];
@@ -368,22 +448,22 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
 using RollFn = void (*)(EnvCfg, EnvPtrs, const float*, int, uint32_t, int64_t, int64_t, float,
                         int, int);
 
-template <int H>
+template <int H, bool PK>
 static RollFn pick(int nw) {
     switch (nw) {
-        case 2: return k_rollout<H, 2>;
-        case 4: return k_rollout<H, 4>;
-        case 6: return k_rollout<H, 6>;
-        case 8: return k_rollout<H, 8>;
-        case 10: return k_rollout<H, 10>;
+        case 2: return k_rollout<H, 2, PK>;
+        case 4: return k_rollout<H, 4, PK>;
+        case 6: return k_rollout<H, 6, PK>;
+        case 8: return k_rollout<H, 8, PK>;
+        case 10: return k_rollout<H, 10, PK>;
         default: return nullptr;
     }
 }
 
-static RollFn roll_fn(int hidden, int nw) {
-    if (hidden == 32) return pick<32>(nw);
-    if (hidden == 64) return pick<64>(nw);
-    if (hidden == 128) return pick<128>(nw);
+static RollFn roll_fn(int hidden, int nw, bool pk = false) {
+    if (hidden == 32) return pk ? pick<32, true>(nw) : pick<32, false>(nw);
+    if (hidden == 64) return pk ? pick<64, true>(nw) : pick<64, false>(nw);
+    if (hidden == 128) return pk ? pick<128, true>(nw) : pick<128, false>(nw);
     return nullptr;
 }
 
@@ -424,8 +504,8 @@ static int default_warps(int hidden, int ld, int device) {
     return best_nw;
 }
 
-static int resident_warps(int hidden, int nw, int device) {
-    RollFn fn = roll_fn(hidden, nw);
+static int resident_warps(int hidden, int nw, int device, bool pk = false) {
+    RollFn fn = roll_fn(hidden, nw, pk);
     int blocks = 0, sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, nw * 32, roll_smem(hidden, nw)) != cudaSuccess) {
@@ -451,15 +531,15 @@ static qsim_status ensure_streams(qsim_handle* h) {
 // own stream, chunks of different partitions are issued interleaved, and the caller's
 // stream joins all partitions at the end.
 qsim_status launch_rollout(qsim_handle* h, const float* actor, int hidden, int T, float sigma,
-                           cudaStream_t st, int nw, int parts, int chunk) {
-    RollFn fn = roll_fn(hidden, nw);
+                           cudaStream_t st, int nw, int parts, int chunk, bool pk) {
+    RollFn fn = roll_fn(hidden, nw, pk);
     if (!fn) return fail(QSIM_EINVAL, "qsim_rollout: no kernel for hidden=%d warps=%d", hidden, nw);
     const size_t smem = roll_smem(hidden, nw);
-    static bool configured[3][11] = {};
+    static bool configured[2][3][11] = {};
     const int hi = hidden == 32 ? 0 : (hidden == 64 ? 1 : 2);
-    if (!configured[hi][nw]) {
+    if (!configured[pk][hi][nw]) {
         QCHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured[hi][nw] = true;
+        configured[pk][hi][nw] = true;
     }
     const int warps = h->ld / 32;
     parts = std::max(1, std::min(parts, std::min(4, warps)));
@@ -516,14 +596,15 @@ extern "C" qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t 
     if (n_steps == 0) return QSIM_OK;
     int nw = h->rollout_warps ? h->rollout_warps : default_warps(hidden, h->ld, h->device);
     if (roll_smem(hidden, nw) > 227 * 1024) nw = 2;
+    const bool pk = h->rollout_packed > 0;
     int parts = h->rollout_parts, chunk = h->rollout_chunk;
     if (parts <= 0) {
         // more than one wave of warps: pipeline two partitions in 100-step chunks
-        parts = (h->ld / 32 > resident_warps(hidden, nw, h->device)) ? 2 : 1;
+        parts = (h->ld / 32 > resident_warps(hidden, nw, h->device, pk)) ? 2 : 1;
         chunk = parts > 1 ? 100 : 0;
     }
     qsim_status s = launch_rollout(h, actor, hidden, n_steps, sigma_e, (cudaStream_t)stream, nw,
-                                   parts, chunk);
+                                   parts, chunk, pk);
     if (s != QSIM_OK) return s;
     h->t_now += n_steps;
     if (h->capacity > 0) {
@@ -545,17 +626,20 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
     QCHECK_CUDA(cudaEventCreate(&e0));
     QCHECK_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_nw = 0, best_parts = 1, best_chunk = 0;
+    int best_nw = 0, best_parts = 1, best_chunk = 0, best_pk = 0;
     struct Sched { int parts, chunk; };
     const int tc = std::max(1, std::min(100, n_steps / 4));
     const Sched scheds[] = {{1, 0}, {2, tc}, {3, tc}, {4, tc}};
+    for (int pk = 0; pk < 2; ++pk)
     for (int nw : kWarpChoices) {
         if (roll_smem(hidden, nw) > (size_t)smem_blk) continue;
+        if (h->rollout_packed >= 0 && pk != h->rollout_packed) continue;
         for (const Sched& sc : scheds) {
             if (((h->t_now + n_steps) >> 32) != 0) break;
-            if (sc.parts > 1 && h->ld / 32 <= resident_warps(hidden, nw, h->device)) continue;
+            if (sc.parts > 1 && h->ld / 32 <= resident_warps(hidden, nw, h->device, pk)) continue;
             cudaEventRecord(e0, st);
-            qsim_status s = launch_rollout(h, actor, hidden, n_steps, -1.0f, st, nw, sc.parts, sc.chunk);
+            qsim_status s = launch_rollout(h, actor, hidden, n_steps, -1.0f, st, nw, sc.parts, sc.chunk,
+                                           pk != 0);
             cudaEventRecord(e1, st);
             if (s != QSIM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
             h->t_now += n_steps;
@@ -566,7 +650,7 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
             cudaEventSynchronize(e1);
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_nw = nw; best_parts = sc.parts; best_chunk = sc.chunk; }
+            if (ms < best) { best = ms; best_nw = nw; best_parts = sc.parts; best_chunk = sc.chunk; best_pk = pk; }
         }
     }
     cudaEventDestroy(e0);
@@ -576,9 +660,16 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
         h->rollout_warps = best_nw;
         h->rollout_parts = best_parts;
         h->rollout_chunk = best_parts > 1 ? 100 : 0;
+        h->rollout_packed = best_pk;
         (void)best_chunk;
     }
     return best_nw;
+}
+
+extern "C" int32_t qsim_rollout_packed(qsim_handle* h, int32_t packed) {
+    if (!h) return 0;
+    if (packed >= -1 && packed <= 1) h->rollout_packed = packed;
+    return h->rollout_packed;
 }
 
 extern "C" int32_t qsim_rollout_schedule(qsim_handle* h, int32_t parts, int32_t chunk) {

@@ -274,3 +274,26 @@ def test_partitioned_schedule_is_bitwise_identical(gpu):
     for o in outs[1:]:
         for x, y in zip(o, outs[0]):
             assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+
+
+@pytest.mark.parametrize("hidden", [32, 64, 128])
+def test_packed_fma_kernel_is_bitwise_identical(gpu, hidden):
+    """The paired-FMA (f32x2) rollout variant performs the same IEEE FMAs in the same order
+    as the scalar variant: results must match bit for bit."""
+    q = gpu
+    n = 3000
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=12, learning_starts=2,
+                             sig_p=0.01, sig_v=0.01)
+    A = torch.tensor(_actor(d, hidden), device="cuda")
+    outs = []
+    for packed in (0, 1):
+        h = q.qsim_create(cfg, veh)
+        q.qsim_rollout_packed(h, packed)
+        q.qsim_rollout_tune(h, 2 if hidden == 128 else 4)
+        q.qsim_rollout(h, A, hidden, 20, 0.1)
+        torch.cuda.synchronize()
+        info = q.qsim_info_get(h)
+        outs.append([cpu(info[k]).copy() for k in ("records", "side", "state", "hist")])
+        q.qsim_destroy(h)
+    for x, y in zip(outs[0], outs[1]):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
