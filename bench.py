@@ -39,7 +39,7 @@ BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, fl
 # DRAM bytes per env-step of k_rollout<64,*> measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum, 32,768 envs x 100 steps; profiles/k_rollout_c2_65536x1000.md).
 # Set to None whenever the kernel changes until it is captured again.
-NCU_DRAM_BYTES_PER_ENV_STEP = None  # kernel changed since the last capture
+NCU_DRAM_BYTES_PER_ENV_STEP = (46.710016e6 + 289.403648e6) / (32768 * 100)
 
 
 def parse():
