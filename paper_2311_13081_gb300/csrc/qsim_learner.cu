@@ -24,12 +24,15 @@
 #include <cooperative_groups.h>
 
 #include "qsim_gemm.cuh"
+#include "qsim_smlp.cuh"
 #include "qsim_internal.h"
 
 namespace cg = cooperative_groups;
 
 namespace qsim {
 
+
+constexpr int SMEM_MAIN = GEMM_SMEM > smlp::floats() ? GEMM_SMEM : smlp::floats();
 
 struct LearnHyper {
     float gamma, tau, lr, beta1, beta2, eps, sigma_t, noise_clip;
@@ -191,6 +194,72 @@ __device__ __forceinline__ void load_env(const RunDesc& R, int e, float* s, floa
                  ldcg(pr + 4 * ld + e), ldcg(pr + 5 * ld + e), ldcg(pr + 6 * ld + e));
 }
 
+// Actor forward for a handful of rows (n <= 8, hidden <= 64, input <= 128): one warp per
+// output unit, lanes split the inputs, every weight load of a warp in flight at once, rows
+// reduced with warp shuffles.  x, h: shared memory; the tanh outputs go to Y (global [n][4]).
+template <int JT, int KC>
+__device__ __forceinline__ void small_layer(const float* Wl, const float* bl, int in, int nout,
+                                            const float* x, int ldx, int n, float* y, int ldy,
+                                            bool last) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float w[JT][KC], bv[JT];
+#pragma unroll
+    for (int t = 0; t < JT; ++t) {
+        const int j = warp + (LT / 32) * t;
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+            const int k = lane + 32 * c;
+            w[t][c] = j < nout && k < in ? ldcg(Wl + (size_t)j * in + k) : 0.0f;
+        }
+        bv[t] = j < nout ? ldcg(bl + j) : 0.0f;
+    }
+    for (int r = 0; r < n; ++r) {
+        float xv[KC];
+#pragma unroll
+        for (int c = 0; c < KC; ++c) xv[c] = lane + 32 * c < in ? x[r * ldx + lane + 32 * c] : 0.0f;
+#pragma unroll
+        for (int t = 0; t < JT; ++t) {
+            const int j = warp + (LT / 32) * t;
+            if (j >= nout) continue;
+            float acc = 0.0f;
+#pragma unroll
+            for (int c = 0; c < KC; ++c) acc = fmaf(w[t][c], xv[c], acc);
+            acc = smlp::warp_sum(acc) + bv[t];
+            if (lane == 0) y[r * ldy + j] = last ? tanhf(acc) : fmaxf(acc, 0.0f);
+        }
+    }
+}
+
+__device__ __noinline__ void actor_small(const float* W, int in, int H, const float* X, int n,
+                                         float* Y, float* sm) {
+    constexpr int LX = 132, LH = 68;
+    float* xs = sm;
+    float* h1 = xs + 8 * LX;
+    float* h2 = h1 + 8 * LH;
+    for (int i = threadIdx.x; i < n * in; i += LT) xs[(i / in) * LX + i % in] = ldcg(X + i);
+    __syncthreads();
+    const float* b1 = W + (size_t)H * in;
+    const float* W2 = b1 + H;
+    const float* b2 = W2 + (size_t)H * H;
+    const float* W3 = b2 + H;
+    const float* b3 = W3 + 4 * H;
+    small_layer<8, 4>(W, b1, in, H, xs, LX, n, h1, LH, false);
+    __syncthreads();
+    small_layer<8, 2>(W2, b2, H, H, h1, LH, n, h2, LH, false);
+    __syncthreads();
+    small_layer<1, 2>(W3, b3, H, 4, h2, LH, n, Y, 4, true);
+    __syncthreads();
+}
+
+// Actor forward of n rows through the shared-memory engine (hidden <= 64).
+__device__ __noinline__ void actor_smem(const float* W, int in, int H, const float* X, int n,
+                                        float* Y, float* sm) {
+    const smlp::Buf b = smlp::carve(sm);
+    smlp::stage(W, in, H, 4, b);
+    for (int r0 = 0; r0 < n; r0 += smlp::MC)
+        smlp::forward(in, H, 4, X, in, r0, min(smlp::MC, n - r0), b, Y, 4, true);
+}
+
 // One env step of all envs of run R (executed by one CTA): observation, actor forward
 // (generic GEMM path), warm-up / exploration, RK4, reward, termination, record write,
 // history update and reset.
@@ -213,10 +282,27 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
             float* row = S.env_obs + (size_t)e * DA;
 #pragma unroll
             for (int k = 0; k < 18; ++k) row[k] = o[k];
-            for (int k = 0; k < 4 * C.n_hist; ++k) row[18 + k] = ldcg(R.E.hist + k * ld + e);
+            // history loads in two halves, each all in flight before its stores
+            const int nh4 = 4 * C.n_hist;
+#pragma unroll 1
+            for (int h0 = 0; h0 < 4 * HMAX; h0 += 2 * HMAX) {
+                float hv[2 * HMAX];
+#pragma unroll
+                for (int k = 0; k < 2 * HMAX; ++k)
+                    hv[k] = h0 + k < nh4 ? ldcg(R.E.hist + (h0 + k) * ld + e) : 0.0f;
+#pragma unroll
+                for (int k = 0; k < 2 * HMAX; ++k)
+                    if (h0 + k < nh4) row[18 + h0 + k] = hv[k];
+            }
         }
         __syncthreads();
-        mlp_fwd(R.actor, DA, H, 4, S.env_obs, DA, n, S.env_h1, S.env_h2, S.env_mu, 4, true, sm);
+        if (n <= 8 && H <= 64 && DA <= 128) {
+            actor_small(R.actor, DA, H, S.env_obs, n, S.env_mu, sm);
+        } else if (H <= smlp::HP && DA <= smlp::INP) {
+            actor_smem(R.actor, DA, H, S.env_obs, n, S.env_mu, sm);
+        } else {
+            mlp_fwd(R.actor, DA, H, 4, S.env_obs, DA, n, S.env_h1, S.env_h2, S.env_mu, 4, true, sm);
+        }
     }
     const float sigma = ldcg(R.E.rewardC + 7);
     float Cr[7];
@@ -226,6 +312,9 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
         float s[NS], d[6], a[4];
         Prm P;
         load_env(R, e, s, d, P);
+        // episode counters: loads in flight across the integration
+        const uint32_t ep_step = ldcg(R.E.ep_step + e);
+        const float ret0 = ldcg(R.E.ep_ret + e);
         if (warm) {
             const uint4 r = draw(C, (uint32_t)e, t, TAG_WARM, 0);
             a[0] = 2.0f * u01(r.x) - 1.0f; a[1] = 2.0f * u01(r.y) - 1.0f;
@@ -253,7 +342,6 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
         rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
         const float r = reward(Cr, s2, a);
         const bool term = terminated(C, s2);
-        const uint32_t ep_step = ldcg(R.E.ep_step + e);
         const uint32_t ep_after = ep_step + 1;
         const bool trunc = !term && (int)ep_after >= C.episode_len;
         if (R.capacity > 0) {
@@ -276,12 +364,26 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
                 for (int i = 0; i < NS; ++i) sd[i * ld] = s2[i];
             }
         }
-        for (int i = C.n_hist - 1; i >= 1; --i)
-            for (int c = 0; c < 4; ++c)
-                R.E.hist[(4 * i + c) * ld + e] = ldcg(R.E.hist + (4 * (i - 1) + c) * ld + e);
-        if (C.n_hist > 0)
-            for (int c = 0; c < 4; ++c) R.E.hist[c * ld + e] = a[c];
-        float ret = ldcg(R.E.ep_ret + e) + r;
+        {
+            // shift the history (newest first) in two halves, the older half first so that
+            // no entry is overwritten before it has been loaded: entries [h0, h0 + 30) move
+            // to [h0 + 4, h0 + 34)
+            const int nh4 = 4 * C.n_hist;
+            constexpr int HH = 2 * HMAX - 2;
+#pragma unroll 1
+            for (int h0 = HH; h0 >= 0; h0 -= HH) {
+                float hv[HH];
+#pragma unroll
+                for (int k = 0; k < HH; ++k)
+                    hv[k] = h0 + k + 4 < nh4 ? ldcg(R.E.hist + (h0 + k) * ld + e) : 0.0f;
+#pragma unroll
+                for (int k = 0; k < HH; ++k)
+                    if (h0 + k + 4 < nh4) R.E.hist[(h0 + k + 4) * ld + e] = hv[k];
+            }
+            if (C.n_hist > 0)
+                for (int c = 0; c < 4; ++c) R.E.hist[c * ld + e] = a[c];
+        }
+        float ret = ret0 + r;
         uint32_t eps = ep_after;
         if (term || trunc) {
             R.E.n_done[e] = ldcg(R.E.n_done + e) + 1;
@@ -311,105 +413,141 @@ __device__ __forceinline__ int64_t pmod64(int64_t a, int64_t m) {
     return r < 0 ? r + m : r;
 }
 
-// Gather one sample: rebuilds o_a, o_a', o_c (with stored action), o_c' (action slot
-// filled later), r and the termination flag from the compact replay records.
-__device__ __noinline__ void gather_sample(const RunDesc& R, int j, uint32_t u, int64_t head, int64_t size,
-                              int64_t t_now, const Scr& S, int jl) {
+// Ring index a mod m for a in [-m, 2m).
+__device__ __forceinline__ int64_t ring(int64_t a, int64_t m) {
+    return a < 0 ? a + m : (a >= m ? a - m : a);
+}
+
+// Gather samples [g0, g0 + G) (G <= 32) of this CTA's share of the minibatch: rebuilds o_a,
+// o_a', o_c (with the stored action), o_c' (action slot filled later), r and the
+// termination flag from the compact replay records.  Lane l handles sample g0 + l; warp 0
+// builds the s_t part, warp 1 the s_{t+1} part and warps 2..7 the action history, each
+// into a shared-memory tile laid out like the scratch rows, which is then written out with
+// coalesced stores.
+__device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int G, uint32_t u,
+                                          int64_t head, int64_t size, int64_t t_now, const Scr& S,
+                                          float* tile) {
     const EnvCfg& C = R.C;
-    const int ld = C.ld, F = C.F, NE = R.n_env, DA = R.DA, DC = R.DC;
+    const int ld = C.ld, F = C.F, NE = R.n_env, DA = R.DA, DC = R.DC, nh = C.n_hist;
     const int64_t CAP = R.capacity;
-    const int64_t lost = size == CAP ? C.n_hist : 0;
-    const uint32_t nvalid = (uint32_t)((size - 1 - lost) * NE);
-    const uint4 rr = draw(C, (uint32_t)j >> 2, u, TAG_REPLAY, 0);
-    const uint32_t x = (j & 3) == 0 ? rr.x : ((j & 3) == 1 ? rr.y : ((j & 3) == 2 ? rr.z : rr.w));
-    const uint32_t idx = (uint32_t)(((uint64_t)x * (uint64_t)nvalid) >> 32);
-    const int64_t k = idx / (uint32_t)NE;
-    const int env = (int)(idx % (uint32_t)NE);
-    const int64_t slot = pmod64(head - size + lost + k, CAP);
-    const uint32_t t_rec = (uint32_t)(t_now - size + lost + k);
-    const float* rec = R.E.rec + (size_t)slot * F * ld + env;
-    const uint32_t fl = __float_as_uint(ldcg(rec + 22 * ld));
-    const bool done = (fl & 3u) != 0;
-    const uint32_t ep = fl >> 8;
-    float s[NS], s2[NS], a[4], pv[NPRIV];
+    const int w = threadIdx.x >> 5, jl = threadIdx.x & 31;
+    float* T_oa = tile;
+    float* T_oa2 = T_oa + (size_t)G * DA;
+    float* T_oc = T_oa2 + (size_t)G * DA;
+    float* T_oc2 = T_oc + (size_t)G * DC;
+    float* T_r = T_oc2 + (size_t)G * DC;
+    float* T_term = T_r + G;
+    if (jl < G) {
+        const int j = j0 + g0 + jl;
+        const int64_t lost = size == CAP ? nh : 0;
+        const uint32_t nvalid = (uint32_t)((size - 1 - lost) * NE);
+        const uint4 rr = draw(C, (uint32_t)j >> 2, u, TAG_REPLAY, 0);
+        const uint32_t x = (j & 3) == 0 ? rr.x : ((j & 3) == 1 ? rr.y : ((j & 3) == 2 ? rr.z : rr.w));
+        const uint32_t idx = (uint32_t)(((uint64_t)x * (uint64_t)nvalid) >> 32);
+        const int64_t k = idx / (uint32_t)NE;
+        const int env = (int)(idx % (uint32_t)NE);
+        const int64_t slot = ring(head - size + lost + k, CAP);
+        const uint32_t t_rec = (uint32_t)(t_now - size + lost + k);
+        const float* rec = R.E.rec + (size_t)slot * F * ld + env;
+        const uint32_t fl = __float_as_uint(ldcg(rec + 22 * ld));
+        const bool done = (fl & 3u) != 0;
+        const uint32_t ep = fl >> 8;
+        float* oa = T_oa + (size_t)jl * DA;
+        float* oa2 = T_oa2 + (size_t)jl * DA;
+        float* oc = T_oc + (size_t)jl * DC;
+        float* oc2 = T_oc2 + (size_t)jl * DC;
+        if (w < 2) {
+            // w == 0: s_t -> o_a, o_c (+ stored action, reward, flag); w == 1: s_{t+1} -> o_a', o_c'
+            const float* src = w == 0 ? rec
+                                      : (done ? R.E.side + (size_t)slot * NS * ld + env
+                                              : R.E.rec + (size_t)ring(slot + 1, CAP) * F * ld + env);
+            float st[NS], a[4], pv[NPRIV];
 #pragma unroll
-    for (int i = 0; i < NS; ++i) s[i] = ldcg(rec + i * ld);
+            for (int i = 0; i < NS; ++i) st[i] = ldcg(src + i * ld);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = ldcg(rec + (17 + i) * ld);
+            for (int i = 0; i < 4; ++i) a[i] = w == 0 ? ldcg(rec + (17 + i) * ld) : 0.0f;
 #pragma unroll
-    for (int k2 = 0; k2 < NPRIV; ++k2) pv[k2] = 0.0f;
-    if (C.n_priv) {
+            for (int q = 0; q < NPRIV; ++q) pv[q] = C.n_priv ? ldcg(rec + (23 + q) * ld) : 0.0f;
+            const float r = w == 0 ? ldcg(rec + 21 * ld) : 0.0f;
+            float* ocx = w == 0 ? oc : oc2;
+            float* oax = w == 0 ? oa : oa2;
+            float o[18];
+            obs_state(st, o);
+            // critic observations (noise-free)
 #pragma unroll
-        for (int k2 = 0; k2 < NPRIV; ++k2) pv[k2] = ldcg(rec + (23 + k2) * ld);
-    }
-    const float* src2 = done ? R.E.side + (size_t)slot * NS * ld + env
-                             : R.E.rec + (size_t)pmod64(slot + 1, CAP) * F * ld + env;
+            for (int q = 0; q < 18; ++q) ocx[q] = o[q];
+            const int rpm_at = C.critic_layout == 2 ? 18 : DA;
 #pragma unroll
-    for (int i = 0; i < NS; ++i) s2[i] = ldcg(src2 + i * ld);
-    float* oa = S.oa + (size_t)jl * DA;
-    float* oa2 = S.oa2 + (size_t)jl * DA;
-    float* oc = S.oc + (size_t)jl * DC;
-    float* oc2 = S.oc2 + (size_t)jl * DC;
-    float o[18], o2[18];
-    obs_state(s, o);
-    obs_state(s2, o2);
-    // critic observations (noise-free)
-    if (C.critic_layout == 2) {
+            for (int i = 0; i < 4; ++i) ocx[rpm_at + i] = rpm_norm(C.veh, st[13 + i]);
+            if (C.critic_layout != 0) {
 #pragma unroll
-        for (int q = 0; q < 18; ++q) { oc[q] = o[q]; oc2[q] = o2[q]; }
+                for (int q = 0; q < 6; ++q) ocx[rpm_at + 4 + q] = pv[q];
+            }
+            if (w == 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { oc[18 + i] = rpm_norm(C.veh, s[13 + i]); oc2[18 + i] = rpm_norm(C.veh, s2[13 + i]); }
+                for (int i = 0; i < 4; ++i) oc[DC - 4 + i] = a[i];
+                T_r[jl] = r;
+                T_term[jl] = (fl & 1u) ? 1.0f : 0.0f;
+            }
+            if (C.any_noise) {
+                float nz[18];
+                obs_noise(C, (uint32_t)env, t_rec + (uint32_t)w, nz);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) { oc[22 + q] = pv[q]; oc2[22 + q] = pv[q]; }
-    } else {
+                for (int q = 0; q < 18; ++q) o[q] += nz[q];
+            }
 #pragma unroll
-        for (int q = 0; q < 18; ++q) { oc[q] = o[q]; oc2[q] = o2[q]; }
+            for (int q = 0; q < 18; ++q) oax[q] = o[q];
+        } else {
+            // history: o_a has a_{t-1..t-NH}, o_a' has a_t, a_{t-1..t-NH+1}; zeros before the
+            // episode start.  Warp w handles lags i = w-1, w+5, w+11.
+            for (int i = w - 1; i <= nh; i += 6) {
+                const bool ok = (uint32_t)i <= ep;
+                const bool ok2 = i == 1 || (uint32_t)(i - 1) <= ep;
+                const float* ap = R.E.rec + (size_t)ring(slot - i, CAP) * F * ld + env + 17 * ld;
+                const float* ap2 = i == 1 ? rec + 17 * ld
+                                          : R.E.rec + (size_t)ring(slot - i + 1, CAP) * F * ld + env + 17 * ld;
+                float h[4], h2[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { oc[DA + i] = rpm_norm(C.veh, s[13 + i]); oc2[DA + i] = rpm_norm(C.veh, s2[13 + i]); }
-        if (C.critic_layout == 1)
+                for (int c = 0; c < 4; ++c) {
+                    h[c] = ok ? ldcg(ap + c * ld) : 0.0f;
+                    h2[c] = ok2 ? ldcg(ap2 + c * ld) : 0.0f;
+                }
 #pragma unroll
-            for (int q = 0; q < 6; ++q) { oc[DA + 4 + q] = pv[q]; oc2[DA + 4 + q] = pv[q]; }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) oc[DC - 4 + i] = a[i];
-    // history: o_a has a_{t-1..t-NH}; o_a' has a_t, a_{t-1..t-NH+1}; zeros before the
-    // episode start
-    for (int i = 1; i <= C.n_hist; ++i) {
-        float h[4] = {0, 0, 0, 0}, h2[4] = {0, 0, 0, 0};
-        if ((uint32_t)i <= ep) {
-            const float* ap = R.E.rec + (size_t)pmod64(slot - i, CAP) * F * ld + env + 17 * ld;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) h[c] = ldcg(ap + c * ld);
-        }
-        if (i == 1) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) h2[c] = a[c];
-        } else if ((uint32_t)(i - 1) <= ep) {
-            const float* ap = R.E.rec + (size_t)pmod64(slot - (i - 1), CAP) * F * ld + env + 17 * ld;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) h2[c] = ldcg(ap + c * ld);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            oa[18 + 4 * (i - 1) + c] = h[c];
-            oa2[18 + 4 * (i - 1) + c] = h2[c];
-            if (C.critic_layout != 2) {
-                oc[18 + 4 * (i - 1) + c] = h[c];
-                oc2[18 + 4 * (i - 1) + c] = h2[c];
+                for (int c = 0; c < 4; ++c) {
+                    const int q = 18 + 4 * (i - 1) + c;
+                    oa[q] = h[c];
+                    oa2[q] = h2[c];
+                    if (C.critic_layout != 2) {
+                        oc[q] = h[c];
+                        oc2[q] = h2[c];
+                    }
+                }
             }
         }
     }
-    if (C.any_noise) {
-        float n1[18], n2[18];
-        obs_noise(C, (uint32_t)env, t_rec, n1);
-        obs_noise(C, (uint32_t)env, t_rec + 1, n2);
-#pragma unroll
-        for (int q = 0; q < 18; ++q) { o[q] += n1[q]; o2[q] += n2[q]; }
+    __syncthreads();
+    // coalesced write-out of the six scratch ranges of this group
+    const int n1 = G * DA, n2 = G * DC;
+    for (int i = threadIdx.x; i < n1; i += LT) {
+        S.oa[(size_t)g0 * DA + i] = T_oa[i];
+        S.oa2[(size_t)g0 * DA + i] = T_oa2[i];
     }
-#pragma unroll
-    for (int q = 0; q < 18; ++q) { oa[q] = o[q]; oa2[q] = o2[q]; }
-    S.r[jl] = ldcg(rec + 21 * ld);
-    S.term[jl] = (fl & 1u) ? 1.0f : 0.0f;
+    for (int i = threadIdx.x; i < n2; i += LT) {
+        S.oc[(size_t)g0 * DC + i] = T_oc[i];
+        S.oc2[(size_t)g0 * DC + i] = T_oc2[i];
+    }
+    if (threadIdx.x < G) {
+        S.r[g0 + threadIdx.x] = T_r[threadIdx.x];
+        S.term[g0 + threadIdx.x] = T_term[threadIdx.x];
+    }
+    __syncthreads();
+}
+
+// Gather of this CTA's Bc samples in groups of 32 (tile: shared memory, free at this point).
+__device__ __forceinline__ void gather_all(const RunDesc& R, int j0, int Bc, uint32_t u,
+                                           int64_t head, int64_t size, int64_t t_now,
+                                           const Scr& S, float* sm) {
+    for (int g0 = 0; g0 < Bc; g0 += 32) gather_group(R, j0, g0, min(32, Bc - g0), u, head, size, t_now, S, sm);
 }
 
 __device__ void adam_slice(float* th, const float* gpart_base, size_t part_stride, int S,
@@ -417,20 +555,61 @@ __device__ void adam_slice(float* th, const float* gpart_base, size_t part_strid
                            const LearnHyper& hp, float gscale) {
     const float bc1 = 1.0f - powf(hp.beta1, (float)t);
     const float bc2 = 1.0f - powf(hp.beta2, (float)t);
-    for (int i = lo + threadIdx.x; i < hi; i += LT) {
-        float g = 0.0f;
-        for (int s = 0; s < S; ++s) g += ldcg(gpart_base + (size_t)s * part_stride + goff + i);
-        g *= gscale;
-        const float mi = fmaf(hp.beta1, m[i], (1.0f - hp.beta1) * g);
-        const float vi = fmaf(hp.beta2, v[i], (1.0f - hp.beta2) * g * g);
-        m[i] = mi;
-        v[i] = vi;
-        th[i] -= hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + hp.eps);
+    // U elements per thread per pass, all their loads issued before the arithmetic; each
+    // element's partial sum keeps the fixed order s = 0..S-1
+    constexpr int U = 4;
+    for (int i0 = lo + threadIdx.x; i0 < hi; i0 += U * LT) {
+        float g[U], mo[U], vo[U], to[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int i = i0 + k * LT;
+            g[k] = 0.0f; mo[k] = 0.0f; vo[k] = 0.0f; to[k] = 0.0f;
+            if (i < hi) { mo[k] = m[i]; vo[k] = v[i]; to[k] = th[i]; }
+        }
+        // partials in batches of 8 (8 x U loads in flight), summed in the order s = 0..S-1
+        for (int s0 = 0; s0 < S; s0 += 8) {
+            float x[8][U];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float* gp = gpart_base + (size_t)(s0 + q) * part_stride + goff;
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    x[q][k] = s0 + q < S && i0 + k * LT < hi ? ldcg(gp + i0 + k * LT) : 0.0f;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    if (s0 + q < S) g[k] += x[q][k];
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int i = i0 + k * LT;
+            if (i >= hi) continue;
+            const float gk = g[k] * gscale;
+            const float mi = fmaf(hp.beta1, mo[k], (1.0f - hp.beta1) * gk);
+            const float vi = fmaf(hp.beta2, vo[k], (1.0f - hp.beta2) * gk * gk);
+            m[i] = mi;
+            v[i] = vi;
+            th[i] = to[k] - hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + hp.eps);
+        }
     }
 }
 
 __device__ void polyak_slice(float* tg, const float* src, int lo, int hi, float tau) {
-    for (int i = lo + threadIdx.x; i < hi; i += LT) tg[i] = fmaf(tau, ldcg(src + i), (1.0f - tau) * tg[i]);
+    constexpr int U = 4;
+    for (int i0 = lo + threadIdx.x; i0 < hi; i0 += U * LT) {
+        float a[U], b[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int i = i0 + k * LT;
+            a[k] = i < hi ? ldcg(src + i) : 0.0f;
+            b[k] = i < hi ? tg[i] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (i0 + k * LT < hi) tg[i0 + k * LT] = fmaf(tau, a[k], (1.0f - tau) * b[k]);
+    }
 }
 
 // Block-wide sum of v over threads (fixed order).
@@ -454,7 +633,7 @@ __device__ __noinline__ void td3_update(RunDesc& R, int64_t head, int64_t size, 
     const LearnHyper& hp = R.hp;
     const int j0 = rk * Bc;
     // a9: gather
-    for (int jl = threadIdx.x; jl < Bc; jl += LT) gather_sample(R, j0 + jl, u, head, size, t_now, S, jl);
+    gather_all(R, j0, Bc, u, head, size, t_now, S, sm);
     __syncthreads();
     // a10: target actor + smoothing
     mlp_fwd(R.actor_t, DA, H, 4, S.oa2, DA, Bc, S.X1, S.X2, S.mu, 4, true, sm);
@@ -487,7 +666,7 @@ __device__ __noinline__ void td3_update(RunDesc& R, int64_t head, int64_t size, 
         S.da[jl] = 2.0f * e2 / (float)B;
         lsum += (e1 * e1 + e2 * e2) / (float)B;
     }
-    lsum = block_sum(lsum, sm);
+    lsum = block_sum(lsum, sm + SMEM_MAIN);
     if (threadIdx.x == 0) S.loss[0] = lsum;
     __syncthreads();
     mlp_bwd(R.c1, DC, H, 1, S.oc, DC, Bc, S.H1a, S.H2a, S.dz3, S.dZ2, S.dZ1, S.g1, nullptr, 0, sm);
@@ -522,7 +701,7 @@ __device__ __noinline__ void td3_update(RunDesc& R, int64_t head, int64_t size, 
         S.dz3[jl] = -1.0f / (float)B;
         qs += -S.q1[jl] / (float)B;
     }
-    qs = block_sum(qs, sm);
+    qs = block_sum(qs, sm + SMEM_MAIN);
     if (threadIdx.x == 0) S.loss[1] = qs;
     __syncthreads();
     // dQ1/d(input) restricted to the action columns [DC-4, DC) -> dX stored in oc2 rows
@@ -544,6 +723,147 @@ __device__ __noinline__ void td3_update(RunDesc& R, int64_t head, int64_t size, 
         if (rk == 0 && threadIdx.x == 0) {
             float l = 0.0f;
             for (int s = 0; s < nS; ++s) l += ldcg(cl0 + (size_t)s * scr_stride + (S.loss - scr_base) + 1);
+            R.stats[1] = l;
+        }
+        __syncthreads();
+        polyak_slice(R.actor_t, R.actor, lo, hi, hp.tau);
+        const int clo = (int)((int64_t)PC * rk / nS), chi = (int)((int64_t)PC * (rk + 1) / nS);
+        polyak_slice(R.c1_t, R.c1, clo, chi, hp.tau);
+        polyak_slice(R.c2_t, R.c2, clo, chi, hp.tau);
+    }
+    cluster_sync_all(nS);
+}
+
+// One TD3 update with every network pass resident in shared memory (hidden <= 64): same
+// phases and cluster reduction as td3_update.  HT/DAT/DCT fix the hidden width and the
+// actor/critic input widths at compile time (0: taken from the run descriptor), so that the
+// common shapes get fully unrolled shared-memory GEMMs.
+template <int HT, int DAT, int DCT>
+__device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t size, int64_t t_now,
+                                             uint32_t u, int64_t& t_a, int64_t& t_c, const Scr& S,
+                                             float* scr_base, size_t scr_stride, int rk, int nS,
+                                             float* sm) {
+    using namespace smlp;
+    const int B = R.B, Bc = B / nS, PA = R.PA, PC = R.PC;
+    const int H = HT ? HT : R.H, DA = DAT ? DAT : R.DA, DC = DCT ? DCT : R.DC;
+    const LearnHyper& hp = R.hp;
+    const int j0 = rk * Bc;
+    const Buf b = carve(sm);
+    float* red = sm + SMEM_MAIN;
+    // a9: gather
+    gather_all(R, j0, Bc, u, head, size, t_now, S, sm);
+    __syncthreads();
+    // a10: target actor + smoothing
+    stage(R.actor_t, DA, H, 4, b);
+    for (int r0 = 0; r0 < Bc; r0 += MC) forward(DA, H, 4, S.oa2, DA, r0, min(MC, Bc - r0), b, S.mu, 4, true);
+    for (int jl = threadIdx.x; jl < Bc; jl += LT) {
+        const uint32_t j = (uint32_t)(j0 + jl);
+        const uint4 r0 = draw(R.C, j, u, TAG_SMOOTH, 0), r1 = draw(R.C, j, u, TAG_SMOOTH, 1);
+        const float z[4] = {gauss(r0.x, r0.y), gauss(r0.z, r0.w), gauss(r1.x, r1.y), gauss(r1.z, r1.w)};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float eps = clampf(hp.sigma_t * z[i], -hp.noise_clip, hp.noise_clip);
+            S.oc2[(size_t)jl * DC + DC - 4 + i] = clampf(S.mu[jl * 4 + i] + eps, -1.0f, 1.0f);
+        }
+    }
+    __syncthreads();
+    // a11: twin target critics
+    stage(R.c1_t, DC, H, 1, b);
+    for (int r0 = 0; r0 < Bc; r0 += MC) forward(DC, H, 1, S.oc2, DC, r0, min(MC, Bc - r0), b, S.q1, 1, false);
+    stage(R.c2_t, DC, H, 1, b);
+    for (int r0 = 0; r0 < Bc; r0 += MC) forward(DC, H, 1, S.oc2, DC, r0, min(MC, Bc - r0), b, S.q2, 1, false);
+    for (int jl = threadIdx.x; jl < Bc; jl += LT) {
+        const float qmin = fminf(S.q1[jl], S.q2[jl]);
+        S.y[jl] = S.r[jl] + (S.term[jl] != 0.0f ? 0.0f : hp.gamma * qmin);
+    }
+    __syncthreads();
+    // a12: critic regression, forward + backward chunk by chunk
+    float lsum = 0.0f;
+    for (int c = 0; c < 2; ++c) {
+        const float* W = c ? R.c2 : R.c1;
+        float* q = c ? S.q2 : S.q1;
+        stage(W, DC, H, 1, b);
+        for (int r0 = 0; r0 < Bc; r0 += MC) {
+            const int mc = min(MC, Bc - r0);
+            forward(DC, H, 1, S.oc, DC, r0, mc, b, q, 1, false);
+            for (int r = threadIdx.x; r < mc; r += LT) {
+                const float e = q[r0 + r] - S.y[r0 + r];
+                b.dZ3s[r * 4] = 2.0f * e / (float)B;
+                lsum += e * e / (float)B;
+            }
+            __syncthreads();
+            backward(DC, H, 1, r0, mc, b, r0 == 0, true, nullptr, 0, 0);
+        }
+        store_grads(c ? S.g2 : S.g1, DC, H, 1, b);
+    }
+    lsum = block_sum(lsum, red);
+    if (threadIdx.x == 0) S.loss[0] = lsum;
+    __syncthreads();
+    cluster_sync_all(nS);
+    // a14 (critics): reduce the partials over the cluster and apply Adam to this slice
+    t_c += 1;
+    {
+        const size_t g1off = (size_t)(S.g1 - scr_base), g2off = (size_t)(S.g2 - scr_base);
+        const float* cl0 = scr_base - (size_t)rk * scr_stride;
+        const int lo = (int)((int64_t)PC * rk / nS), hi = (int)((int64_t)PC * (rk + 1) / nS);
+        adam_slice(R.c1, cl0, scr_stride, nS, (int)g1off, R.m_c1, R.v_c1, lo, hi, t_c, hp, 1.0f);
+        adam_slice(R.c2, cl0, scr_stride, nS, (int)g2off, R.m_c2, R.v_c2, lo, hi, t_c, hp, 1.0f);
+        if (rk == 0 && threadIdx.x == 0) {
+            float l = 0.0f;
+            for (int s2 = 0; s2 < nS; ++s2) l += ldcg(cl0 + (size_t)s2 * scr_stride + (S.loss - scr_base));
+            R.stats[0] = l;
+        }
+    }
+    cluster_sync_all(nS);
+    // a13: delayed actor update through the updated first critic
+    if ((int64_t)(u % (uint32_t)hp.policy_delay) != (int64_t)(hp.policy_delay - 1)) return;
+    stage(R.actor, DA, H, 4, b);
+    for (int r0 = 0; r0 < Bc; r0 += MC) forward(DA, H, 4, S.oa, DA, r0, min(MC, Bc - r0), b, S.mu, 4, true);
+    for (int i = threadIdx.x; i < Bc * 4; i += LT) {
+        const int jl = i >> 2, c = i & 3;
+        S.oc[(size_t)jl * DC + DC - 4 + c] = S.mu[i];
+    }
+    __syncthreads();
+    stage(R.c1, DC, H, 1, b);
+    float qs = 0.0f;
+    for (int r0 = 0; r0 < Bc; r0 += MC) {
+        const int mc = min(MC, Bc - r0);
+        forward(DC, H, 1, S.oc, DC, r0, mc, b, S.q1, 1, false);
+        for (int r = threadIdx.x; r < mc; r += LT) {
+            b.dZ3s[r * 4] = -1.0f / (float)B;
+            qs += -S.q1[r0 + r] / (float)B;
+        }
+        __syncthreads();
+        // dQ1/d(action columns) -> oc2 rows
+        backward(DC, H, 1, r0, mc, b, false, false, S.oc2, DC, DC - 4);
+    }
+    qs = block_sum(qs, red);
+    if (threadIdx.x == 0) S.loss[1] = qs;
+    for (int i = threadIdx.x; i < Bc * 4; i += LT) {
+        const int jl = i >> 2, c = i & 3;
+        const float m = S.mu[i];
+        S.da[i] = S.oc2[(size_t)jl * DC + DC - 4 + c] * (1.0f - m * m);
+    }
+    __syncthreads();
+    stage(R.actor, DA, H, 4, b);
+    for (int r0 = 0; r0 < Bc; r0 += MC) {
+        const int mc = min(MC, Bc - r0);
+        forward(DA, H, 4, S.oa, DA, r0, mc, b, S.mu, 4, true);
+        for (int i = threadIdx.x; i < mc * 4; i += LT) b.dZ3s[i] = S.da[r0 * 4 + i];
+        __syncthreads();
+        backward(DA, H, 4, r0, mc, b, r0 == 0, true, nullptr, 0, 0);
+    }
+    store_grads(S.ga, DA, H, 4, b);
+    cluster_sync_all(nS);
+    t_a += 1;
+    {
+        const size_t gaoff = (size_t)(S.ga - scr_base);
+        const float* cl0 = scr_base - (size_t)rk * scr_stride;
+        const int lo = (int)((int64_t)PA * rk / nS), hi = (int)((int64_t)PA * (rk + 1) / nS);
+        adam_slice(R.actor, cl0, scr_stride, nS, (int)gaoff, R.m_a, R.v_a, lo, hi, t_a, hp, 1.0f);
+        if (rk == 0 && threadIdx.x == 0) {
+            float l = 0.0f;
+            for (int s2 = 0; s2 < nS; ++s2) l += ldcg(cl0 + (size_t)s2 * scr_stride + (S.loss - scr_base) + 1);
             R.stats[1] = l;
         }
         __syncthreads();
@@ -622,9 +942,27 @@ __global__ void __launch_bounds__(LT) k_train(RunDesc* runs, const int* order, c
                 }
                 n_upd = t_now >= R.start_updates ? R.hp.updates_per_step : 0;
             }
+            const bool resident = R.H <= smlp::HP && R.DC <= smlp::INP && R.DA <= smlp::INP;
             for (int k = 0; k < n_upd; ++k) {
-                td3_update(R, head, size, t_now, (uint32_t)u, t_a, t_c, S, my, scr_stride,
-                           blockIdx.x - rk, rk, nS, sm);
+                if (resident) {
+                    // specialised shapes: hidden 64 or 32 over 16 actions of history, and the
+                    // privileged critic (82 + 4 + 6 motor/parameter inputs + 4 actions)
+                    const int key = R.H * 1000000 + R.DA * 1000 + R.DC;
+                    if (key == 64082090)
+                        td3_update_smem<64, 82, 90>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S,
+                                                    my, scr_stride, rk, nS, sm);
+                    else if (key == 32082090)
+                        td3_update_smem<32, 82, 90>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S,
+                                                    my, scr_stride, rk, nS, sm);
+                    else if (key == 64082096)
+                        td3_update_smem<64, 82, 96>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S,
+                                                    my, scr_stride, rk, nS, sm);
+                    else
+                        td3_update_smem<0, 0, 0>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S,
+                                                 my, scr_stride, rk, nS, sm);
+                } else
+                    td3_update(R, head, size, t_now, (uint32_t)u, t_a, t_c, S, my, scr_stride,
+                               blockIdx.x - rk, rk, nS, sm);
                 u += 1;
             }
         }
@@ -655,7 +993,8 @@ __global__ void k_init_params(float* P, int in, int h, int out, uint32_t net_id,
 
 static int grid_for(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
-static size_t learner_smem() { return sizeof(float) * (size_t)GEMM_SMEM; }
+static size_t learner_smem() { return sizeof(float) * (size_t)(SMEM_MAIN + 32); }
+
 
 }  // namespace qsim
 
@@ -773,6 +1112,8 @@ static qsim_status launch_train(std::vector<ac_handle*>& A, std::vector<qsim_han
     QCHECK_CUDA(cudaMemcpyAsync(d_runs, D.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, st));
     QCHECK_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
     QCHECK_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (n_clusters + 1), cudaMemcpyHostToDevice, st));
+    QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)learner_smem()));
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(n_clusters * nS);
     lc.blockDim = dim3(LT);
@@ -808,6 +1149,10 @@ extern "C" qsim_status ac_create(const ac_config* cfg, const qsim_handle* env, a
     if (cfg->policy_delay < 1) return fail(QSIM_EINVAL, "ac_create: policy_delay < 1");
     if (cfg->cluster < 0 || cfg->cluster > 16 || (cfg->cluster & (cfg->cluster - 1)))
         return fail(QSIM_EINVAL, "ac_create: cluster must be 0 or a power of two <= 16");
+    // the learner kernel needs more than the default 48 KB of dynamic shared memory (set on
+    // the current device, where every launch for this learner happens)
+    QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)learner_smem()));
     ac_handle* a = new ac_handle();
     a->cfg = *cfg;
     if (a->cfg.updates_per_step < 1) a->cfg.updates_per_step = 1;

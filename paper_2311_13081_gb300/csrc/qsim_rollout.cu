@@ -626,7 +626,7 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
     QCHECK_CUDA(cudaEventCreate(&e0));
     QCHECK_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_nw = 0, best_parts = 1, best_chunk = 0, best_pk = 0;
+    int best_nw = 0, best_parts = 1, best_pk = 0;
     struct Sched { int parts, chunk; };
     const int tc = std::max(1, std::min(100, n_steps / 4));
     const Sched scheds[] = {{1, 0}, {2, tc}, {3, tc}, {4, tc}};
@@ -650,7 +650,7 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
             cudaEventSynchronize(e1);
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_nw = nw; best_parts = sc.parts; best_chunk = sc.chunk; best_pk = pk; }
+            if (ms < best) { best = ms; best_nw = nw; best_parts = sc.parts; best_pk = pk; }
         }
     }
     cudaEventDestroy(e0);
@@ -661,7 +661,6 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
         h->rollout_parts = best_parts;
         h->rollout_chunk = best_parts > 1 ? 100 : 0;
         h->rollout_packed = best_pk;
-        (void)best_chunk;
     }
     return best_nw;
 }

@@ -1,0 +1,368 @@
+// qsim_smlp.cuh -- shared-memory-resident MLP engine of the learner (hidden width <= 64).
+//
+// One network pass of a CTA: the network's weights are staged into shared memory once (a
+// straight row-major copy), then the CTA's samples are processed in chunks of up to 64 rows
+// whose activations stay in shared memory between layers; weight gradients accumulate in
+// shared memory across chunks and are written out once.  Compared with the global-scratch
+// path this replaces ~30 L2 round trips per update with one weight stage per pass.
+//
+// Layouts (floats): everything row-major with padded row strides chosen == 4 (mod 32) so
+// that the GEMMs' 128-bit shared loads are conflict-free: input chunk Xs[r][k], hidden
+// activations and deltas [r][j], W1s[j][k], W2s[i][j], W3s[o][j].
+#pragma once
+#include "qsim_gemm.cuh"
+
+namespace qsim {
+namespace smlp {
+
+constexpr int HP = 64;    // largest hidden width handled here
+constexpr int INP = 104;  // row stride of the input chunk (critic input <= 100), multiple of 8
+constexpr int AS = 68;    // row stride of hidden activations (== 4 mod 32: conflict-free)
+constexpr int LD1 = 100;  // row stride of W1 [j][k] (>= input width, == 4 mod 32)
+constexpr int LD2 = 68;   // row stride of W2 [j][k]
+constexpr int MC = 64;    // rows per chunk
+
+struct Buf {
+    float *Xs, *H1s, *H2s, *dZ2s, *dZ1s, *dZ3s;
+    float *W1s, *b1, *W2s, *b2, *W3s, *b3;
+    float *gW1, *gb1, *gW2, *gb2, *gW3, *gb3;
+};
+
+__host__ __device__ constexpr int floats() {
+    return MC * INP + 4 * MC * AS + MC * 4 +                // activations
+           HP * LD1 + HP + HP * LD2 + HP + 4 * HP + 4 +    // weights
+           HP * INP + HP + HP * HP + HP + 4 * HP + 4 + 64; // gradient accumulators (+ slack)
+}
+
+__device__ __forceinline__ Buf carve(float* sm) {
+    Buf b;
+    float* p = sm;
+    b.Xs = p; p += MC * INP;
+    b.H1s = p; p += MC * AS;
+    b.H2s = p; p += MC * AS;
+    b.dZ2s = p; p += MC * AS;
+    b.dZ1s = p; p += MC * AS;
+    b.dZ3s = p; p += MC * 4;
+    b.W1s = p; p += HP * LD1;
+    b.b1 = p; p += HP;
+    b.W2s = p; p += HP * LD2;
+    b.b2 = p; p += HP;
+    b.W3s = p; p += 4 * HP;
+    b.b3 = p; p += 4;
+    b.gW1 = p; p += HP * INP;
+    b.gb1 = p; p += HP;
+    b.gW2 = p; p += HP * HP;
+    b.gb2 = p; p += HP;
+    b.gW3 = p; p += 4 * HP;
+    b.gb3 = p;
+    return b;
+}
+
+// C(m, n) = sum_k A(m, k) B(k, n) with A row-major [m][k] (lda, K a multiple of 4, padded
+// with zeros) and B [k][n] (ldb); 4 x 4 outputs per thread, float4 loads along k for A and
+// along n for B.  Operands may extend past M / N inside their buffers; outputs beyond M, N
+// are discarded.
+template <int RM, class Epi>
+__device__ __forceinline__ void gemm_mk_t(int M, int N, int K4, const float* A, int lda,
+                                        const float* B, int ldb, Epi epi) {
+    const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+    for (int m0 = 0; m0 < M; m0 += 16 * RM)
+        for (int n0 = 0; n0 < N; n0 += 64) {
+            const int mb = m0 + tm * RM, nb = n0 + tn * 4;
+            if (mb >= M || nb >= N) continue;
+            float acc[RM][4];
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+            for (int k = 0; k < K4; k += 4) {
+                float a[RM][4], b[4][4];
+#pragma unroll
+                for (int i = 0; i < RM; ++i) {
+                    const float4 v = *reinterpret_cast<const float4*>(A + (mb + i) * lda + k);
+                    a[i][0] = v.x; a[i][1] = v.y; a[i][2] = v.z; a[i][3] = v.w;
+                }
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const float4 v = *reinterpret_cast<const float4*>(B + (k + kk) * ldb + nb);
+                    b[kk][0] = v.x; b[kk][1] = v.y; b[kk][2] = v.z; b[kk][3] = v.w;
+                }
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                    for (int i = 0; i < RM; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i][kk], b[kk][j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (mb + i < M && nb + j < N) epi(mb + i, nb + j, acc[i][j]);
+        }
+    __syncthreads();
+}
+// gemm_mk with 4 rows per thread, or 2 when M <= 32 so that all warps take part.
+template <class Epi>
+__device__ __forceinline__ void gemm_mk(int M, int N, int K4, const float* A, int lda,
+                                        const float* B, int ldb, Epi epi) {
+    if (M <= 32) gemm_mk_t<2>(M, N, K4, A, lda, B, ldb, epi);
+    else gemm_mk_t<4>(M, N, K4, A, lda, B, ldb, epi);
+}
+
+// C(m, n) = sum_k A(m, k) B(n, k): A row-major [m][k], B row-major [n][k] (the weights as
+// stored), both read with float4 along k.  Lane (tm, tn) takes rows 4 tm + i and the
+// interleaved columns tn + 16 j, so that with ldb == 4 (mod 32) the 16 column rows a warp
+// reads per instruction fall into distinct bank quads.
+template <int RM, class Epi>
+__device__ __forceinline__ void gemm_nt_t(int M, int N, int K4, const float* A, int lda,
+                                        const float* B, int ldb, Epi epi) {
+    const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+    for (int m0 = 0; m0 < M; m0 += 16 * RM)
+        for (int n0 = 0; n0 < N; n0 += 64) {
+            const int mb = m0 + tm * RM, nb = n0 + tn;
+            if (mb >= M || nb >= N) continue;
+            float acc[RM][4];
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+            for (int k = 0; k < K4; k += 4) {
+                float a[RM][4], b[4][4];
+#pragma unroll
+                for (int i = 0; i < RM; ++i) {
+                    const float4 v = *reinterpret_cast<const float4*>(A + (mb + i) * lda + k);
+                    a[i][0] = v.x; a[i][1] = v.y; a[i][2] = v.z; a[i][3] = v.w;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 v = *reinterpret_cast<const float4*>(B + (nb + 16 * j) * ldb + k);
+                    b[j][0] = v.x; b[j][1] = v.y; b[j][2] = v.z; b[j][3] = v.w;
+                }
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                    for (int i = 0; i < RM; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i][kk], b[j][kk], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (mb + i < M && nb + 16 * j < N) epi(mb + i, nb + 16 * j, acc[i][j]);
+        }
+    __syncthreads();
+}
+// gemm_nt with 4 rows per thread, or 2 when M <= 32 so that all warps take part.
+template <class Epi>
+__device__ __forceinline__ void gemm_nt(int M, int N, int K4, const float* A, int lda,
+                                        const float* B, int ldb, Epi epi) {
+    if (M <= 32) gemm_nt_t<2>(M, N, K4, A, lda, B, ldb, epi);
+    else gemm_nt_t<4>(M, N, K4, A, lda, B, ldb, epi);
+}
+
+// Dot products y[r][o] = b3[o] + sum_j W3[o][j] H[r][j] for rows r < mc: one warp per
+// (row, output), lanes over j, shuffle reduction (conflict-free row reads).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Same with A stored [k][m] (lda): used for the weight gradients dW = dZ^T X, whose
+// reduction runs over the chunk's rows.
+template <class Epi>
+__device__ __forceinline__ void gemm_km(int M, int N, int K, const float* A, int lda,
+                                        const float* B, int ldb, Epi epi) {
+    const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
+    for (int m0 = 0; m0 < M; m0 += 64)
+        for (int n0 = 0; n0 < N; n0 += 64) {
+            const int mb = m0 + tm * 4, nb = n0 + tn * 4;
+            if (mb >= M || nb >= N) continue;
+            float acc[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) {
+                const float4 a = *reinterpret_cast<const float4*>(A + k * lda + mb);
+                const float4 b = *reinterpret_cast<const float4*>(B + k * ldb + nb);
+                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (mb + i < M && nb + j < N) epi(mb + i, nb + j, acc[i][j]);
+        }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int k4(int in) { return (in + 3) & ~3; }
+
+// Stage a network W1[H][in] b1 W2[H][H] b2 W3[out][H] b3 (global, possibly just updated by
+// another SM: L2 loads) into shared memory.
+// Copies n elements: dst(i) = src(i) for i < n (src index map `sidx`, dst map `didx`,
+// elements past `valid` written as zero), 8 L2 loads in flight per thread before the
+// shared-memory stores that consume them.
+template <class SIdx, class DIdx, class Valid>
+__device__ __forceinline__ void batched_copy(int n, const float* src, float* dst, SIdx sidx,
+                                             DIdx didx, Valid valid) {
+    constexpr int U = 8;
+    for (int base = threadIdx.x; base < n; base += LT * U) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + u * LT;
+            const bool ok = i < n && valid(i);
+            v[u] = ldcg(src + (ok ? sidx(i) : 0));
+            if (!ok) v[u] = 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + u * LT;
+            if (i < n) dst[didx(i)] = v[u];
+        }
+    }
+}
+
+// Stage a network W1[H][in] b1 W2[H][H] b2 W3[out][H] b3 (global, possibly just updated by
+// another SM: L2 loads) into shared memory.
+__device__ __forceinline__ void stage(const float* W, int in, int H, int out, const Buf& b) {
+    const float* gb1 = W + H * in;
+    const float* gW2 = gb1 + H;
+    const float* gb2 = gW2 + H * H;
+    const float* gW3 = gb2 + H;
+    const float* gb3 = gW3 + out * H;
+    const int K4 = k4(in);
+    batched_copy(H * K4, W, b.W1s, [&](int i) { return (i / K4) * in + i % K4; },
+                 [&](int i) { return (i / K4) * LD1 + i % K4; }, [&](int i) { return i % K4 < in; });
+    batched_copy(H * H, gW2, b.W2s, [&](int i) { return i; },
+                 [&](int i) { return (i / H) * LD2 + i % H; }, [&](int) { return true; });
+    batched_copy(H, gb1, b.b1, [&](int i) { return i; }, [&](int i) { return i; }, [&](int) { return true; });
+    batched_copy(H, gb2, b.b2, [&](int i) { return i; }, [&](int i) { return i; }, [&](int) { return true; });
+    batched_copy(out * H, gW3, b.W3s, [&](int i) { return i; },
+                 [&](int i) { return (i / H) * HP + i % H; }, [&](int) { return true; });
+    if (threadIdx.x < out) b.b3[threadIdx.x] = ldcg(gb3 + threadIdx.x);
+    __syncthreads();
+}
+
+// Forward of rows [r0, r0 + mc) of X (global [rows][ldx]): hidden activations stay in
+// shared memory; the outputs go to Y (global [rows][ldy]).
+__device__ __forceinline__ void forward(int in, int H, int out, const float* X, int ldx, int r0,
+                                        int mc, const Buf& b, float* Y, int ldy, bool tanh_out) {
+    const int K4 = k4(in);
+    batched_copy(mc * K4, X + (size_t)r0 * ldx, b.Xs, [&](int i) { return (i / K4) * ldx + i % K4; },
+                 [&](int i) { return (i / K4) * INP + i % K4; }, [&](int i) { return i % K4 < in; });
+    __syncthreads();
+    gemm_nt(mc, H, K4, b.Xs, INP, b.W1s, LD1,
+            [&](int m, int n, float v) { b.H1s[m * AS + n] = fmaxf(v + b.b1[n], 0.0f); });
+    gemm_nt(mc, H, H, b.H1s, AS, b.W2s, LD2,
+            [&](int m, int n, float v) { b.H2s[m * AS + n] = fmaxf(v + b.b2[n], 0.0f); });
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int item = warp; item < mc * out; item += LT / 32) {
+        const int r = item / out, o = item - r * out;
+        float acc = 0.0f;
+        for (int j = lane; j < H; j += 32) acc = fmaf(b.W3s[o * HP + j], b.H2s[r * AS + j], acc);
+        acc = warp_sum(acc) + b.b3[o];
+        if (lane == 0) Y[(size_t)(r0 + r) * ldy + o] = tanh_out ? tanhf(acc) : acc;
+    }
+    __syncthreads();
+}
+
+// Reverse of the chunk just run by forward(); dZ3s [mc][4] holds dLoss/d(output
+// pre-activation).  Accumulates the parameter gradient (first: overwrite) when want_w;
+// writes dLoss/dX for columns [x_lo, in) to dX (global [rows][ldx]) when dX != nullptr.
+__device__ __forceinline__ void backward(int in, int H, int out, int r0, int mc, const Buf& b,
+                                         bool first, bool want_w, float* dX, int ldx, int x_lo) {
+    if (want_w) {
+        for (int i = threadIdx.x; i < out * H; i += LT) {
+            const int o = i / H, j = i - o * H;
+            float s = 0.0f;
+            for (int r = 0; r < mc; ++r) s = fmaf(b.dZ3s[r * 4 + o], b.H2s[r * AS + j], s);
+            b.gW3[o * HP + j] = first ? s : b.gW3[o * HP + j] + s;
+        }
+        if (threadIdx.x < out) {
+            float s = 0.0f;
+            for (int r = 0; r < mc; ++r) s += b.dZ3s[r * 4 + threadIdx.x];
+            b.gb3[threadIdx.x] = first ? s : b.gb3[threadIdx.x] + s;
+        }
+    }
+    for (int i = threadIdx.x; i < mc * H; i += LT) {
+        const int r = i / H, j = i - r * H;
+        float v = 0.0f;
+        for (int o = 0; o < out; ++o) v = fmaf(b.dZ3s[r * 4 + o], b.W3s[o * HP + j], v);
+        b.dZ2s[r * AS + j] = b.H2s[r * AS + j] > 0.0f ? v : 0.0f;
+    }
+    __syncthreads();
+    if (want_w) {
+        gemm_km(H, H, mc, b.dZ2s, AS, b.H1s, AS, [&](int m, int n, float v) {
+            b.gW2[m * HP + n] = first ? v : b.gW2[m * HP + n] + v;
+        });
+        for (int j = threadIdx.x; j < H; j += LT) {
+            float s = 0.0f;
+            for (int r = 0; r < mc; ++r) s += b.dZ2s[r * AS + j];
+            b.gb2[j] = first ? s : b.gb2[j] + s;
+        }
+    }
+    gemm_mk(mc, H, H, b.dZ2s, AS, b.W2s, LD2, [&](int m, int n, float v) {
+        b.dZ1s[m * AS + n] = b.H1s[m * AS + n] > 0.0f ? v : 0.0f;
+    });
+    if (want_w) {
+        gemm_km(H, in, mc, b.dZ1s, AS, b.Xs, INP, [&](int m, int n, float v) {
+            b.gW1[m * INP + n] = first ? v : b.gW1[m * INP + n] + v;
+        });
+        for (int j = threadIdx.x; j < H; j += LT) {
+            float s = 0.0f;
+            for (int r = 0; r < mc; ++r) s += b.dZ1s[r * AS + j];
+            b.gb1[j] = first ? s : b.gb1[j] + s;
+        }
+    }
+    if (dX) {
+        const int nc = in - x_lo;
+        for (int i = threadIdx.x; i < mc * nc; i += LT) {
+            const int r = i / nc, c = x_lo + (i - r * nc);
+            float s = 0.0f;
+            for (int j = 0; j < H; ++j) s = fmaf(b.dZ1s[r * AS + j], b.W1s[j * LD1 + c], s);
+            dX[(size_t)(r0 + r) * ldx + c] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Writes the accumulated gradient in the parameter layout of W (global).
+__device__ __forceinline__ void store_grads(float* G, int in, int H, int out, const Buf& b) {
+    float* gW1 = G;
+    float* gb1 = gW1 + H * in;
+    float* gW2 = gb1 + H;
+    float* gb2 = gW2 + H * H;
+    float* gW3 = gb2 + H;
+    float* gb3 = gW3 + out * H;
+    for (int i = threadIdx.x; i < H * in; i += LT) {
+        const int j = i / in, k = i - j * in;
+        gW1[i] = b.gW1[j * INP + k];
+    }
+    for (int i = threadIdx.x; i < H * H; i += LT) {
+        const int r = i / H, c = i - r * H;
+        gW2[i] = b.gW2[r * HP + c];
+    }
+    for (int i = threadIdx.x; i < H; i += LT) {
+        gb1[i] = b.gb1[i];
+        gb2[i] = b.gb2[i];
+    }
+    for (int i = threadIdx.x; i < out * H; i += LT) {
+        const int o = i / H, j = i - o * H;
+        gW3[i] = b.gW3[o * HP + j];
+    }
+    if (threadIdx.x < out) gb3[threadIdx.x] = b.gb3[threadIdx.x];
+    __syncthreads();
+}
+
+}  // namespace smlp
+}  // namespace qsim
