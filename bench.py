@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--parts", type=int, default=1, help="with --warps: env partitions")
     ap.add_argument("--chunk", type=int, default=100, help="with --warps: steps per chunk")
     ap.add_argument("--packed", type=int, default=1, help="with --warps: paired-FMA variant")
+    ap.add_argument("--engine", type=int, default=-1,
+                    help="rollout engine: 0 SIMT, 1 SIMT paired FMA, 2 tensor cores, -1 autotuned")
     return ap.parse_args()
 
 
@@ -463,8 +465,10 @@ def main():
     if args.warps:
         tuned = q.qsim_rollout_tune(h, args.warps)
         q.qsim_rollout_schedule(h, args.parts, args.chunk if args.parts > 1 else 0)
-        q.qsim_rollout_packed(h, args.packed)
+        q.qsim_rollout_engine(h, args.engine if args.engine >= 0 else args.packed)
     else:
+        if args.engine >= 0:
+            q.qsim_rollout_engine(h, args.engine)
         tuned = q.qsim_rollout_autotune(h, actor, hidden, 100)
     for _ in range(args.warmup):
         q.qsim_rollout(h, actor, hidden, horizon)
@@ -485,7 +489,7 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    packed_used = q.qsim_rollout_packed(h, -2)
+    packed_used = q.qsim_rollout_engine(h, -2)
     parts_used = q.qsim_rollout_schedule(h, -1, -1)
     t_dev = sum(ms) / 1e3
     if world > 1:
@@ -550,7 +554,7 @@ def main():
                        "envs_per_gpu": n, "steps_per_bench_step": horizon,
                        "l2": "flushed before every timed step (512 MB write)",
                        "rollout_warps_per_block": tuned,
-                       "rollout_packed_fma": packed_used,
+                       "rollout_engine": packed_used,
                        "rollout_partitions": parts_used},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": achieved / fp32_peak,

@@ -222,7 +222,17 @@ int32_t qsim_rollout_schedule(qsim_handle* h, int32_t parts, int32_t chunk);
  * single-precision FMAs per instruction, results identical to the scalar kernel), 0 the
  * scalar kernel, -1 automatic (the autotuner decides; scalar until it has run).  Returns the
  * setting in effect. */
-int32_t qsim_rollout_packed(qsim_handle* h, int32_t packed);
+int32_t qsim_rollout_packed(qsim_handle* h, int32_t packed);  /* engines 0/1 of qsim_rollout_engine */
+
+/* Rollout engine: 0 the SIMT kernel (scalar FMA), 1 the SIMT kernel with paired FMA (same
+ * results as 0), 2 the tensor-core kernel (hidden = 64 only: the two hidden layers as
+ * tcgen05 TF32 MMAs with a three-term hi/lo split that keeps FP32 accuracy, accumulators in
+ * tensor memory, 256 envs per block; results agree with 0 to FP32 rounding, not bitwise),
+ * -1 automatic (the autotuner decides; scalar SIMT until it has run).  Any other value
+ * leaves the setting unchanged.  Returns the setting in effect.  The paper's environment
+ * step has no counterpart of this switch: it selects among kernels computing the same step
+ * (Sec. III, Eq. 1-4 dynamics, Sec. IV actor). */
+int32_t qsim_rollout_engine(qsim_handle* h, int32_t engine);
 
 /* Autotuner: times every (warps-per-block, schedule) variant of the rollout kernel that fits
  * on this device with n_steps-step rollouts (CUDA events on `stream`; these are real env

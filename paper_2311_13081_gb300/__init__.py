@@ -120,6 +120,7 @@ _SIGS = {
     "qsim_rollout_autotune": (C.c_int32, [P, P, C.c_int32, C.c_int32, P]),
     "qsim_rollout_schedule": (C.c_int32, [P, C.c_int32, C.c_int32]),
     "qsim_rollout_packed": (C.c_int32, [P, C.c_int32]),
+    "qsim_rollout_engine": (C.c_int32, [P, C.c_int32]),
     "qsim_ffma_probe": (C.c_int, [C.c_int32, C.c_int32, P, P]),
     "qsim_recalc_rewards": (C.c_int, [P, P]),
     "qsim_set_reward": (C.c_int, [P, P, C.c_float, P]),
@@ -358,6 +359,12 @@ def qsim_rollout_schedule(h, parts=-1, chunk=-1) -> int:
 
 def qsim_rollout_packed(h, packed=-1) -> int:
     return int(_lib.qsim_rollout_packed(h, packed))
+
+
+def qsim_rollout_engine(h, engine=-2) -> int:
+    """0 SIMT, 1 SIMT paired FMA, 2 tensor cores (hidden 64), -1 automatic; other values
+    only query."""
+    return int(_lib.qsim_rollout_engine(h, engine))
 
 
 def qsim_ffma_probe(n_blocks, iters, out, stream=None):

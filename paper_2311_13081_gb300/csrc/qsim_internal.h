@@ -53,7 +53,7 @@ struct qsim_handle {
     // rollout scheduling: env partitions on internal streams, launched in time chunks so
     // that one partition's next chunk fills SMs the other leaves idle
     int rollout_parts, rollout_chunk;
-    int rollout_packed;  // paired-FMA kernel variant: -1 automatic, 0 off, 1 on
+    int rollout_packed;  // rollout engine: -1 automatic, 0 SIMT, 1 SIMT paired FMA, 2 tensor cores
     cudaStream_t part_stream[4];
     cudaEvent_t ev_fork, ev_join[4];
     bool streams_ready;

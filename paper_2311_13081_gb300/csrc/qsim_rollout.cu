@@ -515,6 +515,14 @@ static int resident_warps(int hidden, int nw, int device, bool pk = false) {
     return std::max(1, blocks) * nw * sms;
 }
 
+// Resident CTAs of the tensor-core kernel: one per SM (its shared memory and its 512 TMEM
+// columns both take the whole SM).
+static int tc_resident_ctas(int device) {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return sms;
+}
+
 static qsim_status ensure_streams(qsim_handle* h) {
     if (h->streams_ready) return QSIM_OK;
     for (int p = 0; p < 4; ++p) {
@@ -526,18 +534,25 @@ static qsim_status ensure_streams(qsim_handle* h) {
     return QSIM_OK;
 }
 
+qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, uint32_t t0, int64_t head,
+                                    float sigma, int w0, int w1, cudaStream_t st);
+
 // Launches T steps of the rollout as `parts` env partitions x chunks of `chunk` steps.
 // Partition p owns warps [W p / parts, W (p+1) / parts); its chunks run in order on its
 // own stream, chunks of different partitions are issued interleaved, and the caller's
 // stream joins all partitions at the end.
+// engine 2 (tensor cores) ignores nw.
 qsim_status launch_rollout(qsim_handle* h, const float* actor, int hidden, int T, float sigma,
-                           cudaStream_t st, int nw, int parts, int chunk, bool pk) {
-    RollFn fn = roll_fn(hidden, nw, pk);
-    if (!fn) return fail(QSIM_EINVAL, "qsim_rollout: no kernel for hidden=%d warps=%d", hidden, nw);
-    const size_t smem = roll_smem(hidden, nw);
+                           cudaStream_t st, int nw, int parts, int chunk, int engine) {
+    const bool tc = engine == 2;
+    const bool pk = engine == 1;
+    if (tc && hidden != 64) return fail(QSIM_EINVAL, "qsim_rollout: tensor-core engine needs hidden=64");
+    RollFn fn = tc ? nullptr : roll_fn(hidden, nw, pk);
+    if (!tc && !fn) return fail(QSIM_EINVAL, "qsim_rollout: no kernel for hidden=%d warps=%d", hidden, nw);
+    const size_t smem = tc ? 0 : roll_smem(hidden, nw);
     static bool configured[2][3][11] = {};
     const int hi = hidden == 32 ? 0 : (hidden == 64 ? 1 : 2);
-    if (!configured[pk][hi][nw]) {
+    if (!tc && !configured[pk][hi][nw]) {
         QCHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured[pk][hi][nw] = true;
     }
@@ -545,6 +560,29 @@ qsim_status launch_rollout(qsim_handle* h, const float* actor, int hidden, int T
     parts = std::max(1, std::min(parts, std::min(4, warps)));
     if (chunk <= 0 || chunk > T) chunk = T;
     const uint32_t t0 = (uint32_t)h->t_now;
+    if (tc) {
+        if (parts == 1 && chunk == T)
+            return launch_rollout_tc_range(h, actor, T, t0, h->head, sigma, 0, warps, st);
+        qsim_status s = ensure_streams(h);
+        if (s != QSIM_OK) return s;
+        QCHECK_CUDA(cudaEventRecord(h->ev_fork, st));
+        for (int p = 0; p < parts; ++p) QCHECK_CUDA(cudaStreamWaitEvent(h->part_stream[p], h->ev_fork, 0));
+        for (int t = 0; t < T; t += chunk) {
+            const int tcn = std::min(chunk, T - t);
+            for (int p = 0; p < parts; ++p) {
+                const int w0 = (int)((int64_t)warps * p / parts), w1 = (int)((int64_t)warps * (p + 1) / parts);
+                if (w1 <= w0) continue;
+                s = launch_rollout_tc_range(h, actor, tcn, t0 + (uint32_t)t, h->head + t, sigma, w0, w1,
+                                            h->part_stream[p]);
+                if (s != QSIM_OK) return s;
+            }
+        }
+        for (int p = 0; p < parts; ++p) {
+            QCHECK_CUDA(cudaEventRecord(h->ev_join[p], h->part_stream[p]));
+            QCHECK_CUDA(cudaStreamWaitEvent(st, h->ev_join[p], 0));
+        }
+        return QSIM_OK;
+    }
     if (parts == 1 && chunk == T) {
         const int grid = (warps + nw - 1) / nw;
         fn<<<grid, nw * 32, smem, st>>>(h->dc, h->p, actor, T, t0, h->head, h->capacity, sigma, 0,
@@ -596,15 +634,18 @@ extern "C" qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t 
     if (n_steps == 0) return QSIM_OK;
     int nw = h->rollout_warps ? h->rollout_warps : default_warps(hidden, h->ld, h->device);
     if (roll_smem(hidden, nw) > 227 * 1024) nw = 2;
-    const bool pk = h->rollout_packed > 0;
+    int engine = h->rollout_packed > 0 ? h->rollout_packed : 0;
+    if (engine == 2 && hidden != 64) engine = 1;
     int parts = h->rollout_parts, chunk = h->rollout_chunk;
     if (parts <= 0) {
         // more than one wave of warps: pipeline two partitions in 100-step chunks
-        parts = (h->ld / 32 > resident_warps(hidden, nw, h->device, pk)) ? 2 : 1;
+        const int resident = engine == 2 ? 8 * tc_resident_ctas(h->device)
+                                         : resident_warps(hidden, nw, h->device, engine == 1);
+        parts = (h->ld / 32 > resident) ? 2 : 1;
         chunk = parts > 1 ? 100 : 0;
     }
     qsim_status s = launch_rollout(h, actor, hidden, n_steps, sigma_e, (cudaStream_t)stream, nw,
-                                   parts, chunk, pk);
+                                   parts, chunk, engine);
     if (s != QSIM_OK) return s;
     h->t_now += n_steps;
     if (h->capacity > 0) {
@@ -630,16 +671,19 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
     struct Sched { int parts, chunk; };
     const int tc = std::max(1, std::min(100, n_steps / 4));
     const Sched scheds[] = {{1, 0}, {2, tc}, {3, tc}, {4, tc}};
-    for (int pk = 0; pk < 2; ++pk)
+    for (int pk = 0; pk < 3; ++pk)
     for (int nw : kWarpChoices) {
-        if (roll_smem(hidden, nw) > (size_t)smem_blk) continue;
+        if (pk == 2 && (hidden != 64 || nw != kWarpChoices[0])) continue;  // one tensor-core shape
+        if (pk < 2 && roll_smem(hidden, nw) > (size_t)smem_blk) continue;
         if (h->rollout_packed >= 0 && pk != h->rollout_packed) continue;
         for (const Sched& sc : scheds) {
             if (((h->t_now + n_steps) >> 32) != 0) break;
-            if (sc.parts > 1 && h->ld / 32 <= resident_warps(hidden, nw, h->device, pk)) continue;
+            const int resident = pk == 2 ? 8 * tc_resident_ctas(h->device)
+                                         : resident_warps(hidden, nw, h->device, pk == 1);
+            if (sc.parts > 1 && h->ld / 32 <= resident) continue;
             cudaEventRecord(e0, st);
             qsim_status s = launch_rollout(h, actor, hidden, n_steps, -1.0f, st, nw, sc.parts, sc.chunk,
-                                           pk != 0);
+                                           pk);
             cudaEventRecord(e1, st);
             if (s != QSIM_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
             h->t_now += n_steps;
@@ -668,6 +712,12 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
 extern "C" int32_t qsim_rollout_packed(qsim_handle* h, int32_t packed) {
     if (!h) return 0;
     if (packed >= -1 && packed <= 1) h->rollout_packed = packed;
+    return h->rollout_packed;
+}
+
+extern "C" int32_t qsim_rollout_engine(qsim_handle* h, int32_t engine) {
+    if (!h) return 0;
+    if (engine >= -1 && engine <= 2) h->rollout_packed = engine;
     return h->rollout_packed;
 }
 

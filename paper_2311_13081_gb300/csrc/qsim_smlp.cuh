@@ -206,8 +206,13 @@ __device__ __forceinline__ void gemm_km(int M, int N, int K, const float* A, int
 
 __device__ __forceinline__ int k4(int in) { return (in + 3) & ~3; }
 
-// Stage a network W1[H][in] b1 W2[H][H] b2 W3[out][H] b3 (global, possibly just updated by
-// another SM: L2 loads) into shared memory.
+__device__ __forceinline__ float4 ldcg4(const float* p) {
+    float4 r;
+    asm volatile("ld.global.cg.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+    return r;
+}
+
 // Copies n elements: dst(i) = src(i) for i < n (src index map `sidx`, dst map `didx`,
 // elements past `valid` written as zero), 8 L2 loads in flight per thread before the
 // shared-memory stores that consume them.
@@ -232,24 +237,70 @@ __device__ __forceinline__ void batched_copy(int n, const float* src, float* dst
     }
 }
 
-// Stage a network W1[H][in] b1 W2[H][H] b2 W3[out][H] b3 (global, possibly just updated by
-// another SM: L2 loads) into shared memory.
+// Reads the contiguous global range src[0, n) with L2-only loads and hands every element
+// to place(i, value) (a shared-memory store).  The 16-byte-aligned body is read as float4,
+// U of them per thread in flight at once; the unaligned head and tail (< 4 elements each)
+// element by element.  Nothing outside src[0, n) is read.
+template <class Place>
+__device__ __forceinline__ void load_scatter(const float* src, int n, Place place) {
+    constexpr int U = 12;
+    const int lead = (int)((4u - ((uint32_t)(uintptr_t)src >> 2)) & 3u);  // elements to 16-byte alignment
+    const int ia = min(lead, n);
+    const int nv = (n - ia) >> 2;
+    const int ib = ia + 4 * nv;
+    if (threadIdx.x < ia) place(threadIdx.x, ldcg(src + threadIdx.x));
+    if (threadIdx.x < n - ib) place(ib + threadIdx.x, ldcg(src + ib + threadIdx.x));
+    const float* body = src + ia;
+    for (int v0 = threadIdx.x; v0 < nv; v0 += LT * U) {
+        float4 x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int v = v0 + u * LT;
+            x[u] = v < nv ? ldcg4(body + 4 * v) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int v = v0 + u * LT;
+            if (v < nv) {
+                const int i = ia + 4 * v;
+                place(i, x[u].x);
+                place(i + 1, x[u].y);
+                place(i + 2, x[u].z);
+                place(i + 3, x[u].w);
+            }
+        }
+    }
+}
+
+// Stage a network W1[H][in] b1 W2[H][H] b2 W3[out][H] b3 (global, contiguous, possibly just
+// updated by another SM: L2 loads) into shared memory, W1 rows zero-padded to a multiple
+// of 4 columns.
 __device__ __forceinline__ void stage(const float* W, int in, int H, int out, const Buf& b) {
-    const float* gb1 = W + H * in;
-    const float* gW2 = gb1 + H;
-    const float* gb2 = gW2 + H * H;
-    const float* gW3 = gb2 + H;
-    const float* gb3 = gW3 + out * H;
     const int K4 = k4(in);
-    batched_copy(H * K4, W, b.W1s, [&](int i) { return (i / K4) * in + i % K4; },
-                 [&](int i) { return (i / K4) * LD1 + i % K4; }, [&](int i) { return i % K4 < in; });
-    batched_copy(H * H, gW2, b.W2s, [&](int i) { return i; },
-                 [&](int i) { return (i / H) * LD2 + i % H; }, [&](int) { return true; });
-    batched_copy(H, gb1, b.b1, [&](int i) { return i; }, [&](int i) { return i; }, [&](int) { return true; });
-    batched_copy(H, gb2, b.b2, [&](int i) { return i; }, [&](int i) { return i; }, [&](int) { return true; });
-    batched_copy(out * H, gW3, b.W3s, [&](int i) { return i; },
-                 [&](int i) { return (i / H) * HP + i % H; }, [&](int) { return true; });
-    if (threadIdx.x < out) b.b3[threadIdx.x] = ldcg(gb3 + threadIdx.x);
+    const int e1 = H * in, e2 = e1 + H, e3 = e2 + H * H, e4 = e3 + H, e5 = e4 + out * H;
+    const int n = e5 + out;
+    load_scatter(W, n, [&](int i, float v) {
+        if (i < e1) {
+            const int j = i / in;
+            b.W1s[j * LD1 + (i - j * in)] = v;
+        } else if (i < e2) {
+            b.b1[i - e1] = v;
+        } else if (i < e3) {
+            const int r = (i - e2) / H;
+            b.W2s[r * LD2 + (i - e2 - r * H)] = v;
+        } else if (i < e4) {
+            b.b2[i - e3] = v;
+        } else if (i < e5) {
+            const int o = (i - e4) / H;
+            b.W3s[o * HP + (i - e4 - o * H)] = v;
+        } else {
+            b.b3[i - e5] = v;
+        }
+    });
+    for (int i = threadIdx.x; i < H * (K4 - in); i += LT) {
+        const int j = i / (K4 - in);
+        b.W1s[j * LD1 + in + (i - j * (K4 - in))] = 0.0f;
+    }
     __syncthreads();
 }
 
@@ -258,8 +309,20 @@ __device__ __forceinline__ void stage(const float* W, int in, int H, int out, co
 __device__ __forceinline__ void forward(int in, int H, int out, const float* X, int ldx, int r0,
                                         int mc, const Buf& b, float* Y, int ldy, bool tanh_out) {
     const int K4 = k4(in);
-    batched_copy(mc * K4, X + (size_t)r0 * ldx, b.Xs, [&](int i) { return (i / K4) * ldx + i % K4; },
-                 [&](int i) { return (i / K4) * INP + i % K4; }, [&](int i) { return i % K4 < in; });
+    if (ldx == in) {
+        // rows contiguous: one range, float4 body
+        load_scatter(X + (size_t)r0 * ldx, mc * in, [&](int i, float v) {
+            const int r = i / in;
+            b.Xs[r * INP + (i - r * in)] = v;
+        });
+        for (int i = threadIdx.x; i < mc * (K4 - in); i += LT) {
+            const int r = i / (K4 - in);
+            b.Xs[r * INP + in + (i - r * (K4 - in))] = 0.0f;
+        }
+    } else {
+        batched_copy(mc * K4, X + (size_t)r0 * ldx, b.Xs, [&](int i) { return (i / K4) * ldx + i % K4; },
+                     [&](int i) { return (i / K4) * INP + i % K4; }, [&](int i) { return i % K4 < in; });
+    }
     __syncthreads();
     gemm_nt(mc, H, K4, b.Xs, INP, b.W1s, LD1,
             [&](int m, int n, float v) { b.H1s[m * AS + n] = fmaxf(v + b.b1[n], 0.0f); });

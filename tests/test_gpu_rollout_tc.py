@@ -1,0 +1,142 @@
+"""Tensor-core rollout engine (tcgen05 TF32 with the hi/lo split) against the FP64 oracle,
+teacher-forced per call; schedule invariance and determinism of the engine itself."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from helpers import (STATE_SCALE, assert_close, compare_records, cpu, f64, gpu_records,
+                     lib_config, oracle_envs, u32)
+
+pytestmark = pytest.mark.gpu
+
+TC = 2  # qsim_rollout_engine: tensor cores
+
+
+def _actor(d, hidden=64, seed=0):
+    dd = dict(d)
+    dd["seed"] = seed
+    return O.init_params(dd, 0, O.actor_in(d), hidden, 4).astype(np.float32)
+
+
+def _run_parity(q, n, calls, n_hist=None, **over):
+    kw = dict(capacity=6, learning_starts=3, episode_len=40, sig_p=0.005, sig_R=0.01,
+              sig_v=0.02, sig_w=0.02)
+    kw.update(over)
+    if n_hist is not None:
+        kw["n_hist"] = n_hist
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, **kw)
+    h = q.qsim_create(cfg, veh)
+    cap = kw["capacity"]
+    try:
+        assert q.qsim_rollout_engine(h, TC) == TC
+        actor = _actor(d)
+        A = torch.tensor(actor, device="cuda")
+        ids = np.arange(n)
+        for call, T in enumerate(calls):
+            info = q.qsim_info_get(h)
+            e = oracle_envs(info, ids)
+            t0, head0 = info["t_now"], info["head"]
+            q.qsim_rollout(h, A, 64, T, 0.1)
+            q.qsim_sync(h)
+            ref = O.rollout(d, W.REWARD, e, T, t0, actor=actor.astype(np.float64), hidden=64,
+                            sigma_e=0.1, n_threads=8)
+            info = q.qsim_info_get(h)
+            slots = [(head0 + k) % cap for k in range(T)]
+            g = gpu_records(info, slots, ids)
+            compare_records({k: v[:1] for k, v in g.items()}, {k: v[:1] for k, v in ref.items()},
+                            what=f"tc rollout{call}.0")
+            if T == 1:
+                assert_close(f64(info["state"])[:, :n].T, e["s"], STATE_SCALE, what="state")
+                assert_close(f64(info["hist"])[:, :n].T, e["hist"], 1.0, what="hist")
+                assert np.array_equal(u32(info["ep_step"])[:n], e["ep_step"])
+            else:
+                same = np.all(g["rec_flags"] == ref["rec_flags"], axis=0)
+                assert same.mean() > 0.99
+                assert_close(g["rec_s"][:, same], ref["rec_s"][:, same], STATE_SCALE, what="multi s")
+                assert_close(g["rec_a"][:, same], ref["rec_a"][:, same], 1.0, what="multi a")
+    finally:
+        q.qsim_destroy(h)
+
+
+@pytest.mark.parametrize("n", [300, 1000, 64, 257])
+def test_tc_rollout_parity(gpu, n):
+    """Ragged tiles (300, 257: partial 128-env tiles and inactive warps), a single partial
+    tile (64), several 256-env blocks (1000); warm-up steps then actor steps."""
+    _run_parity(gpu, n, (2, 1, 3, 1))
+
+
+def test_tc_rollout_parity_short_history(gpu):
+    """History shorter than the 16-slot ring: the lag blocks past n_hist carry zero weights."""
+    _run_parity(gpu, 300, (4, 1, 2), n_hist=5)
+
+
+def test_tc_episode_ends_clear_the_action_ring(gpu):
+    """Episodes of 4 steps inside one 10-step call: the ring is cleared at every episode end
+    (per lane, inside a warp where other lanes continue) and refilled step by step."""
+    _run_parity(gpu, 200, (10, 1), capacity=12, learning_starts=0, episode_len=4)
+
+
+def test_tc_full_size_sampled(gpu):
+    """65,536 envs, default schedule of the engine; 256 sampled envs checked."""
+    q = gpu
+    n = 65536
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=4, learning_starts=0)
+    h = q.qsim_create(cfg, veh)
+    try:
+        q.qsim_rollout_engine(h, TC)
+        actor = _actor(d)
+        A = torch.tensor(actor, device="cuda")
+        q.qsim_rollout(h, A, 64, 3, 0.1)
+        ids = np.unique([O.replay_index(int(O.philox([i, 0, 4 << 24, 0], [0, 0])[0]), n)
+                         for i in range(256)])
+        info = q.qsim_info_get(h)
+        e = oracle_envs(info, ids)
+        t0, head0 = info["t_now"], info["head"]
+        q.qsim_rollout(h, A, 64, 1, 0.1)
+        q.qsim_sync(h)
+        ref = O.rollout(d, W.REWARD, e, 1, t0, actor=actor.astype(np.float64), hidden=64,
+                        sigma_e=0.1, n_threads=8)
+        info = q.qsim_info_get(h)
+        compare_records(gpu_records(info, [head0], ids), ref, what="c2 tc sampled")
+        assert_close(f64(info["state"])[:, ids].T, e["s"], STATE_SCALE, what="c2 tc state")
+    finally:
+        q.qsim_destroy(h)
+
+
+def test_tc_schedule_invariant_and_deterministic(gpu):
+    """Each env's arithmetic does not depend on which envs share its tile or on the launch
+    grouping: partitions / chunks and repeated runs agree bit for bit."""
+    q = gpu
+    n = 40000
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=8, learning_starts=2)
+    A = torch.tensor(_actor(d), device="cuda")
+    outs = []
+    for parts, chunk in ((1, 0), (3, 2), (2, 1), (1, 0)):
+        h = q.qsim_create(cfg, veh)
+        q.qsim_rollout_engine(h, TC)
+        q.qsim_rollout_schedule(h, parts, chunk)
+        q.qsim_rollout(h, A, 64, 5, 0.1)
+        q.qsim_sync(h)
+        info = q.qsim_info_get(h)
+        outs.append([cpu(info[k]).copy() for k in ("records", "side", "state", "hist", "ep_step")])
+        q.qsim_destroy(h)
+    for o in outs[1:]:
+        for x, y in zip(o, outs[0]):
+            assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+
+
+def test_tc_engine_other_widths_run_on_simt(gpu):
+    q = gpu
+    d, cfg, veh = lib_config(q, "c2", n_envs=64, capacity=4)
+    h = q.qsim_create(cfg, veh)
+    try:
+        q.qsim_rollout_engine(h, TC)
+        A = torch.tensor(_actor(d, 32), device="cuda")
+        # hidden 32 has no tensor-core kernel: the SIMT engine runs instead
+        q.qsim_rollout(h, A, 32, 2, 0.1)
+        q.qsim_sync(h)
+        assert q.qsim_rollout_engine(h, 5) == TC
+    finally:
+        q.qsim_destroy(h)
