@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 METRIC = ("env-steps/s (sim+policy) and wall time to N actor-critic updates on 1 GB300, "
           "vs plain")
 FLOP_ACTOR = lambda da, h: 2 * (da * h + h * h + 4 * h)  # noqa: E731
+# tensor-core engine: the two hidden layers as TF32 MMAs with the hi/lo split, three
+# products per FP32-accurate product (A_hi W_hi + A_hi W_lo + A_lo W_hi)
+FLOP_TC_MMA = lambda da, h: 3 * 2 * (da * h + h * h)  # noqa: E731
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rate of the part
 FLOP_DYN = 672        # RK4 (4 derivative evaluations + stage/accumulation arithmetic)
 FLOP_MISC = 60        # observation rotation matrix, reward, termination, action map
 BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, flags)
@@ -40,6 +44,8 @@ BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, fl
 # dram__bytes_write.sum, 32,768 envs x 100 steps; profiles/k_rollout_c2_65536x1000.md).
 # Set to None whenever the kernel changes until it is captured again.
 NCU_DRAM_BYTES_PER_ENV_STEP = (46.710016e6 + 289.403648e6) / (32768 * 100)
+# same for the tensor-core kernel k_rollout_tc (profiles/k_rollout_tc_c2_65536x1000.md)
+NCU_DRAM_BYTES_PER_ENV_STEP_TC = (35.136512e6 + 97.005312e6) / (65536 * 20)
 
 
 def parse():
@@ -136,10 +142,14 @@ def device_peaks(torch, q):
         max_mhz = float(mp.get("sm_max_mhz", max_mhz))
         hbm = float(mp["hbm_gbs"])
         hbm_src = "measured"
+        bf16_sus = float(mp["bf16_tflops_sustained"])
+        tc_src = "measured"
     except Exception:
         hbm, hbm_src = 6800.0, "fallback"
+        bf16_sus, tc_src = 1700.0, "fallback"
     fp32 = sms * 128 * 2 * max_mhz * 1e6 / 1e12
-    return sms, max_mhz, fp32, hbm, hbm_src
+    tf32 = bf16_sus * TF32_PER_BF16
+    return sms, max_mhz, fp32, hbm, hbm_src, tf32, tc_src
 
 
 # -------------------------------------------------------------------------- measurements
@@ -499,7 +509,7 @@ def main():
         dist.barrier()
     env_steps = n * horizon * args.steps * world
     value = env_steps / t_dev
-    sms, max_mhz, fp32_peak, hbm, hbm_src = device_peaks(torch, q)
+    sms, max_mhz, fp32_peak, hbm, hbm_src, tf32_peak, tc_src = device_peaks(torch, q)
     flop_step = FLOP_ACTOR(82, hidden) + FLOP_DYN + FLOP_MISC
     achieved = n * horizon * flop_step / (sum(ms) / args.steps * 1e-3) / 1e12
     clocks = clk.summary()
@@ -539,6 +549,34 @@ def main():
         extras["learner_single_run_c1"] = measure_c1(torch, q, W)
         extras["differentiation_c3"] = measure_diff(torch, q, W)
         extras["asymmetric_curriculum_c5"] = measure_c5(torch, q, W)
+    step_s = sum(ms) / args.steps * 1e-3
+    hbm_ach = n * horizon * BYTES_STEP / step_s / 1e9
+    if packed_used == 2:
+        # tensor-core engine: the dominant unit is the tensor pipe (TF32 MMAs)
+        tc_flop = FLOP_TC_MMA(82, hidden)
+        ach = n * horizon * tc_flop / step_s / 1e12
+        roofline = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                    "frac": ach / tf32_peak,
+                    "traffic": (None if NCU_DRAM_BYTES_PER_ENV_STEP_TC is None
+                                else NCU_DRAM_BYTES_PER_ENV_STEP_TC * n * horizon),
+                    "peak_source": f"TF32 dense, sustained: {tc_src} bf16 sustained x {TF32_PER_BF16:.3f} "
+                                   "(nominal TF32:BF16)",
+                    "flop_per_env_step": tc_flop,
+                    "fp32_equivalent_tflops": ach / 3,
+                    "simt_fp32_tflops": n * horizon * (FLOP_DYN + FLOP_MISC + 2 * 4 * hidden) / step_s / 1e12,
+                    "simt_fp32_peak": fp32_peak,
+                    "hbm_gbs_achieved": hbm_ach, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                    "traffic": (None if NCU_DRAM_BYTES_PER_ENV_STEP is None
+                                else NCU_DRAM_BYTES_PER_ENV_STEP * n * horizon),
+                    "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                    "flop_per_env_step": flop_step,
+                    "hbm_gbs_achieved": hbm_ach, "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src}
+    chunk_used = args.chunk if args.warps else 100
+    launches = args.steps * (parts_used * -(-horizon // max(1, min(chunk_used, horizon)))
+                             if parts_used > 1 else 1)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -556,15 +594,8 @@ def main():
                        "rollout_warps_per_block": tuned,
                        "rollout_engine": packed_used,
                        "rollout_partitions": parts_used},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                         "traffic": (None if NCU_DRAM_BYTES_PER_ENV_STEP is None
-                                     else NCU_DRAM_BYTES_PER_ENV_STEP * n * horizon),
-                         "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
-                         "flop_per_env_step": flop_step,
-                         "hbm_gbs_achieved": n * horizon * BYTES_STEP / (sum(ms) / args.steps * 1e-3) / 1e9,
-                         "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src},
-            "clocks": clocks, "e2e": e2e, "gpu_launches": args.steps,
+            "roofline": roofline,
+            "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
             "cpu_baseline": cpu, "step_ms": ms, "wall_s": wall,
         }
         line.update(extras)

@@ -5,8 +5,12 @@
 // replay write, state in registers, one thread per env); what changes is where the
 // 82 -> 64 -> 64 products run:
 //   * a tile is 128 envs = the MMA's M = the 128 TMEM lanes; thread r of the tile owns env
-//     r and TMEM lane r.  A CTA holds two tiles (8 warps) that run independently, so one
-//     tile's SIMT work (dynamics, Philox, epilogues) overlaps the other tile's MMAs.
+//     r and TMEM lane r.  A CTA holds two tiles of 4 compute warps each plus one MMA warp
+//     per tile (warp specialisation): issuing a tcgen05.mma costs its thread ~85 cycles
+//     whatever N, so the 57 MMAs of a step are issued by the tile's MMA warp while the
+//     compute warps draw the step's exploration noise and write the previous step's replay
+//     record; compute and MMA warps hand over through mbarriers (A1 ready, D1 full, A2
+//     ready, D2 full).  The two tiles run independently.
 //   * FP32 accuracy from TF32 inputs by the three-term split x = x_hi + x_lo (x_hi: x with
 //     the low 13 mantissa bits cleared, x_lo = x - x_hi exactly): A.W ~ A_hi.W_hi +
 //     A_hi.W_lo + A_lo.W_hi, all accumulated in FP32 in tensor memory; the dropped
@@ -21,8 +25,9 @@
 //     64 -> 4 output layer in registers (SIMT), tanh.
 // Shared-memory operands use the no-swizzle K-major layout: 8-row x 16-byte core matrices,
 // K-adjacent core matrices 128 B apart (LBO), 8-row groups kc * 128 B apart (SBO).
-// Every wait on an MMA completion is bounded; on expiry the tile records DEV_TIMEOUT in the
-// status word, stops issuing work and leaves the step loop; TMEM is freed on every path.
+// Every hand-over wait is bounded; on expiry the waiting warp records DEV_TIMEOUT in the
+// status word and raises the CTA's abort flag, every warp leaves its step loop at its next
+// wait, and TMEM is freed on every path.
 #include <algorithm>
 
 #include "qsim_internal.h"
@@ -33,7 +38,8 @@ namespace tcr {
 constexpr int H = 64;            // hidden width handled here
 constexpr int TILE = 128;        // envs per tile
 constexpr int TILES = 2;         // tiles per CTA
-constexpr int NT = TILE * TILES; // threads per CTA
+constexpr int NCW = TILE * TILES / 32;  // compute warps per CTA
+constexpr int NT = TILE * TILES + 32 * TILES;  // threads per CTA: compute + one MMA warp per tile
 constexpr int K1 = 88;           // layer-1 A columns
 constexpr int KW1 = 92;          // layer-1 B columns: 24 + 17 lag blocks of 4
 constexpr int KC1 = KW1 / 4;     // core-matrix columns of W1
@@ -53,14 +59,14 @@ constexpr int OFF_B1 = OFF_A2 + TILES * 2 * SZ_A2;
 constexpr int OFF_B2 = OFF_B1 + 4 * H;
 constexpr int OFF_W3 = OFF_B2 + 4 * H;  // [H] float4: W3[0..3][j]
 constexpr int OFF_B3 = OFF_W3 + 16 * H;
-constexpr int OFF_BAR = OFF_B3 + 16;     // TILES mbarriers
-constexpr int OFF_TSLOT = OFF_BAR + 8 * TILES;
+constexpr int OFF_BAR = OFF_B3 + 16;     // per tile: A1 ready, D1 full, A2 ready, D2 full
+constexpr int OFF_TSLOT = OFF_BAR + 32 * TILES;
 constexpr int OFF_ABORT = OFF_TSLOT + 16;
 constexpr int SMEM = OFF_ABORT + 16;
 static_assert(SMEM <= 227 * 1024, "tensor-core rollout: shared memory");
 static_assert(OFF_W1LO % 128 == 0 && OFF_W2HI % 128 == 0 && OFF_A2 % 128 == 0, "alignment");
 
-constexpr int WAIT_LIMIT = 1 << 22;  // polls of an MMA-completion barrier before giving up
+constexpr int WAIT_LIMIT = 1 << 22;  // polls of a hand-over barrier before giving up
 
 // instruction descriptor: D f32, A and B tf32, both K-major, N = 64, M = 128
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(H >> 3) << 17) |
@@ -99,22 +105,39 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait for the completion of phase `parity` of an mbarrier; gives up early once the
+// CTA's abort flag is set.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
     for (int i = 0; i < WAIT_LIMIT; ++i) {
         uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
         if (done) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
     }
     return false;
+}
+
+// Lane 0 waits, the warp follows; false (warp-uniform) when the wait gave up.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        ok = mbar_wait(bar, parity, abort_flag);
+        if (!ok) {
+            *abort_flag = 1;
+            if (status) atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+        }
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tile_bar(int tile) {
-    asm volatile("bar.sync %0, %1;" :: "r"(1 + tile), "r"(TILE) : "memory");
-}
 
 #define QSIM_R4(v, o) "r"(__float_as_uint(v[o])), "r"(__float_as_uint(v[o + 1])), "r"(__float_as_uint(v[o + 2])), "r"(__float_as_uint(v[o + 3]))
 
@@ -188,7 +211,8 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smb + OFF_ABORT);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tile = warp >> 2, r = tid & (TILE - 1);
+    const bool mma_warp = warp >= NCW;
+    const int tile = mma_warp ? warp - NCW : warp >> 2;
     const int DA = C.obs_dim, nh = C.n_hist, ld = C.ld;
 
     // ---- stage W1 (lag-reversed, padded), W2 as hi / lo halves; b1, b2, W3, b3
@@ -227,13 +251,17 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
         }
         if (tid < 4) sB3[tid] = gb3[tid];
         if (tid == 0) {
-            for (int k = 0; k < TILES; ++k)
-                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(smb + OFF_BAR + 8 * k)));
+            for (int k = 0; k < TILES; ++k) {
+                const uint32_t b0 = smem_addr(smb + OFF_BAR + 32 * k);
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b0), "r"(4));        // A1 ready
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b0 + 8), "r"(1));    // D1 full
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b0 + 16), "r"(4));   // A2 ready
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(b0 + 24), "r"(1));   // D2 full
+            }
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            abort_flag[0] = 0;
-            abort_flag[1] = 0;
+            *abort_flag = 0;
         }
-        if (warp == 0) {
+        if (warp == NCW) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                          :: "r"(smem_addr(tslot)), "r"(TILES * T_COLS) : "memory");
             asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -243,100 +271,26 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
         __syncthreads();
         fence_after();
     }
-    const uint32_t tmem = *tslot + (uint32_t)(tile * T_COLS);            // this tile's columns, lane 0
-    const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);      // this warp's lanes
-    const uint32_t bar = smem_addr(smb + OFF_BAR + 8 * tile);
-    const uint32_t sW1hi = smem_addr(W1hi), sW1lo = smem_addr(W1lo);
-    const uint32_t sW2hi = smem_addr(W2hi), sW2lo = smem_addr(W2lo);
+    const uint32_t tmem = *tslot + (uint32_t)(tile * T_COLS);  // this tile's columns, lane 0
+    const uint32_t bar_a1 = smem_addr(smb + OFF_BAR + 32 * tile);
+    const uint32_t bar_d1 = bar_a1 + 8, bar_a2 = bar_a1 + 16, bar_d2 = bar_a1 + 24;
     float* A2hi = reinterpret_cast<float*>(smb + OFF_A2 + (2 * tile) * SZ_A2);
     float* A2lo = reinterpret_cast<float*>(smb + OFF_A2 + (2 * tile + 1) * SZ_A2);
-    const uint32_t sA2hi = smem_addr(A2hi), sA2lo = smem_addr(A2lo);
-    const bool leader = (warp & 3) == 0 && lane == 0;
 
-    const int gw = warp0 + blockIdx.x * (NT / 32) + warp;  // global warp (32 envs)
-    const bool active = gw < warp_end;                       // warp-uniform
-    const int g = active ? gw * 32 + lane : lane;            // inactive warps: an in-range index, never stored to
-
-    // ---- per-env state into registers (inactive warps: a benign copy of nothing)
-    float s[NS], d[6];
-    Prm P = make_prm(1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f);
-    uint32_t ep_index = 0, ep_step = 0, n_done = 0, len_sum = 0;
-    float ep_ret = 0.0f, ret_sum = 0.0f;
-#pragma unroll
-    for (int i = 0; i < NS; ++i) s[i] = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) d[i] = 0.0f;
-    s[3] = 1.0f;
-    if (active) {
-#pragma unroll
-        for (int i = 0; i < NS; ++i) s[i] = p.state[i * ld + g];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) d[i] = p.dist[i * ld + g];
-        P = make_prm(p.prm[g], p.prm[ld + g], p.prm[2 * ld + g], p.prm[3 * ld + g], p.prm[4 * ld + g],
-                     p.prm[5 * ld + g], p.prm[6 * ld + g]);
-        ep_index = p.ep_index[g]; ep_step = p.ep_step[g];
-        n_done = p.n_done[g]; len_sum = p.len_sum[g];
-        ep_ret = p.ep_ret[g]; ret_sum = p.ret_sum[g];
-    }
-    float Cr[7];
-#pragma unroll
-    for (int i = 0; i < 7; ++i) Cr[i] = p.rewardC[i];
-    const float sigma = sigma_in >= 0.0f ? sigma_in : p.rewardC[7];
-    // action ring: slot (t0 - i) mod 16 holds a_{t0-i} (global history is newest first)
+    if (mma_warp) {
+        // ================= MMA warp of this tile: lane 0 issues, the warp follows the waits
+        const uint32_t sW1hi = smem_addr(W1hi), sW1lo = smem_addr(W1lo);
+        const uint32_t sW2hi = smem_addr(W2hi), sW2lo = smem_addr(W2lo);
+        const uint32_t sA2hi = smem_addr(A2hi), sA2lo = smem_addr(A2lo);
+        uint32_t ph = 0;
+        int issued = 0;  // 0: nothing in flight, 1: layer 1 committed, 2: layer 2 committed
 #pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-        float x[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int sl = 4 * q + (j >> 2), c = j & 3;
-            const int i = (int)((t0 - (uint32_t)sl) & 15u) == 0 ? 16 : (int)((t0 - (uint32_t)sl) & 15u);
-            x[j] = 0.0f;
-            if (active && i <= nh) x[j] = p.hist[(4 * (i - 1) + c) * ld + g];
-        }
-        ring_store16(tl + T_AHI + 24 + 16 * q, tl + T_ALO + 24 + 16 * q, x);
-    }
-    int64_t slot = capacity > 0 ? head0 % capacity : 0;
-    const int F = C.F;
-    uint32_t phase = 0;
-
-#pragma unroll 1
-    for (int tt = 0; tt < T; ++tt) {
-        const uint32_t t = t0 + (uint32_t)tt;
-        float a[4];
-        if ((int64_t)t < (int64_t)C.learning_starts) {
-            const uint4 rr = draw(C, (uint32_t)g, t, TAG_WARM, 0);
-            a[0] = 2.0f * u01(rr.x) - 1.0f;
-            a[1] = 2.0f * u01(rr.y) - 1.0f;
-            a[2] = 2.0f * u01(rr.z) - 1.0f;
-            a[3] = 2.0f * u01(rr.w) - 1.0f;
-        } else {
-            // ---------------- observation -> A columns 0..23 (hi / lo)
-            {
-                float o[24];
-                obs_state(s, o);
-                if (C.any_noise) {
-                    float nz[18];
-                    obs_noise(C, (uint32_t)g, t, nz);
-#pragma unroll
-                    for (int k = 0; k < 18; ++k) o[k] += nz[k];
-                }
-#pragma unroll
-                for (int k = 18; k < 24; ++k) o[k] = 0.0f;
-                float hi[24], lo[24];
-#pragma unroll
-                for (int k = 0; k < 24; ++k) { hi[k] = tf32_hi(o[k]); lo[k] = o[k] - hi[k]; }
-                st16(tl + T_AHI, hi);
-                st8(tl + T_AHI + 16, hi + 16);
-                st16(tl + T_ALO, lo);
-                st8(tl + T_ALO + 16, lo + 16);
-                wait_st();
-            }
-            fence_before();
-            tile_bar(tile);
-            if (abort_flag[tile]) break;
-            // ---------------- layer 1: D = A . W1^T over 11 K-steps x 3 products
-            if (leader) {
-                fence_after();
+        for (int tt = 0; tt < T; ++tt) {
+            const uint32_t t = t0 + (uint32_t)tt;
+            if ((int64_t)t < (int64_t)C.learning_starts) continue;
+            if (!warp_wait(bar_a1, ph, abort_flag, p.status)) break;
+            fence_after();
+            if (lane == 0) {
 #pragma unroll 1
                 for (int j = 0; j < K1 / 8; ++j) {
                     int wcol;  // first W1 column of this K-step
@@ -352,40 +306,13 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     mma_tt(tmem + T_D, tmem + T_AHI + 8 * j, blo, 1);
                     mma_tt(tmem + T_D, tmem + T_ALO + 8 * j, bhi, 1);
                 }
-                mma_commit(bar);
+                mma_commit(bar_d1);
             }
-            if (!mbar_wait(bar, phase)) {
-                abort_flag[tile] = 1 + (int)phase;
-                if (p.status) atomicCAS(p.status, DEV_OK, DEV_TIMEOUT);
-            }
-            phase ^= 1u;
+            __syncwarp();
+            issued = 1;
+            if (!warp_wait(bar_a2, ph, abort_flag, p.status)) break;
             fence_after();
-            // ---------------- epilogue 1: bias, ReLU, split -> A2 (shared memory)
-#pragma unroll 1
-            for (int c0 = 0; c0 < H; c0 += 16) {
-                float v[16];
-                ld16(tl + T_D + c0, v);
-                float hv[16], lv[16];
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const float x = fmaxf(v[e] + sB1[c0 + e], 0.0f);
-                    hv[e] = tf32_hi(x);
-                    lv[e] = x - hv[e];
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int off = cano(r, c0 + 4 * q, KC2);
-                    *reinterpret_cast<float4*>(A2hi + off) = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
-                    *reinterpret_cast<float4*>(A2lo + off) = make_float4(lv[4 * q], lv[4 * q + 1], lv[4 * q + 2], lv[4 * q + 3]);
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            fence_before();
-            tile_bar(tile);
-            if (abort_flag[tile]) break;
-            // ---------------- layer 2: D = A2 . W2^T over 8 K-steps x 3 products
-            if (leader) {
-                fence_after();
+            if (lane == 0) {
 #pragma unroll 1
                 for (int j = 0; j < H / 8; ++j) {
                     const uint32_t ko = (uint32_t)(2 * j) * 128u;
@@ -395,132 +322,276 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     mma_ss(tmem + T_D, ahi, blo, 1);
                     mma_ss(tmem + T_D, alo, bhi, 1);
                 }
-                mma_commit(bar);
+                mma_commit(bar_d2);
             }
-            if (!mbar_wait(bar, phase)) {
-                abort_flag[tile] = 1 + (int)phase;
-                if (p.status) atomicCAS(p.status, DEV_OK, DEV_TIMEOUT);
-            }
-            phase ^= 1u;
-            fence_after();
-            // ---------------- epilogue 2 + output layer (64 -> 4), tanh
-            float pp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll 1
-            for (int c0 = 0; c0 < H; c0 += 16) {
-                float v[16];
-                ld16(tl + T_D + c0, v);
-#pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const float hcur = fmaxf(v[e] + sB2[c0 + e], 0.0f);
-                    const float4 w3 = sW3[c0 + e];
-                    pp[0] = fmaf(w3.x, hcur, pp[0]);
-                    pp[1] = fmaf(w3.y, hcur, pp[1]);
-                    pp[2] = fmaf(w3.z, hcur, pp[2]);
-                    pp[3] = fmaf(w3.w, hcur, pp[3]);
-                }
-            }
-            float mu[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) mu[j] = tanhf(pp[j] + sB3[j]);
-            if (sigma > 0.0f) {
-                const uint4 r0 = draw(C, (uint32_t)g, t, TAG_EXPL, 0);
-                const uint4 r1 = draw(C, (uint32_t)g, t, TAG_EXPL, 1);
-                a[0] = clampf(fmaf(sigma, gauss(r0.x, r0.y), mu[0]), -1.0f, 1.0f);
-                a[1] = clampf(fmaf(sigma, gauss(r0.z, r0.w), mu[1]), -1.0f, 1.0f);
-                a[2] = clampf(fmaf(sigma, gauss(r1.x, r1.y), mu[2]), -1.0f, 1.0f);
-                a[3] = clampf(fmaf(sigma, gauss(r1.z, r1.w), mu[3]), -1.0f, 1.0f);
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) a[j] = clampf(mu[j], -1.0f, 1.0f);
+            __syncwarp();
+            issued = 2;
+            ph ^= 1u;
+        }
+        // on an abort, let the last committed batch finish before the memory is released
+        if (*abort_flag && lane == 0 && issued) {
+            for (int i = 0; i < WAIT_LIMIT; ++i) {
+                uint32_t done;
+                const uint32_t b = issued == 1 ? bar_d1 : bar_d2;
+                const uint32_t par = issued == 1 ? ph : ph ^ 1u;
+                asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                             "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(b), "r"(par) : "memory");
+                if (done) break;
             }
         }
-        // ---------------- dynamics, reward, termination
-        float u[4], s2[NS];
-        action_to_rpm(C.veh, a, u);
+    } else {
+        // ================= compute warps: thread r of the tile owns env r and TMEM lane r
+        const int r = tid & (TILE - 1);
+        const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
+        const int gw = warp0 + blockIdx.x * NCW + warp;                  // global warp (32 envs)
+        const bool active = gw < warp_end;                               // warp-uniform
+        const int g = active ? gw * 32 + lane : lane;  // inactive warps: an in-range index, never stored to
+
+        float s[NS], d[6];
+        Prm P = make_prm(1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f);
+        uint32_t ep_index = 0, ep_step = 0, n_done = 0, len_sum = 0;
+        float ep_ret = 0.0f, ret_sum = 0.0f;
 #pragma unroll
-        for (int i = 0; i < NS; ++i) s2[i] = s[i];
-        rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
-        const float rw = reward(Cr, s2, a);
-        const bool term = terminated(C, s2);
-        const uint32_t ep_after = ep_step + 1;
-        const bool trunc = !term && (int)ep_after >= C.episode_len;
-        // ---------------- transition record (field-major, streaming stores)
-        if (capacity > 0) {
-            if (active) {
-                float* rec = p.rec + (size_t)slot * F * ld + g;
+        for (int i = 0; i < NS; ++i) s[i] = 0.0f;
 #pragma unroll
-                for (int i = 0; i < NS; ++i) __stcs(rec + i * ld, s[i]);
+        for (int i = 0; i < 6; ++i) d[i] = 0.0f;
+        s[3] = 1.0f;
+        if (active) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) __stcs(rec + (17 + i) * ld, a[i]);
-                __stcs(rec + 21 * ld, rw);
-                __stcs(rec + 22 * ld, __uint_as_float(pack_flags(term, trunc, ep_step)));
+            for (int i = 0; i < NS; ++i) s[i] = p.state[i * ld + g];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) d[i] = p.dist[i * ld + g];
+            P = make_prm(p.prm[g], p.prm[ld + g], p.prm[2 * ld + g], p.prm[3 * ld + g], p.prm[4 * ld + g],
+                         p.prm[5 * ld + g], p.prm[6 * ld + g]);
+            ep_index = p.ep_index[g]; ep_step = p.ep_step[g];
+            n_done = p.n_done[g]; len_sum = p.len_sum[g];
+            ep_ret = p.ep_ret[g]; ret_sum = p.ret_sum[g];
+        }
+        float Cr[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) Cr[i] = p.rewardC[i];
+        const float sigma = sigma_in >= 0.0f ? sigma_in : p.rewardC[7];
+        // action ring: slot (t0 - i) mod 16 holds a_{t0-i} (global history is newest first)
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+            float x[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int sl = 4 * q + (j >> 2), c = j & 3;
+                const int i0 = (int)((t0 - (uint32_t)sl) & 15u);
+                const int i = i0 == 0 ? 16 : i0;
+                x[j] = 0.0f;
+                if (active && i <= nh) x[j] = p.hist[(4 * (i - 1) + c) * ld + g];
+            }
+            ring_store16(tl + T_AHI + 24 + 16 * q, tl + T_ALO + 24 + 16 * q, x);
+        }
+        int64_t slot = capacity > 0 ? head0 % capacity : 0;
+        const int F = C.F;
+        uint32_t ph = 0;
+        // the previous step's transition, written while the next step's MMAs run
+        bool pend = false;
+        float ps[NS], ps2[NS], pa[4], pr = 0.0f;
+        uint32_t pflags = 0;
+        int64_t pslot = 0;
+        Prm pP = P;
+        float pd[6];
+        auto flush = [&]() {
+            if (pend && capacity > 0 && active) {
+                float* rec = p.rec + (size_t)pslot * F * ld + g;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) __stcs(rec + i * ld, ps[i]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) __stcs(rec + (17 + i) * ld, pa[i]);
+                __stcs(rec + 21 * ld, pr);
+                __stcs(rec + 22 * ld, __uint_as_float(pflags));
                 if (C.n_priv) {
                     float pv[NPRIV];
-                    priv_vals(C, P, d, pv);
+                    priv_vals(C, pP, pd, pv);
 #pragma unroll
                     for (int k = 0; k < NPRIV; ++k) __stcs(rec + (23 + k) * ld, pv[k]);
                 }
-                if (term || trunc) {
-                    float* sd = p.side + (size_t)slot * NS * ld + g;
+                if (pflags & 3u) {
+                    float* sd = p.side + (size_t)pslot * NS * ld + g;
 #pragma unroll
-                    for (int i = 0; i < NS; ++i) __stcs(sd + i * ld, s2[i]);
+                    for (int i = 0; i < NS; ++i) __stcs(sd + i * ld, ps2[i]);
                 }
             }
-            slot = (slot + 1 == capacity) ? 0 : slot + 1;
-        }
-        // ---------------- action ring: a_t into slot t mod 16; an episode end clears the ring
-        const bool reset = term || trunc;
-        const int hs = (int)(t & 15u);
-        if (!__any_sync(0xffffffffu, reset)) {
-            float hi[4], lo[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) { hi[c] = tf32_hi(a[c]); lo[c] = a[c] - hi[c]; }
-            st4(tl + T_AHI + 24 + 4 * hs, hi);
-            st4(tl + T_ALO + 24 + 4 * hs, lo);
-        } else {
-#pragma unroll 1
-            for (int q = 0; q < 4; ++q) {
-                float vh[16], vl[16], x[16];
-                ld16x2(tl + T_AHI + 24 + 16 * q, vh, tl + T_ALO + 24 + 16 * q, vl);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int sl = 4 * q + (j >> 2);
-                    x[j] = reset ? 0.0f : (sl == hs ? a[j & 3] : vh[j] + vl[j]);
-                }
-                ring_store16(tl + T_AHI + 24 + 16 * q, tl + T_ALO + 24 + 16 * q, x);
-            }
-        }
-        ep_ret += rw;
-        if (reset) {
-            n_done += 1;
-            len_sum += ep_after;
-            ret_sum += ep_ret;
-            ep_index += 1;
-            float prm7[7];
-            reset_env(C, (uint32_t)g, ep_index, s, prm7, d);
-            P = make_prm(prm7[0], prm7[1], prm7[2], prm7[3], prm7[4], prm7[5], prm7[6]);
-            ep_step = 0;
-            ep_ret = 0.0f;
-        } else {
-#pragma unroll
-            for (int i = 0; i < NS; ++i) s[i] = s2[i];
-            ep_step = ep_after;
-        }
-    }
-    wait_st();
+            pend = false;
+        };
 
-    // ---- write back (state, parameters, counters, history newest first)
-    if (active) {
+#pragma unroll 1
+        for (int tt = 0; tt < T; ++tt) {
+            const uint32_t t = t0 + (uint32_t)tt;
+            float a[4];
+            if ((int64_t)t < (int64_t)C.learning_starts) {
+                flush();
+                const uint4 rr = draw(C, (uint32_t)g, t, TAG_WARM, 0);
+                a[0] = 2.0f * u01(rr.x) - 1.0f;
+                a[1] = 2.0f * u01(rr.y) - 1.0f;
+                a[2] = 2.0f * u01(rr.z) - 1.0f;
+                a[3] = 2.0f * u01(rr.w) - 1.0f;
+            } else {
+                // ---------------- observation -> A columns 0..23 (hi / lo); hand over
+                {
+                    float o[24];
+                    obs_state(s, o);
+                    if (C.any_noise) {
+                        float nz[18];
+                        obs_noise(C, (uint32_t)g, t, nz);
 #pragma unroll
-        for (int i = 0; i < NS; ++i) p.state[i * ld + g] = s[i];
-        p.prm[g] = P.m; p.prm[ld + g] = P.Jx; p.prm[2 * ld + g] = P.Jy; p.prm[3 * ld + g] = P.Jz;
-        p.prm[4 * ld + g] = P.kf; p.prm[5 * ld + g] = P.km; p.prm[6 * ld + g] = P.tm;
+                        for (int k = 0; k < 18; ++k) o[k] += nz[k];
+                    }
 #pragma unroll
-        for (int i = 0; i < 6; ++i) p.dist[i * ld + g] = d[i];
-        p.ep_index[g] = ep_index; p.ep_step[g] = ep_step; p.ep_ret[g] = ep_ret;
-        p.n_done[g] = n_done; p.len_sum[g] = len_sum; p.ret_sum[g] = ret_sum;
-    }
-    {
+                    for (int k = 18; k < 24; ++k) o[k] = 0.0f;
+                    float hi[24], lo[24];
+#pragma unroll
+                    for (int k = 0; k < 24; ++k) { hi[k] = tf32_hi(o[k]); lo[k] = o[k] - hi[k]; }
+                    st16(tl + T_AHI, hi);
+                    st8(tl + T_AHI + 16, hi + 16);
+                    st16(tl + T_ALO, lo);
+                    st8(tl + T_ALO + 16, lo + 16);
+                    wait_st();
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_a1);
+                // ---------------- while layer 1 runs: exploration noise, last step's record
+                float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                if (sigma > 0.0f) {
+                    const uint4 r0 = draw(C, (uint32_t)g, t, TAG_EXPL, 0);
+                    const uint4 r1 = draw(C, (uint32_t)g, t, TAG_EXPL, 1);
+                    z[0] = gauss(r0.x, r0.y); z[1] = gauss(r0.z, r0.w);
+                    z[2] = gauss(r1.x, r1.y); z[3] = gauss(r1.z, r1.w);
+                }
+                flush();
+                if (!warp_wait(bar_d1, ph, abort_flag, p.status)) break;
+                fence_after();
+                // ---------------- epilogue 1: bias, ReLU, split -> A2 (shared memory); hand over
+#pragma unroll 1
+                for (int c0 = 0; c0 < H; c0 += 32) {
+                    float v[32];
+                    ld16x2(tl + T_D + c0, v, tl + T_D + c0 + 16, v + 16);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float hv[4], lv[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float x = fmaxf(v[4 * q + e] + sB1[c0 + 4 * q + e], 0.0f);
+                            hv[e] = tf32_hi(x);
+                            lv[e] = x - hv[e];
+                        }
+                        const int off = cano(r, c0 + 4 * q, KC2);
+                        *reinterpret_cast<float4*>(A2hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+                        *reinterpret_cast<float4*>(A2lo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_a2);
+                if (!warp_wait(bar_d2, ph, abort_flag, p.status)) break;
+                fence_after();
+                ph ^= 1u;
+                // ---------------- epilogue 2 + output layer (64 -> 4), tanh
+                float pp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 1
+                for (int c0 = 0; c0 < H; c0 += 32) {
+                    float v[32];
+                    ld16x2(tl + T_D + c0, v, tl + T_D + c0 + 16, v + 16);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const float hcur = fmaxf(v[e] + sB2[c0 + e], 0.0f);
+                        const float4 w3 = sW3[c0 + e];
+                        pp[0] = fmaf(w3.x, hcur, pp[0]);
+                        pp[1] = fmaf(w3.y, hcur, pp[1]);
+                        pp[2] = fmaf(w3.z, hcur, pp[2]);
+                        pp[3] = fmaf(w3.w, hcur, pp[3]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float mu = tanhf(pp[j] + sB3[j]);
+                    a[j] = clampf(sigma > 0.0f ? fmaf(sigma, z[j], mu) : mu, -1.0f, 1.0f);
+                }
+            }
+            // ---------------- dynamics, reward, termination
+            float u[4], s2[NS];
+            action_to_rpm(C.veh, a, u);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) s2[i] = s[i];
+            rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
+            const float rw = reward(Cr, s2, a);
+            const bool term = terminated(C, s2);
+            const uint32_t ep_after = ep_step + 1;
+            const bool trunc = !term && (int)ep_after >= C.episode_len;
+            // ---------------- transition: kept for the next step's MMA shadow
+            if (capacity > 0) {
+                pend = true;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) { ps[i] = s[i]; ps2[i] = s2[i]; }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) pa[i] = a[i];
+                pr = rw;
+                pflags = pack_flags(term, trunc, ep_step);
+                pslot = slot;
+                pP = P;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) pd[i] = d[i];
+                slot = (slot + 1 == capacity) ? 0 : slot + 1;
+            }
+            // ---------------- action ring: a_t into slot t mod 16; an episode end clears the ring
+            const bool reset = term || trunc;
+            const int hs = (int)(t & 15u);
+            if (!__any_sync(0xffffffffu, reset)) {
+                float hi[4], lo[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) { hi[c] = tf32_hi(a[c]); lo[c] = a[c] - hi[c]; }
+                st4(tl + T_AHI + 24 + 4 * hs, hi);
+                st4(tl + T_ALO + 24 + 4 * hs, lo);
+            } else {
+#pragma unroll 1
+                for (int q = 0; q < 4; ++q) {
+                    float vh[16], vl[16], x[16];
+                    ld16x2(tl + T_AHI + 24 + 16 * q, vh, tl + T_ALO + 24 + 16 * q, vl);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int sl = 4 * q + (j >> 2);
+                        x[j] = reset ? 0.0f : (sl == hs ? a[j & 3] : vh[j] + vl[j]);
+                    }
+                    ring_store16(tl + T_AHI + 24 + 16 * q, tl + T_ALO + 24 + 16 * q, x);
+                }
+            }
+            ep_ret += rw;
+            if (reset) {
+                n_done += 1;
+                len_sum += ep_after;
+                ret_sum += ep_ret;
+                ep_index += 1;
+                float prm7[7];
+                reset_env(C, (uint32_t)g, ep_index, s, prm7, d);
+                P = make_prm(prm7[0], prm7[1], prm7[2], prm7[3], prm7[4], prm7[5], prm7[6]);
+                ep_step = 0;
+                ep_ret = 0.0f;
+            } else {
+#pragma unroll
+                for (int i = 0; i < NS; ++i) s[i] = s2[i];
+                ep_step = ep_after;
+            }
+        }
+        flush();
+        wait_st();
+
+        // ---- write back (state, parameters, counters, history newest first)
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < NS; ++i) p.state[i * ld + g] = s[i];
+            p.prm[g] = P.m; p.prm[ld + g] = P.Jx; p.prm[2 * ld + g] = P.Jy; p.prm[3 * ld + g] = P.Jz;
+            p.prm[4 * ld + g] = P.kf; p.prm[5 * ld + g] = P.km; p.prm[6 * ld + g] = P.tm;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) p.dist[i * ld + g] = d[i];
+            p.ep_index[g] = ep_index; p.ep_step[g] = ep_step; p.ep_ret[g] = ep_ret;
+            p.n_done[g] = n_done; p.len_sum[g] = len_sum; p.ret_sum[g] = ret_sum;
+        }
         const uint32_t t_end = t0 + (uint32_t)T;
 #pragma unroll 1
         for (int q = 0; q < 4; ++q) {
@@ -537,16 +608,15 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
             }
         }
     }
-    // ---- release tensor memory (after any MMA still in flight on an aborted tile)
-    if (leader && abort_flag[tile]) (void)mbar_wait(bar, (uint32_t)(abort_flag[tile] - 1));
+    // ---- release tensor memory
     fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 0)
+    if (warp == NCW)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(*tslot), "r"(TILES * T_COLS) : "memory");
 }
 
-// Launches T steps on warps [w0, w1) of the env set (8 warps = 256 envs per CTA).
+// Launches T steps on env warps [w0, w1) (8 env warps = 256 envs per CTA, plus 2 MMA warps).
 qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, uint32_t t0, int64_t head,
                                     float sigma, int w0, int w1, cudaStream_t st) {
     static bool configured = false;
@@ -554,7 +624,7 @@ qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, u
         QCHECK_CUDA(cudaFuncSetAttribute(k_rollout_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
         configured = true;
     }
-    const int grid = (w1 - w0 + NT / 32 - 1) / (NT / 32);
+    const int grid = (w1 - w0 + NCW - 1) / NCW;
     k_rollout_tc<<<grid, NT, SMEM, st>>>(h->dc, h->p, actor, T, t0, head, h->capacity, sigma, w0, w1);
     QCHECK_LAUNCH("k_rollout_tc");
     return QSIM_OK;
