@@ -33,10 +33,10 @@ sys.path.insert(0, ROOT)
 METRIC = ("env-steps/s (sim+policy) and wall time to N actor-critic updates on 1 GB300, "
           "vs plain")
 FLOP_ACTOR = lambda da, h: 2 * (da * h + h * h + 4 * h)  # noqa: E731
-# tensor-core engine: the two hidden layers as TF32 MMAs with the hi/lo split, three
-# products per FP32-accurate product (A_hi W_hi + A_hi W_lo + A_lo W_hi)
+# tensor-core engine: the two hidden layers as fp16 MMAs on hi/lo halves, three products
+# per FP32-accurate product (A_hi W_hi + A_hi W_lo + A_lo W_hi); fp16 and bf16 dense
+# tensor rates are equal on this part, so the measured bf16 peak is the fp16 peak
 FLOP_TC_MMA = lambda da, h: 3 * 2 * (da * h + h * h)  # noqa: E731
-TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 tensor rate of the part
 FLOP_DYN = 672        # RK4 (4 derivative evaluations + stage/accumulation arithmetic)
 FLOP_MISC = 60        # observation rotation matrix, reward, termination, action map
 BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, flags)
@@ -45,7 +45,7 @@ BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, fl
 # Set to None whenever the kernel changes until it is captured again.
 NCU_DRAM_BYTES_PER_ENV_STEP = (46.710016e6 + 289.403648e6) / (32768 * 100)
 # same for the tensor-core kernel k_rollout_tc (profiles/k_rollout_tc_c2_65536x1000.md)
-NCU_DRAM_BYTES_PER_ENV_STEP_TC = (35.136512e6 + 97.005312e6) / (65536 * 20)
+NCU_DRAM_BYTES_PER_ENV_STEP_TC = None
 
 
 def parse():
@@ -148,8 +148,7 @@ def device_peaks(torch, q):
         hbm, hbm_src = 6800.0, "fallback"
         bf16_sus, tc_src = 1700.0, "fallback"
     fp32 = sms * 128 * 2 * max_mhz * 1e6 / 1e12
-    tf32 = bf16_sus * TF32_PER_BF16
-    return sms, max_mhz, fp32, hbm, hbm_src, tf32, tc_src
+    return sms, max_mhz, fp32, hbm, hbm_src, bf16_sus, tc_src
 
 
 # -------------------------------------------------------------------------- measurements
@@ -509,7 +508,7 @@ def main():
         dist.barrier()
     env_steps = n * horizon * args.steps * world
     value = env_steps / t_dev
-    sms, max_mhz, fp32_peak, hbm, hbm_src, tf32_peak, tc_src = device_peaks(torch, q)
+    sms, max_mhz, fp32_peak, hbm, hbm_src, f16_peak, tc_src = device_peaks(torch, q)
     flop_step = FLOP_ACTOR(82, hidden) + FLOP_DYN + FLOP_MISC
     achieved = n * horizon * flop_step / (sum(ms) / args.steps * 1e-3) / 1e12
     clocks = clk.summary()
@@ -555,12 +554,12 @@ def main():
         # tensor-core engine: the dominant unit is the tensor pipe (TF32 MMAs)
         tc_flop = FLOP_TC_MMA(82, hidden)
         ach = n * horizon * tc_flop / step_s / 1e12
-        roofline = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
-                    "frac": ach / tf32_peak,
+        roofline = {"bound": "tensor", "achieved": ach, "peak": f16_peak, "unit": "TFLOP/s",
+                    "frac": ach / f16_peak,
                     "traffic": (None if NCU_DRAM_BYTES_PER_ENV_STEP_TC is None
                                 else NCU_DRAM_BYTES_PER_ENV_STEP_TC * n * horizon),
-                    "peak_source": f"TF32 dense, sustained: {tc_src} bf16 sustained x {TF32_PER_BF16:.3f} "
-                                   "(nominal TF32:BF16)",
+                    "peak_source": f"fp16 dense tensor, sustained ({tc_src} bf16 sustained; equal rates)",
+                    "mma_instructions_per_env_step": 30 / 128,
                     "flop_per_env_step": tc_flop,
                     "fp32_equivalent_tflops": ach / 3,
                     "simt_fp32_tflops": n * horizon * (FLOP_DYN + FLOP_MISC + 2 * 4 * hidden) / step_s / 1e12,

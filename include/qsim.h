@@ -226,8 +226,10 @@ int32_t qsim_rollout_packed(qsim_handle* h, int32_t packed);  /* engines 0/1 of 
 
 /* Rollout engine: 0 the SIMT kernel (scalar FMA), 1 the SIMT kernel with paired FMA (same
  * results as 0), 2 the tensor-core kernel (hidden = 64 only: the two hidden layers as
- * tcgen05 TF32 MMAs with a three-term hi/lo split that keeps FP32 accuracy, accumulators in
- * tensor memory, 256 envs per block; results agree with 0 to FP32 rounding, not bitwise),
+ * tcgen05 fp16 MMAs on hi/lo halves of every operand, three products per layer that keep
+ * FP32 accuracy, accumulators in tensor memory, 384 envs per block; results agree with 0
+ * to FP32 rounding, not bitwise; an actor input or hidden activation of magnitude >= 65504
+ * is reported by qsim_sync as QSIM_ESTATE),
  * -1 automatic (the autotuner decides; scalar SIMT until it has run).  Any other value
  * leaves the setting unchanged.  Returns the setting in effect.  The paper's environment
  * step has no counterpart of this switch: it selects among kernels computing the same step

@@ -339,7 +339,7 @@ __device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsign
 }
 
 // Device status codes (first error wins).
-enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADSIZE = 2 };
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADSIZE = 2, DEV_RANGE = 3 };
 
 __device__ __forceinline__ void set_status(int* st, int code) {
     if (st) atomicCAS(st, DEV_OK, code);

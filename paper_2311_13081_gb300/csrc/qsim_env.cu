@@ -586,6 +586,9 @@ extern "C" qsim_status qsim_sync(qsim_handle* h) {
     if (st != DEV_OK) {
         cudaMemset(h->p.status, 0, 4);
         if (st == DEV_TIMEOUT) return fail(QSIM_ETIMEOUT, "device-side wait ran out");
+        if (st == DEV_RANGE)
+            return fail(QSIM_ESTATE, "tensor-core rollout: an actor input or hidden activation "
+                                     "exceeded the half-precision range (|x| >= 65504)");
         return fail(QSIM_ESTATE, "device reported status %d", st);
     }
     return QSIM_OK;

@@ -515,8 +515,7 @@ static int resident_warps(int hidden, int nw, int device, bool pk = false) {
     return std::max(1, blocks) * nw * sms;
 }
 
-// Resident CTAs of the tensor-core kernel: one per SM (its shared memory and its 512 TMEM
-// columns both take the whole SM).
+// Resident CTAs of the tensor-core kernel: one per SM (it allocates all 512 TMEM columns).
 static int tc_resident_ctas(int device) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
@@ -536,6 +535,7 @@ static qsim_status ensure_streams(qsim_handle* h) {
 
 qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, uint32_t t0, int64_t head,
                                     float sigma, int w0, int w1, cudaStream_t st);
+int rollout_tc_warps_per_cta();
 
 // Launches T steps of the rollout as `parts` env partitions x chunks of `chunk` steps.
 // Partition p owns warps [W p / parts, W (p+1) / parts); its chunks run in order on its
@@ -639,7 +639,7 @@ extern "C" qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t 
     int parts = h->rollout_parts, chunk = h->rollout_chunk;
     if (parts <= 0) {
         // more than one wave of warps: pipeline two partitions in 100-step chunks
-        const int resident = engine == 2 ? 8 * tc_resident_ctas(h->device)
+        const int resident = engine == 2 ? rollout_tc_warps_per_cta() * tc_resident_ctas(h->device)
                                          : resident_warps(hidden, nw, h->device, engine == 1);
         parts = (h->ld / 32 > resident) ? 2 : 1;
         chunk = parts > 1 ? 100 : 0;
@@ -678,7 +678,7 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
         if (h->rollout_packed >= 0 && pk != h->rollout_packed) continue;
         for (const Sched& sc : scheds) {
             if (((h->t_now + n_steps) >> 32) != 0) break;
-            const int resident = pk == 2 ? 8 * tc_resident_ctas(h->device)
+            const int resident = pk == 2 ? rollout_tc_warps_per_cta() * tc_resident_ctas(h->device)
                                          : resident_warps(hidden, nw, h->device, pk == 1);
             if (sc.parts > 1 && h->ld / 32 <= resident) continue;
             cudaEventRecord(e0, st);
