@@ -128,17 +128,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     return false;
 }
 
-// Lane 0 waits, the warp follows; false (warp-uniform) when the wait gave up.
+// The whole warp waits (try_wait suspends it in hardware between polls), kept uniform by a
+// vote; false (warp-uniform) when the wait gave up.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
-    int ok = 1;
-    if ((threadIdx.x & 31) == 0) {
-        ok = mbar_wait(bar, parity, abort_flag);
-        if (!ok) {
-            *abort_flag = 1;
-            if (status) atomicCAS(status, DEV_OK, DEV_TIMEOUT);
-        }
+    for (int i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t done;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (__any_sync(0xffffffffu, done)) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
     }
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    if ((threadIdx.x & 31) == 0) {
+        *abort_flag = 1;
+        if (status) atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+    }
+    return false;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -175,13 +179,14 @@ __device__ __forceinline__ void ld16x2(uint32_t ta, uint32_t* r, uint32_t tb, ui
 __device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
 __device__ __forceinline__ __half2 u2h(uint32_t u) { return *reinterpret_cast<__half2*>(&u); }
 
-// Split a pair (x0, x1) into packed hi and lo halves; |x| >= 65504 raises `bad`.
-__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo, bool& bad) {
+// Split a pair (x0, x1) into packed hi and lo halves; amax tracks the largest magnitude
+// (checked against the half-precision range once per launch).
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo, float& amax) {
     const __half2 h = __floats2half2_rn(x0, x1);
     const float2 f = __half22float2(h);
     hi = h2u(h);
     lo = h2u(__floats2half2_rn(x0 - f.x, x1 - f.y));
-    bad |= !(fabsf(x0) < HALF_MAX) || !(fabsf(x1) < HALF_MAX);
+    amax = fmaxf(amax, fmaxf(fabsf(x0), fabsf(x1)));
 }
 
 // Value of a packed hi/lo pair.
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
             ep_ret = p.ep_ret[g]; ret_sum = p.ret_sum[g];
         }
         const float sigma = sigma_in >= 0.0f ? sigma_in : p.rewardC[7];
-        bool bad = false;
+        float amax = 0.0f;
         // action ring: slot (t0 - i) mod 16 holds a_{t0-i} (global history is newest first);
         // slot k = ring columns 2k, 2k + 1 (packed halves), after the 16 observation columns
 #pragma unroll 1
@@ -392,7 +397,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     x[e] = 0.0f;
                     if (active && i <= nh) x[e] = p.hist[(4 * (i - 1) + cc) * ld + g];
                 }
-                split2(x[0], x[1], vh[c], vl[c], bad);
+                split2(x[0], x[1], vh[c], vl[c], amax);
             }
             st16(tl + T_AHI + 16 + 16 * q, vh);
             st16(tl + T_ALO + 16 + 16 * q, vl);
@@ -426,7 +431,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     for (int k = 18; k < 32; ++k) o[k] = 0.0f;
                     uint32_t vh[16], vl[16];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) split2(o[2 * c], o[2 * c + 1], vh[c], vl[c], bad);
+                    for (int c = 0; c < 16; ++c) split2(o[2 * c], o[2 * c + 1], vh[c], vl[c], amax);
                     st16(tl + T_AHI, vh);
                     st16(tl + T_ALO, vl);
                     wait_st();
@@ -457,7 +462,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                             const int u = c0 + 8 * q + 2 * e;
                             const float x0 = fmaxf(__uint_as_float(v[8 * q + 2 * e]) + sB1[u], 0.0f);
                             const float x1 = fmaxf(__uint_as_float(v[8 * q + 2 * e + 1]) + sB1[u + 1], 0.0f);
-                            split2(x0, x1, hv[e], lv[e], bad);
+                            split2(x0, x1, hv[e], lv[e], amax);
                         }
                         const int off = cano16(r, c0 + 8 * q, KC2);
                         *reinterpret_cast<uint4*>(A2hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
@@ -472,7 +477,8 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 fence_after();
                 ph ^= 1u;
                 // ---------------- epilogue 2 + output layer (64 -> 4), tanh
-                float pp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                // outputs (0, 1) and (2, 3) as paired FMAs (same IEEE FMAs, same order)
+                unsigned long long p01 = 0ull, p23 = 0ull;
 #pragma unroll 1
                 for (int c0 = 0; c0 < H; c0 += 32) {
                     uint32_t v[32];
@@ -481,12 +487,14 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     for (int e = 0; e < 32; ++e) {
                         const float hcur = fmaxf(__uint_as_float(v[e]) + sB2[c0 + e], 0.0f);
                         const float4 w3 = sW3[c0 + e];
-                        pp[0] = fmaf(w3.x, hcur, pp[0]);
-                        pp[1] = fmaf(w3.y, hcur, pp[1]);
-                        pp[2] = fmaf(w3.z, hcur, pp[2]);
-                        pp[3] = fmaf(w3.w, hcur, pp[3]);
+                        const unsigned long long hh = f2pack(hcur, hcur);
+                        p01 = f2fma(f2pack(w3.x, w3.y), hh, p01);
+                        p23 = f2fma(f2pack(w3.z, w3.w), hh, p23);
                     }
                 }
+                float pp[4];
+                f2unpack(p01, pp[0], pp[1]);
+                f2unpack(p23, pp[2], pp[3]);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const float mu = tanhf(pp[j] + sB3[j]);
@@ -538,8 +546,8 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
             const int hs = (int)(t & 15u);
             if (!__any_sync(0xffffffffu, reset)) {
                 uint32_t h0, h1, l0, l1;
-                split2(a[0], a[1], h0, l0, bad);
-                split2(a[2], a[3], h1, l1, bad);
+                split2(a[0], a[1], h0, l0, amax);
+                split2(a[2], a[3], h1, l1, amax);
                 st2(tl + T_AHI + 16 + 2 * hs, h0, h1);
                 st2(tl + T_ALO + 16 + 2 * hs, l0, l1);
             } else {
@@ -553,7 +561,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                         float2 x = join2(vh[c], vl[c]);
                         if (sl == hs) x = (c & 1) ? make_float2(a[2], a[3]) : make_float2(a[0], a[1]);
                         if (reset) x = make_float2(0.0f, 0.0f);
-                        split2(x.x, x.y, vh[c], vl[c], bad);
+                        split2(x.x, x.y, vh[c], vl[c], amax);
                     }
                     st16(tl + T_AHI + 16 + 16 * q, vh);
                     st16(tl + T_ALO + 16 + 16 * q, vl);
@@ -577,6 +585,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
             }
         }
         wait_st();
+        const bool bad = !(amax < HALF_MAX);  // also catches a NaN that reached an operand
         if (__any_sync(0xffffffffu, bad) && lane == 0 && active && p.status) atomicCAS(p.status, DEV_OK, DEV_RANGE);
 
         // ---- write back (state, parameters, counters, history newest first)
