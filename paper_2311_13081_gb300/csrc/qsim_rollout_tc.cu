@@ -17,15 +17,16 @@
 //     (A1 ready, D1 full, A2 ready, D2 full); the compute warps draw the step's exploration
 //     noise while layer 1 runs.  The tiles run independently.
 //   * layer-1 operand A (128 x 96 halves) lives in TMEM as packed halves (element 2c in the
-//     low 16 bits of column c), hi and lo: elements 0..17 the observation, 18..31 zero,
-//     32..95 a 16-slot ring of past actions (a_tau in slot tau mod 16).  Nothing moves when
+//     low 16 bits of column c), hi and lo: elements 0..17 the observation, 18 the constant 1
+//     (its W1 column holds b1, so layer 1's bias comes out of the MMA), 19..31 zero, 32..95
+//     a 16-slot ring of past actions (a_tau in slot tau mod 16).  Nothing moves when
 //     the window slides: each K=16 MMA step covers ring slots 4s..4s+3, which hold lags
 //     (i, i-1, i-2, i-3) (cyclically in 1..16), and points its B descriptor at the matching
 //     four lag blocks of a lag-reversed copy of W1 ([lag16 .. lag1, lag16, lag15, lag14]).
 //     A B descriptor must start on an 8-element core-matrix boundary while lag blocks are 4
 //     elements wide, so W1 is staged twice, shifted by 4 elements: even and odd start
 //     blocks each find an aligned copy.
-//   * layer-1 output: tcgen05.ld -> bias, ReLU, split -> layer-2 operand in shared memory
+//   * layer-1 output: tcgen05.ld -> ReLU, split -> layer-2 operand in shared memory
 //     (canonical K-major layout) -> layer-2 MMAs -> tcgen05.ld -> bias, ReLU and the
 //     64 -> 4 output layer in registers (SIMT), tanh.
 //   * the half-precision range (|x| < 65504) holds for the observation of any state that
@@ -67,7 +68,7 @@ constexpr int OFF_W2 = OFF_W1 + 4 * SZ_W1;  // [hi, lo]
 constexpr int OFF_A2 = OFF_W2 + 2 * SZ_W2;  // tile k: hi at + 2k SZ_A2, lo at + (2k+1) SZ_A2
 constexpr int OFF_B1 = OFF_A2 + TILES * 2 * SZ_A2;
 constexpr int OFF_B2 = OFF_B1 + 4 * H;
-constexpr int OFF_W3 = OFF_B2 + 4 * H;  // [H] float4: W3[0..3][j]
+constexpr int OFF_W3 = OFF_B2 + 4 * H;  // [H/2][4] float2: (W3[o][2i], W3[o][2i+1])
 constexpr int OFF_B3 = OFF_W3 + 16 * H;
 constexpr int OFF_BAR = OFF_B3 + 16;  // per tile: A1 ready, D1 full, A2 ready, D2 full
 constexpr int OFF_TSLOT = OFF_BAR + 32 * TILES;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
     __half* W2s = reinterpret_cast<__half*>(smb + OFF_W2);
     float* sB1 = reinterpret_cast<float*>(smb + OFF_B1);
     float* sB2 = reinterpret_cast<float*>(smb + OFF_B2);
-    const float4* sW3 = reinterpret_cast<const float4*>(smb + OFF_W3);
+    const float4* sW3 = reinterpret_cast<const float4*>(smb + OFF_W3);  // [H/2][2]: outputs (0,1), (2,3)
     float* sB3 = reinterpret_cast<float*>(smb + OFF_B3);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smb + OFF_TSLOT);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smb + OFF_ABORT);
@@ -231,6 +232,8 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
             float w = 0.0f;
             if (kk < 18) {
                 w = gW1[n * DA + kk];
+            } else if (kk == 18) {
+                w = gb1[n];  // multiplies the constant-1 element of the observation block
             } else if (kk >= 32) {
                 const int kb = kk - (copy ? 36 : 32);  // position inside the lag blocks
                 if (kb >= 0 && kb < 4 * 19) {
@@ -254,7 +257,10 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
         for (int i = tid; i < H; i += NT) {
             sB1[i] = gb1[i];
             sB2[i] = gb2[i];
-            reinterpret_cast<float4*>(smb + OFF_W3)[i] = make_float4(gW3[i], gW3[H + i], gW3[2 * H + i], gW3[3 * H + i]);
+            if (i < H / 2)
+#pragma unroll
+                for (int o = 0; o < 4; ++o)
+                    reinterpret_cast<float2*>(smb + OFF_W3)[4 * i + o] = make_float2(gW3[o * H + 2 * i], gW3[o * H + 2 * i + 1]);
         }
         if (tid < 4) sB3[tid] = gb3[tid];
         if (tid == 0) {
@@ -427,8 +433,9 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
 #pragma unroll
                         for (int k = 0; k < 18; ++k) o[k] += nz[k];
                     }
+                    o[18] = 1.0f;  // bias input of layer 1
 #pragma unroll
-                    for (int k = 18; k < 32; ++k) o[k] = 0.0f;
+                    for (int k = 19; k < 32; ++k) o[k] = 0.0f;
                     uint32_t vh[16], vl[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c) split2(o[2 * c], o[2 * c + 1], vh[c], vl[c], amax);
@@ -459,9 +466,8 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                         uint32_t hv[4], lv[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            const int u = c0 + 8 * q + 2 * e;
-                            const float x0 = fmaxf(__uint_as_float(v[8 * q + 2 * e]) + sB1[u], 0.0f);
-                            const float x1 = fmaxf(__uint_as_float(v[8 * q + 2 * e + 1]) + sB1[u + 1], 0.0f);
+                            const float x0 = fmaxf(__uint_as_float(v[8 * q + 2 * e]), 0.0f);
+                            const float x1 = fmaxf(__uint_as_float(v[8 * q + 2 * e + 1]), 0.0f);
                             split2(x0, x1, hv[e], lv[e], amax);
                         }
                         const int off = cano16(r, c0 + 8 * q, KC2);
@@ -477,24 +483,33 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 fence_after();
                 ph ^= 1u;
                 // ---------------- epilogue 2 + output layer (64 -> 4), tanh
-                // outputs (0, 1) and (2, 3) as paired FMAs (same IEEE FMAs, same order)
-                unsigned long long p01 = 0ull, p23 = 0ull;
+                // hidden units in pairs (2i, 2i+1): bias and FMAs as f32x2; acc[o] holds the
+                // even- and odd-unit partial sums of output o, added at the end
+                unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+                const unsigned long long* b2p = reinterpret_cast<const unsigned long long*>(sB2);
+                const unsigned long long* w3p = reinterpret_cast<const unsigned long long*>(sW3);
 #pragma unroll 1
                 for (int c0 = 0; c0 < H; c0 += 32) {
                     uint32_t v[32];
                     ld16x2(tl + T_D + c0, v, tl + T_D + c0 + 16, v + 16);
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const float hcur = fmaxf(__uint_as_float(v[e]) + sB2[c0 + e], 0.0f);
-                        const float4 w3 = sW3[c0 + e];
-                        const unsigned long long hh = f2pack(hcur, hcur);
-                        p01 = f2fma(f2pack(w3.x, w3.y), hh, p01);
-                        p23 = f2fma(f2pack(w3.z, w3.w), hh, p23);
+                    for (int e = 0; e < 32; e += 2) {
+                        const int i = (c0 + e) >> 1;
+                        const unsigned long long z2 = f2add(f2pack(__uint_as_float(v[e]), __uint_as_float(v[e + 1])), b2p[i]);
+                        float h0, h1;
+                        f2unpack(z2, h0, h1);
+                        const unsigned long long hh = f2pack(fmaxf(h0, 0.0f), fmaxf(h1, 0.0f));
+#pragma unroll
+                        for (int o = 0; o < 4; ++o) acc[o] = f2fma(w3p[4 * i + o], hh, acc[o]);
                     }
                 }
                 float pp[4];
-                f2unpack(p01, pp[0], pp[1]);
-                f2unpack(p23, pp[2], pp[3]);
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    float ev, od;
+                    f2unpack(acc[o], ev, od);
+                    pp[o] = ev + od;
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const float mu = tanhf(pp[j] + sB3[j]);
@@ -551,6 +566,11 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 st2(tl + T_AHI + 16 + 2 * hs, h0, h1);
                 st2(tl + T_ALO + 16 + 2 * hs, l0, l1);
             } else {
+                // some lane of the warp starts a new episode: rewrite the ring words (kept as
+                // they are, slot hs <- a_t, all zero for the lanes that reset)
+                uint32_t h0, h1, l0, l1;
+                split2(a[0], a[1], h0, l0, amax);
+                split2(a[2], a[3], h1, l1, amax);
 #pragma unroll 1
                 for (int q = 0; q < 2; ++q) {
                     uint32_t vh[16], vl[16];
@@ -558,10 +578,8 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
                         const int sl = (32 * q + 2 * c) >> 2;  // both halves of column c share a slot
-                        float2 x = join2(vh[c], vl[c]);
-                        if (sl == hs) x = (c & 1) ? make_float2(a[2], a[3]) : make_float2(a[0], a[1]);
-                        if (reset) x = make_float2(0.0f, 0.0f);
-                        split2(x.x, x.y, vh[c], vl[c], amax);
+                        if (sl == hs) { vh[c] = (c & 1) ? h1 : h0; vl[c] = (c & 1) ? l1 : l0; }
+                        if (reset) { vh[c] = 0u; vl[c] = 0u; }
                     }
                     st16(tl + T_AHI + 16 + 16 * q, vh);
                     st16(tl + T_ALO + 16 + 16 * q, vl);
