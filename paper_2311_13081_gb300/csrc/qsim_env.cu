@@ -503,6 +503,7 @@ extern "C" qsim_status qsim_create(const qsim_config* cfg, const qsim_params* ve
     h->rollout_chunk = 0;
     h->rollout_packed = -1;
     h->streams_ready = false;
+    h->tc_sched = nullptr;
     cudaGetDevice(&h->device);
     const size_t ld = (size_t)h->ld;
     auto alloc = [&](void** p, size_t bytes) -> bool {
@@ -542,7 +543,7 @@ extern "C" qsim_status qsim_destroy(qsim_handle* h) {
     if (!h) return QSIM_OK;
     void* ptrs[] = {h->p.state, h->p.prm, h->p.dist, h->p.hist, h->p.ep_ret, h->p.ret_sum,
                     h->p.ep_index, h->p.ep_step, h->p.n_done, h->p.len_sum, h->p.rec,
-                    h->p.side, h->p.rewardC, h->p.status};
+                    h->p.side, h->p.rewardC, h->p.status, h->tc_sched};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->streams_ready) {

@@ -57,6 +57,7 @@ struct qsim_handle {
     cudaStream_t part_stream[4];
     cudaEvent_t ev_fork, ev_join[4];
     bool streams_ready;
+    int* tc_sched;  // persistent tensor-core rollout: [next unit, done chunks per group]
 };
 
 struct ac_handle {

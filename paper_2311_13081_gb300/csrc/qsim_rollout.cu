@@ -474,6 +474,8 @@ static size_t roll_smem(int hidden, int nw) {
 }
 
 static const int kWarpChoices[] = {2, 4, 6, 8, 10};
+// steps per work unit of the persistent tensor-core schedule (parts = 1)
+static const int kTcChunk = 50;
 
 // Largest-smem-fitting default: the variant with most resident warps per SM whose grid
 // needs the fewest waves.
@@ -534,7 +536,7 @@ static qsim_status ensure_streams(qsim_handle* h) {
 }
 
 qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, uint32_t t0, int64_t head,
-                                    float sigma, int w0, int w1, cudaStream_t st);
+                                    float sigma, int w0, int w1, cudaStream_t st, int chunk, int* sched);
 int rollout_tc_warps_per_cta();
 
 // Launches T steps of the rollout as `parts` env partitions x chunks of `chunk` steps.
@@ -561,8 +563,15 @@ qsim_status launch_rollout(qsim_handle* h, const float* actor, int hidden, int T
     if (chunk <= 0 || chunk > T) chunk = T;
     const uint32_t t0 = (uint32_t)h->t_now;
     if (tc) {
-        if (parts == 1 && chunk == T)
-            return launch_rollout_tc_range(h, actor, T, t0, h->head, sigma, 0, warps, st);
+        if (parts == 1) {
+            // one persistent launch walking (group of 384 envs, chunk of steps) units
+            if (!h->tc_sched) {
+                const int groups = (warps + rollout_tc_warps_per_cta() - 1) / rollout_tc_warps_per_cta();
+                QCHECK_CUDA(cudaMalloc((void**)&h->tc_sched, sizeof(int) * (size_t)(1 + groups)));
+            }
+            return launch_rollout_tc_range(h, actor, T, t0, h->head, sigma, 0, warps, st,
+                                           chunk < T ? chunk : kTcChunk, h->tc_sched);
+        }
         qsim_status s = ensure_streams(h);
         if (s != QSIM_OK) return s;
         QCHECK_CUDA(cudaEventRecord(h->ev_fork, st));
@@ -573,7 +582,7 @@ qsim_status launch_rollout(qsim_handle* h, const float* actor, int hidden, int T
                 const int w0 = (int)((int64_t)warps * p / parts), w1 = (int)((int64_t)warps * (p + 1) / parts);
                 if (w1 <= w0) continue;
                 s = launch_rollout_tc_range(h, actor, tcn, t0 + (uint32_t)t, h->head + t, sigma, w0, w1,
-                                            h->part_stream[p]);
+                                            h->part_stream[p], 0, nullptr);
                 if (s != QSIM_OK) return s;
             }
         }
@@ -638,11 +647,14 @@ extern "C" qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t 
     if (engine == 2 && hidden != 64) engine = 1;
     int parts = h->rollout_parts, chunk = h->rollout_chunk;
     if (parts <= 0) {
-        // more than one wave of warps: pipeline two partitions in 100-step chunks
-        const int resident = engine == 2 ? rollout_tc_warps_per_cta() * tc_resident_ctas(h->device)
-                                         : resident_warps(hidden, nw, h->device, engine == 1);
-        parts = (h->ld / 32 > resident) ? 2 : 1;
-        chunk = parts > 1 ? 100 : 0;
+        if (engine == 2) {
+            parts = 1;  // the persistent work-unit schedule
+            chunk = 0;
+        } else {
+            // more than one wave of warps: pipeline two partitions in 100-step chunks
+            parts = (h->ld / 32 > resident_warps(hidden, nw, h->device, engine == 1)) ? 2 : 1;
+            chunk = parts > 1 ? 100 : 0;
+        }
     }
     qsim_status s = launch_rollout(h, actor, hidden, n_steps, sigma_e, (cudaStream_t)stream, nw,
                                    parts, chunk, engine);
@@ -667,10 +679,12 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
     QCHECK_CUDA(cudaEventCreate(&e0));
     QCHECK_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_nw = 0, best_parts = 1, best_pk = 0;
+    int best_nw = 0, best_parts = 1, best_pk = 0, best_chunk = 0;
     struct Sched { int parts, chunk; };
     const int tc = std::max(1, std::min(100, n_steps / 4));
-    const Sched scheds[] = {{1, 0}, {2, tc}, {3, tc}, {4, tc}};
+    // parts = 1 with chunk c: one launch (SIMT) or the persistent unit schedule with c-step
+    // units (tensor cores; c = 0: the default unit)
+    const Sched scheds[] = {{1, 0}, {1, std::max(1, n_steps / 4)}, {2, tc}, {3, tc}, {4, tc}};
     for (int pk = 0; pk < 3; ++pk)
     for (int nw : kWarpChoices) {
         if (pk == 2 && (hidden != 64 || nw != kWarpChoices[0])) continue;  // one tensor-core shape
@@ -678,6 +692,7 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
         if (h->rollout_packed >= 0 && pk != h->rollout_packed) continue;
         for (const Sched& sc : scheds) {
             if (((h->t_now + n_steps) >> 32) != 0) break;
+            if (pk < 2 && sc.parts == 1 && sc.chunk > 0) continue;  // chunked single stream: SIMT gains nothing
             const int resident = pk == 2 ? rollout_tc_warps_per_cta() * tc_resident_ctas(h->device)
                                          : resident_warps(hidden, nw, h->device, pk == 1);
             if (sc.parts > 1 && h->ld / 32 <= resident) continue;
@@ -694,7 +709,7 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
             cudaEventSynchronize(e1);
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_nw = nw; best_parts = sc.parts; best_pk = pk; }
+            if (ms < best) { best = ms; best_nw = nw; best_parts = sc.parts; best_pk = pk; best_chunk = sc.chunk; }
         }
     }
     cudaEventDestroy(e0);
@@ -703,7 +718,7 @@ extern "C" int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int
     if (best_nw) {
         h->rollout_warps = best_nw;
         h->rollout_parts = best_parts;
-        h->rollout_chunk = best_parts > 1 ? 100 : 0;
+        h->rollout_chunk = best_parts > 1 ? 100 : (best_pk == 2 ? best_chunk : 0);
         h->rollout_packed = best_pk;
     }
     return best_nw;

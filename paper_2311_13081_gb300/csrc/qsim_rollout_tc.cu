@@ -73,7 +73,8 @@ constexpr int OFF_B3 = OFF_W3 + 16 * H;
 constexpr int OFF_BAR = OFF_B3 + 16;  // per tile: A1 ready, D1 full, A2 ready, D2 full
 constexpr int OFF_TSLOT = OFF_BAR + 32 * TILES;
 constexpr int OFF_ABORT = OFF_TSLOT + 16;
-constexpr int SMEM = OFF_ABORT + 16;
+constexpr int OFF_UNIT = OFF_ABORT + 16;
+constexpr int SMEM = OFF_UNIT + 16;
 static_assert(SMEM <= 227 * 1024, "tensor-core rollout: shared memory");
 static_assert(SZ_W1 % 128 == 0 && OFF_A2 % 128 == 0 && SZ_A2 % 128 == 0, "alignment");
 
@@ -200,9 +201,16 @@ __device__ __forceinline__ float2 join2(uint32_t hi, uint32_t lo) {
 
 using namespace tcr;
 
+// Work units: (group g of NCW env warps, chunk k of `chunk` steps).  With `sched` (device
+// counters [next unit, done chunks of group 0 .. n_groups-1], zeroed by the host) the grid is
+// persistent: each CTA takes units in chunk-major order from the counter and starts chunk k
+// of a group once chunk k-1 of that group has been published (a bounded wait); every unit
+// it waits for was taken earlier by a running CTA, so the wait always ends.  Without
+// `sched`, CTA b runs group b for all T steps.
 __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const float* __restrict__ actor,
                                                       int T, uint32_t t0, int64_t head0, int64_t capacity,
-                                                      float sigma_in, int warp0, int warp_end) {
+                                                      float sigma_in, int warp0, int warp_end,
+                                                      int n_groups, int chunk, int* sched) {
     extern __shared__ __align__(1024) unsigned char smb[];
     __half* W1s = reinterpret_cast<__half*>(smb + OFF_W1);
     __half* W2s = reinterpret_cast<__half*>(smb + OFF_W2);
@@ -290,352 +298,394 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
     __half* A2hi = reinterpret_cast<__half*>(smb + OFF_A2 + (2 * tile) * SZ_A2);
     __half* A2lo = reinterpret_cast<__half*>(smb + OFF_A2 + (2 * tile + 1) * SZ_A2);
 
-    if (mma_warp) {
-        // ================= MMA warp of this tile: lane 0 issues, the warp follows the waits
-        const uint32_t sW1 = smem_addr(W1s), sW2 = smem_addr(W2s);
-        const uint32_t sA2hi = smem_addr(A2hi), sA2lo = smem_addr(A2lo);
-        uint32_t ph = 0;
-        int issued = 0;  // 0: nothing in flight, 1: layer 1 committed, 2: layer 2 committed
+    volatile int* unit_slot = reinterpret_cast<volatile int*>(smb + OFF_UNIT);
+    const int n_chunks = (T + chunk - 1) / chunk;
+    const int n_units = n_groups * n_chunks;
+    uint32_t ph = 0;  // hand-over phase, advanced once per actor step (compute and MMA warps alike)
+    int issued = 0;   // MMA warp: 0 nothing in flight, 1 layer 1 committed, 2 layer 2 committed
 #pragma unroll 1
-        for (int tt = 0; tt < T; ++tt) {
-            const uint32_t t = t0 + (uint32_t)tt;
-            if ((int64_t)t < (int64_t)C.learning_starts) continue;
-            if (!warp_wait(bar_a1, ph, abort_flag, p.status)) break;
-            fence_after();
-            if (lane == 0) {
-#pragma unroll 1
-                for (int j = 0; j < KA / 16; ++j) {
-                    // W1 copy and first element of this K-step's 16-element window
-                    uint32_t wbase;
-                    int kk;
-                    if (j < 2) {
-                        wbase = sW1;
-                        kk = 16 * j;
-                    } else {
-                        const int i0 = (int)((t - 1u - (uint32_t)(4 * (j - 2))) & 15u) + 1;  // lag of slot 4(j-2)
-                        const int b0 = 16 - i0;
-                        wbase = sW1 + (uint32_t)((b0 & 1) * 2 * SZ_W1);
-                        kk = (b0 & 1) ? 36 + 4 * b0 : 32 + 4 * b0;
-                    }
-                    const uint64_t bhi = sdesc(wbase + (uint32_t)(kk / 8) * 128u, KC1);
-                    const uint64_t blo = sdesc(wbase + (uint32_t)SZ_W1 + (uint32_t)(kk / 8) * 128u, KC1);
-                    mma_tt(tmem + T_D, tmem + T_AHI + 8 * j, bhi, j > 0);
-                    mma_tt(tmem + T_D, tmem + T_AHI + 8 * j, blo, 1);
-                    mma_tt(tmem + T_D, tmem + T_ALO + 8 * j, bhi, 1);
+    for (int it = 0;; ++it) {
+        if (tid == 0) {
+            int u = sched ? atomicAdd(sched, 1) : (it == 0 ? (int)blockIdx.x : n_units);
+            if (sched && u < n_units && u >= n_groups) {
+                // chunk k of group g needs chunk k-1 of the same group published
+                const int* done = sched + 1 + u % n_groups;
+                const int need = u / n_groups;
+                bool ok = false;
+                for (int i = 0; i < WAIT_LIMIT; ++i) {
+                    int v;
+                    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(done) : "memory");
+                    if (v >= need) { ok = true; break; }
+                    if (*abort_flag) break;
+                    __nanosleep(256);
                 }
-                mma_commit(bar_d1);
+                if (!ok) {
+                    *abort_flag = 1;
+                    if (p.status) atomicCAS(p.status, DEV_OK, DEV_TIMEOUT);
+                }
             }
-            __syncwarp();
-            issued = 1;
-            if (!warp_wait(bar_a2, ph, abort_flag, p.status)) break;
-            fence_after();
-            if (lane == 0) {
+            *unit_slot = u;
+        }
+        __syncthreads();
+        const int u = *unit_slot;
+        if (u >= n_units || *abort_flag) break;
+        const int ug = u % n_groups, uk = u / n_groups;
+        const int Tu = min(chunk, T - uk * chunk);
+        const uint32_t t0u = t0 + (uint32_t)(uk * chunk);
+        const int64_t headu = head0 + (int64_t)uk * chunk;
+        if (mma_warp) {
+            // ================= MMA warp of this tile: lane 0 issues, the warp follows the waits
+            const uint32_t sW1 = smem_addr(W1s), sW2 = smem_addr(W2s);
+            const uint32_t sA2hi = smem_addr(A2hi), sA2lo = smem_addr(A2lo);
 #pragma unroll 1
-                for (int j = 0; j < H / 16; ++j) {
-                    const uint32_t ko = (uint32_t)(2 * j) * 128u;
-                    const uint64_t ahi = sdesc(sA2hi + ko, KC2), alo = sdesc(sA2lo + ko, KC2);
-                    const uint64_t bhi = sdesc(sW2 + ko, KC2), blo = sdesc(sW2 + (uint32_t)SZ_W2 + ko, KC2);
-                    mma_ss(tmem + T_D, ahi, bhi, j > 0);
-                    mma_ss(tmem + T_D, ahi, blo, 1);
-                    mma_ss(tmem + T_D, alo, bhi, 1);
-                }
-                mma_commit(bar_d2);
-            }
-            __syncwarp();
-            issued = 2;
-            ph ^= 1u;
-        }
-        // on an abort, let the last committed batch finish before the memory is released
-        if (*abort_flag && lane == 0 && issued) {
-            const uint32_t b = issued == 1 ? bar_d1 : bar_d2;
-            const uint32_t par = issued == 1 ? ph : ph ^ 1u;
-            for (int i = 0; i < WAIT_LIMIT; ++i) {
-                uint32_t done;
-                asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                             "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(b), "r"(par) : "memory");
-                if (done) break;
-            }
-        }
-    } else {
-        // ================= compute warps: thread r of the tile owns env r and TMEM lane r
-        const int r = tid & (TILE - 1);
-        const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
-        const int gw = warp0 + blockIdx.x * NCW + warp;                  // global warp (32 envs)
-        const bool active = gw < warp_end;                               // warp-uniform
-        const int g = active ? gw * 32 + lane : lane;  // inactive warps: an in-range index, never stored to
-
-        float s[NS], d[6];
-        Prm P = make_prm(1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f);
-        uint32_t ep_index = 0, ep_step = 0, n_done = 0, len_sum = 0;
-        float ep_ret = 0.0f, ret_sum = 0.0f;
-#pragma unroll
-        for (int i = 0; i < NS; ++i) s[i] = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 6; ++i) d[i] = 0.0f;
-        s[3] = 1.0f;
-        if (active) {
-#pragma unroll
-            for (int i = 0; i < NS; ++i) s[i] = p.state[i * ld + g];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) d[i] = p.dist[i * ld + g];
-            P = make_prm(p.prm[g], p.prm[ld + g], p.prm[2 * ld + g], p.prm[3 * ld + g], p.prm[4 * ld + g],
-                         p.prm[5 * ld + g], p.prm[6 * ld + g]);
-            ep_index = p.ep_index[g]; ep_step = p.ep_step[g];
-            n_done = p.n_done[g]; len_sum = p.len_sum[g];
-            ep_ret = p.ep_ret[g]; ret_sum = p.ret_sum[g];
-        }
-        const float sigma = sigma_in >= 0.0f ? sigma_in : p.rewardC[7];
-        float amax = 0.0f;
-        // action ring: slot (t0 - i) mod 16 holds a_{t0-i} (global history is newest first);
-        // slot k = ring columns 2k, 2k + 1 (packed halves), after the 16 observation columns
-#pragma unroll 1
-        for (int q = 0; q < 2; ++q) {
-            uint32_t vh[16], vl[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                float x[2];
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int el = 32 * q + 2 * c + e;  // element inside the ring
-                    const int sl = el >> 2, cc = el & 3;
-                    const int i0 = (int)((t0 - (uint32_t)sl) & 15u);
-                    const int i = i0 == 0 ? 16 : i0;
-                    x[e] = 0.0f;
-                    if (active && i <= nh) x[e] = p.hist[(4 * (i - 1) + cc) * ld + g];
-                }
-                split2(x[0], x[1], vh[c], vl[c], amax);
-            }
-            st16(tl + T_AHI + 16 + 16 * q, vh);
-            st16(tl + T_ALO + 16 + 16 * q, vl);
-        }
-        int64_t slot = capacity > 0 ? head0 % capacity : 0;
-        const int F = C.F;
-        uint32_t ph = 0;
-
-#pragma unroll 1
-        for (int tt = 0; tt < T; ++tt) {
-            const uint32_t t = t0 + (uint32_t)tt;
-            float a[4];
-            if ((int64_t)t < (int64_t)C.learning_starts) {
-                const uint4 rr = draw(C, (uint32_t)g, t, TAG_WARM, 0);
-                a[0] = 2.0f * u01(rr.x) - 1.0f;
-                a[1] = 2.0f * u01(rr.y) - 1.0f;
-                a[2] = 2.0f * u01(rr.z) - 1.0f;
-                a[3] = 2.0f * u01(rr.w) - 1.0f;
-            } else {
-                // ---------------- observation -> A elements 0..31 (hi / lo); hand over
-                {
-                    float o[32];
-                    obs_state(s, o);
-                    if (C.any_noise) {
-                        float nz[18];
-                        obs_noise(C, (uint32_t)g, t, nz);
-#pragma unroll
-                        for (int k = 0; k < 18; ++k) o[k] += nz[k];
-                    }
-                    o[18] = 1.0f;  // bias input of layer 1
-#pragma unroll
-                    for (int k = 19; k < 32; ++k) o[k] = 0.0f;
-                    uint32_t vh[16], vl[16];
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) split2(o[2 * c], o[2 * c + 1], vh[c], vl[c], amax);
-                    st16(tl + T_AHI, vh);
-                    st16(tl + T_ALO, vl);
-                    wait_st();
-                }
-                fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(bar_a1);
-                // ---------------- while layer 1 runs: exploration noise
-                float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                if (sigma > 0.0f) {
-                    const uint4 r0 = draw(C, (uint32_t)g, t, TAG_EXPL, 0);
-                    const uint4 r1 = draw(C, (uint32_t)g, t, TAG_EXPL, 1);
-                    z[0] = gauss(r0.x, r0.y); z[1] = gauss(r0.z, r0.w);
-                    z[2] = gauss(r1.x, r1.y); z[3] = gauss(r1.z, r1.w);
-                }
-                if (!warp_wait(bar_d1, ph, abort_flag, p.status)) break;
+            for (int tt = 0; tt < Tu; ++tt) {
+                const uint32_t t = t0u + (uint32_t)tt;
+                if ((int64_t)t < (int64_t)C.learning_starts) continue;
+                if (!warp_wait(bar_a1, ph, abort_flag, p.status)) break;
                 fence_after();
-                // ---------------- epilogue 1: bias, ReLU, split -> A2 (shared memory); hand over
+                if (lane == 0) {
 #pragma unroll 1
-                for (int c0 = 0; c0 < H; c0 += 32) {
-                    uint32_t v[32];
-                    ld16x2(tl + T_D + c0, v, tl + T_D + c0 + 16, v + 16);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {  // 8 hidden units = one 16-byte core-matrix row
-                        uint32_t hv[4], lv[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float x0 = fmaxf(__uint_as_float(v[8 * q + 2 * e]), 0.0f);
-                            const float x1 = fmaxf(__uint_as_float(v[8 * q + 2 * e + 1]), 0.0f);
-                            split2(x0, x1, hv[e], lv[e], amax);
+                    for (int j = 0; j < KA / 16; ++j) {
+                        // W1 copy and first element of this K-step's 16-element window
+                        uint32_t wbase;
+                        int kk;
+                        if (j < 2) {
+                            wbase = sW1;
+                            kk = 16 * j;
+                        } else {
+                            const int i0 = (int)((t - 1u - (uint32_t)(4 * (j - 2))) & 15u) + 1;  // lag of slot 4(j-2)
+                            const int b0 = 16 - i0;
+                            wbase = sW1 + (uint32_t)((b0 & 1) * 2 * SZ_W1);
+                            kk = (b0 & 1) ? 36 + 4 * b0 : 32 + 4 * b0;
                         }
-                        const int off = cano16(r, c0 + 8 * q, KC2);
-                        *reinterpret_cast<uint4*>(A2hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                        *reinterpret_cast<uint4*>(A2lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                        const uint64_t bhi = sdesc(wbase + (uint32_t)(kk / 8) * 128u, KC1);
+                        const uint64_t blo = sdesc(wbase + (uint32_t)SZ_W1 + (uint32_t)(kk / 8) * 128u, KC1);
+                        mma_tt(tmem + T_D, tmem + T_AHI + 8 * j, bhi, j > 0);
+                        mma_tt(tmem + T_D, tmem + T_AHI + 8 * j, blo, 1);
+                        mma_tt(tmem + T_D, tmem + T_ALO + 8 * j, bhi, 1);
                     }
+                    mma_commit(bar_d1);
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(bar_a2);
-                if (!warp_wait(bar_d2, ph, abort_flag, p.status)) break;
+                issued = 1;
+                if (!warp_wait(bar_a2, ph, abort_flag, p.status)) break;
                 fence_after();
+                if (lane == 0) {
+#pragma unroll 1
+                    for (int j = 0; j < H / 16; ++j) {
+                        const uint32_t ko = (uint32_t)(2 * j) * 128u;
+                        const uint64_t ahi = sdesc(sA2hi + ko, KC2), alo = sdesc(sA2lo + ko, KC2);
+                        const uint64_t bhi = sdesc(sW2 + ko, KC2), blo = sdesc(sW2 + (uint32_t)SZ_W2 + ko, KC2);
+                        mma_ss(tmem + T_D, ahi, bhi, j > 0);
+                        mma_ss(tmem + T_D, ahi, blo, 1);
+                        mma_ss(tmem + T_D, alo, bhi, 1);
+                    }
+                    mma_commit(bar_d2);
+                }
+                __syncwarp();
+                issued = 2;
                 ph ^= 1u;
-                // ---------------- epilogue 2 + output layer (64 -> 4), tanh
-                // hidden units in pairs (2i, 2i+1): bias and FMAs as f32x2; acc[o] holds the
-                // even- and odd-unit partial sums of output o, added at the end
-                unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
-                const unsigned long long* b2p = reinterpret_cast<const unsigned long long*>(sB2);
-                const unsigned long long* w3p = reinterpret_cast<const unsigned long long*>(sW3);
-#pragma unroll 1
-                for (int c0 = 0; c0 < H; c0 += 32) {
-                    uint32_t v[32];
-                    ld16x2(tl + T_D + c0, v, tl + T_D + c0 + 16, v + 16);
-#pragma unroll
-                    for (int e = 0; e < 32; e += 2) {
-                        const int i = (c0 + e) >> 1;
-                        const unsigned long long z2 = f2add(f2pack(__uint_as_float(v[e]), __uint_as_float(v[e + 1])), b2p[i]);
-                        float h0, h1;
-                        f2unpack(z2, h0, h1);
-                        const unsigned long long hh = f2pack(fmaxf(h0, 0.0f), fmaxf(h1, 0.0f));
-#pragma unroll
-                        for (int o = 0; o < 4; ++o) acc[o] = f2fma(w3p[4 * i + o], hh, acc[o]);
-                    }
-                }
-                float pp[4];
-#pragma unroll
-                for (int o = 0; o < 4; ++o) {
-                    float ev, od;
-                    f2unpack(acc[o], ev, od);
-                    pp[o] = ev + od;
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float mu = tanhf(pp[j] + sB3[j]);
-                    a[j] = clampf(sigma > 0.0f ? fmaf(sigma, z[j], mu) : mu, -1.0f, 1.0f);
-                }
             }
-            // ---------------- dynamics, reward, termination
-            float u[4], s2[NS];
-            action_to_rpm(C.veh, a, u);
-#pragma unroll
-            for (int i = 0; i < NS; ++i) s2[i] = s[i];
-            rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
-            float rw;
-            {
-                float Cr[7];
-#pragma unroll
-                for (int i = 0; i < 7; ++i) Cr[i] = p.rewardC[i];
-                rw = reward(Cr, s2, a);
-            }
-            const bool term = terminated(C, s2);
-            const uint32_t ep_after = ep_step + 1;
-            const bool trunc = !term && (int)ep_after >= C.episode_len;
-            // ---------------- transition record (field-major, streaming stores)
-            if (capacity > 0) {
-                if (active) {
-                    float* rec = p.rec + (size_t)slot * F * ld + g;
-#pragma unroll
-                    for (int i = 0; i < NS; ++i) __stcs(rec + i * ld, s[i]);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) __stcs(rec + (17 + i) * ld, a[i]);
-                    __stcs(rec + 21 * ld, rw);
-                    __stcs(rec + 22 * ld, __uint_as_float(pack_flags(term, trunc, ep_step)));
-                    if (C.n_priv) {
-                        float pv[NPRIV];
-                        priv_vals(C, P, d, pv);
-#pragma unroll
-                        for (int k = 0; k < NPRIV; ++k) __stcs(rec + (23 + k) * ld, pv[k]);
-                    }
-                    if (term || trunc) {
-                        float* sd = p.side + (size_t)slot * NS * ld + g;
-#pragma unroll
-                        for (int i = 0; i < NS; ++i) __stcs(sd + i * ld, s2[i]);
-                    }
-                }
-                slot = (slot + 1 == capacity) ? 0 : slot + 1;
-            }
-            // ---------------- action ring: a_t into slot t mod 16; an episode end clears the ring
-            const bool reset = term || trunc;
-            const int hs = (int)(t & 15u);
-            if (!__any_sync(0xffffffffu, reset)) {
-                uint32_t h0, h1, l0, l1;
-                split2(a[0], a[1], h0, l0, amax);
-                split2(a[2], a[3], h1, l1, amax);
-                st2(tl + T_AHI + 16 + 2 * hs, h0, h1);
-                st2(tl + T_ALO + 16 + 2 * hs, l0, l1);
-            } else {
-                // some lane of the warp starts a new episode: rewrite the ring words (kept as
-                // they are, slot hs <- a_t, all zero for the lanes that reset)
-                uint32_t h0, h1, l0, l1;
-                split2(a[0], a[1], h0, l0, amax);
-                split2(a[2], a[3], h1, l1, amax);
-#pragma unroll 1
-                for (int q = 0; q < 2; ++q) {
-                    uint32_t vh[16], vl[16];
-                    ld16x2(tl + T_AHI + 16 + 16 * q, vh, tl + T_ALO + 16 + 16 * q, vl);
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const int sl = (32 * q + 2 * c) >> 2;  // both halves of column c share a slot
-                        if (sl == hs) { vh[c] = (c & 1) ? h1 : h0; vl[c] = (c & 1) ? l1 : l0; }
-                        if (reset) { vh[c] = 0u; vl[c] = 0u; }
-                    }
-                    st16(tl + T_AHI + 16 + 16 * q, vh);
-                    st16(tl + T_ALO + 16 + 16 * q, vl);
-                }
-            }
-            ep_ret += rw;
-            if (reset) {
-                n_done += 1;
-                len_sum += ep_after;
-                ret_sum += ep_ret;
-                ep_index += 1;
-                float prm7[7];
-                reset_env(C, (uint32_t)g, ep_index, s, prm7, d);
-                P = make_prm(prm7[0], prm7[1], prm7[2], prm7[3], prm7[4], prm7[5], prm7[6]);
-                ep_step = 0;
-                ep_ret = 0.0f;
-            } else {
-#pragma unroll
-                for (int i = 0; i < NS; ++i) s[i] = s2[i];
-                ep_step = ep_after;
-            }
-        }
-        wait_st();
-        const bool bad = !(amax < HALF_MAX);  // also catches a NaN that reached an operand
-        if (__any_sync(0xffffffffu, bad) && lane == 0 && active && p.status) atomicCAS(p.status, DEV_OK, DEV_RANGE);
+        } else {
+            // ================= compute warps: thread r of the tile owns env r and TMEM lane r
+            const int r = tid & (TILE - 1);
+            const uint32_t tl = tmem + ((uint32_t)(32 * (warp & 3)) << 16);  // this warp's lanes
+            const int gw = warp0 + ug * NCW + warp;                          // global warp (32 envs)
+            const bool active = gw < warp_end;                               // warp-uniform
+            const int g = active ? gw * 32 + lane : lane;  // inactive warps: an in-range index, never stored to
 
-        // ---- write back (state, parameters, counters, history newest first)
-        if (active) {
+            float s[NS], d[6];
+            Prm P = make_prm(1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f);
+            uint32_t ep_index = 0, ep_step = 0, n_done = 0, len_sum = 0;
+            float ep_ret = 0.0f, ret_sum = 0.0f;
 #pragma unroll
-            for (int i = 0; i < NS; ++i) p.state[i * ld + g] = s[i];
-            p.prm[g] = P.m; p.prm[ld + g] = P.Jx; p.prm[2 * ld + g] = P.Jy; p.prm[3 * ld + g] = P.Jz;
-            p.prm[4 * ld + g] = P.kf; p.prm[5 * ld + g] = P.km; p.prm[6 * ld + g] = P.tm;
+            for (int i = 0; i < NS; ++i) s[i] = 0.0f;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) p.dist[i * ld + g] = d[i];
-            p.ep_index[g] = ep_index; p.ep_step[g] = ep_step; p.ep_ret[g] = ep_ret;
-            p.n_done[g] = n_done; p.len_sum[g] = len_sum; p.ret_sum[g] = ret_sum;
-        }
-        const uint32_t t_end = t0 + (uint32_t)T;
-#pragma unroll 1
-        for (int q = 0; q < 2; ++q) {
-            uint32_t vh[16], vl[16];
-            ld16x2(tl + T_AHI + 16 + 16 * q, vh, tl + T_ALO + 16 + 16 * q, vl);
+            for (int i = 0; i < 6; ++i) d[i] = 0.0f;
+            s[3] = 1.0f;
             if (active) {
 #pragma unroll
+                for (int i = 0; i < NS; ++i) s[i] = __ldcg(p.state + i * ld + g);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) d[i] = __ldcg(p.dist + i * ld + g);
+                P = make_prm(__ldcg(p.prm + g), __ldcg(p.prm + ld + g), __ldcg(p.prm + 2 * ld + g),
+                             __ldcg(p.prm + 3 * ld + g), __ldcg(p.prm + 4 * ld + g), __ldcg(p.prm + 5 * ld + g),
+                             __ldcg(p.prm + 6 * ld + g));
+                ep_index = __ldcg(p.ep_index + g); ep_step = __ldcg(p.ep_step + g);
+                n_done = __ldcg(p.n_done + g); len_sum = __ldcg(p.len_sum + g);
+                ep_ret = __ldcg(p.ep_ret + g); ret_sum = __ldcg(p.ret_sum + g);
+            }
+            const float sigma = sigma_in >= 0.0f ? sigma_in : p.rewardC[7];
+            float amax = 0.0f;
+            // action ring: slot (t0 - i) mod 16 holds a_{t0-i} (global history is newest first);
+            // slot k = ring columns 2k, 2k + 1 (packed halves), after the 16 observation columns
+#pragma unroll 1
+            for (int q = 0; q < 2; ++q) {
+                uint32_t vh[16], vl[16];
+#pragma unroll
                 for (int c = 0; c < 16; ++c) {
-                    const float2 x = join2(vh[c], vl[c]);
+                    float x[2];
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
-                        const int el = 32 * q + 2 * c + e;
+                        const int el = 32 * q + 2 * c + e;  // element inside the ring
                         const int sl = el >> 2, cc = el & 3;
-                        const int i0 = (int)((t_end - (uint32_t)sl) & 15u);
-                        const int i = i0 == 0 ? 16 : i0;  // lag of slot sl after the last step
-                        if (i <= nh) p.hist[(4 * (i - 1) + cc) * ld + g] = e ? x.y : x.x;
+                        const int i0 = (int)((t0u - (uint32_t)sl) & 15u);
+                        const int i = i0 == 0 ? 16 : i0;
+                        x[e] = 0.0f;
+                        if (active && i <= nh) x[e] = __ldcg(p.hist + (4 * (i - 1) + cc) * ld + g);
+                    }
+                    split2(x[0], x[1], vh[c], vl[c], amax);
+                }
+                st16(tl + T_AHI + 16 + 16 * q, vh);
+                st16(tl + T_ALO + 16 + 16 * q, vl);
+            }
+            int64_t slot = capacity > 0 ? headu % capacity : 0;
+            const int F = C.F;
+
+#pragma unroll 1
+            for (int tt = 0; tt < Tu; ++tt) {
+                const uint32_t t = t0u + (uint32_t)tt;
+                float a[4];
+                if ((int64_t)t < (int64_t)C.learning_starts) {
+                    const uint4 rr = draw(C, (uint32_t)g, t, TAG_WARM, 0);
+                    a[0] = 2.0f * u01(rr.x) - 1.0f;
+                    a[1] = 2.0f * u01(rr.y) - 1.0f;
+                    a[2] = 2.0f * u01(rr.z) - 1.0f;
+                    a[3] = 2.0f * u01(rr.w) - 1.0f;
+                } else {
+                    // ---------------- observation -> A elements 0..31 (hi / lo); hand over
+                    {
+                        float o[32];
+                        obs_state(s, o);
+                        if (C.any_noise) {
+                            float nz[18];
+                            obs_noise(C, (uint32_t)g, t, nz);
+#pragma unroll
+                            for (int k = 0; k < 18; ++k) o[k] += nz[k];
+                        }
+                        o[18] = 1.0f;  // bias input of layer 1
+#pragma unroll
+                        for (int k = 19; k < 32; ++k) o[k] = 0.0f;
+                        uint32_t vh[16], vl[16];
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) split2(o[2 * c], o[2 * c + 1], vh[c], vl[c], amax);
+                        st16(tl + T_AHI, vh);
+                        st16(tl + T_ALO, vl);
+                        wait_st();
+                    }
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar_a1);
+                    // ---------------- while layer 1 runs: exploration noise
+                    float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    if (sigma > 0.0f) {
+                        const uint4 r0 = draw(C, (uint32_t)g, t, TAG_EXPL, 0);
+                        const uint4 r1 = draw(C, (uint32_t)g, t, TAG_EXPL, 1);
+                        z[0] = gauss(r0.x, r0.y); z[1] = gauss(r0.z, r0.w);
+                        z[2] = gauss(r1.x, r1.y); z[3] = gauss(r1.z, r1.w);
+                    }
+                    if (!warp_wait(bar_d1, ph, abort_flag, p.status)) break;
+                    fence_after();
+                    // ---------------- epilogue 1: bias, ReLU, split -> A2 (shared memory); hand over
+#pragma unroll 1
+                    for (int c0 = 0; c0 < H; c0 += 32) {
+                        uint32_t v[32];
+                        ld16x2(tl + T_D + c0, v, tl + T_D + c0 + 16, v + 16);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {  // 8 hidden units = one 16-byte core-matrix row
+                            uint32_t hv[4], lv[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float x0 = fmaxf(__uint_as_float(v[8 * q + 2 * e]), 0.0f);
+                                const float x1 = fmaxf(__uint_as_float(v[8 * q + 2 * e + 1]), 0.0f);
+                                split2(x0, x1, hv[e], lv[e], amax);
+                            }
+                            const int off = cano16(r, c0 + 8 * q, KC2);
+                            *reinterpret_cast<uint4*>(A2hi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                            *reinterpret_cast<uint4*>(A2lo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                        }
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(bar_a2);
+                    if (!warp_wait(bar_d2, ph, abort_flag, p.status)) break;
+                    fence_after();
+                    ph ^= 1u;
+                    // ---------------- epilogue 2 + output layer (64 -> 4), tanh
+                    // hidden units in pairs (2i, 2i+1): bias and FMAs as f32x2; acc[o] holds the
+                    // even- and odd-unit partial sums of output o, added at the end
+                    unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+                    const unsigned long long* b2p = reinterpret_cast<const unsigned long long*>(sB2);
+                    const unsigned long long* w3p = reinterpret_cast<const unsigned long long*>(sW3);
+#pragma unroll 1
+                    for (int c0 = 0; c0 < H; c0 += 32) {
+                        uint32_t v[32];
+                        ld16x2(tl + T_D + c0, v, tl + T_D + c0 + 16, v + 16);
+#pragma unroll
+                        for (int e = 0; e < 32; e += 2) {
+                            const int i = (c0 + e) >> 1;
+                            const unsigned long long z2 = f2add(f2pack(__uint_as_float(v[e]), __uint_as_float(v[e + 1])), b2p[i]);
+                            float h0, h1;
+                            f2unpack(z2, h0, h1);
+                            const unsigned long long hh = f2pack(fmaxf(h0, 0.0f), fmaxf(h1, 0.0f));
+#pragma unroll
+                            for (int o = 0; o < 4; ++o) acc[o] = f2fma(w3p[4 * i + o], hh, acc[o]);
+                        }
+                    }
+                    float pp[4];
+#pragma unroll
+                    for (int o = 0; o < 4; ++o) {
+                        float ev, od;
+                        f2unpack(acc[o], ev, od);
+                        pp[o] = ev + od;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float mu = tanhf(pp[j] + sB3[j]);
+                        a[j] = clampf(sigma > 0.0f ? fmaf(sigma, z[j], mu) : mu, -1.0f, 1.0f);
+                    }
+                }
+                // ---------------- dynamics, reward, termination
+                float u[4], s2[NS];
+                action_to_rpm(C.veh, a, u);
+#pragma unroll
+                for (int i = 0; i < NS; ++i) s2[i] = s[i];
+                rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
+                float rw;
+                {
+                    float Cr[7];
+#pragma unroll
+                    for (int i = 0; i < 7; ++i) Cr[i] = p.rewardC[i];
+                    rw = reward(Cr, s2, a);
+                }
+                const bool term = terminated(C, s2);
+                const uint32_t ep_after = ep_step + 1;
+                const bool trunc = !term && (int)ep_after >= C.episode_len;
+                // ---------------- transition record (field-major, streaming stores)
+                if (capacity > 0) {
+                    if (active) {
+                        float* rec = p.rec + (size_t)slot * F * ld + g;
+#pragma unroll
+                        for (int i = 0; i < NS; ++i) __stcs(rec + i * ld, s[i]);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) __stcs(rec + (17 + i) * ld, a[i]);
+                        __stcs(rec + 21 * ld, rw);
+                        __stcs(rec + 22 * ld, __uint_as_float(pack_flags(term, trunc, ep_step)));
+                        if (C.n_priv) {
+                            float pv[NPRIV];
+                            priv_vals(C, P, d, pv);
+#pragma unroll
+                            for (int k = 0; k < NPRIV; ++k) __stcs(rec + (23 + k) * ld, pv[k]);
+                        }
+                        if (term || trunc) {
+                            float* sd = p.side + (size_t)slot * NS * ld + g;
+#pragma unroll
+                            for (int i = 0; i < NS; ++i) __stcs(sd + i * ld, s2[i]);
+                        }
+                    }
+                    slot = (slot + 1 == capacity) ? 0 : slot + 1;
+                }
+                // ---------------- action ring: a_t into slot t mod 16; an episode end clears the ring
+                const bool reset = term || trunc;
+                const int hs = (int)(t & 15u);
+                if (!__any_sync(0xffffffffu, reset)) {
+                    uint32_t h0, h1, l0, l1;
+                    split2(a[0], a[1], h0, l0, amax);
+                    split2(a[2], a[3], h1, l1, amax);
+                    st2(tl + T_AHI + 16 + 2 * hs, h0, h1);
+                    st2(tl + T_ALO + 16 + 2 * hs, l0, l1);
+                } else {
+                    // some lane of the warp starts a new episode: rewrite the ring words (kept as
+                    // they are, slot hs <- a_t, all zero for the lanes that reset)
+                    uint32_t h0, h1, l0, l1;
+                    split2(a[0], a[1], h0, l0, amax);
+                    split2(a[2], a[3], h1, l1, amax);
+#pragma unroll 1
+                    for (int q = 0; q < 2; ++q) {
+                        uint32_t vh[16], vl[16];
+                        ld16x2(tl + T_AHI + 16 + 16 * q, vh, tl + T_ALO + 16 + 16 * q, vl);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const int sl = (32 * q + 2 * c) >> 2;  // both halves of column c share a slot
+                            if (sl == hs) { vh[c] = (c & 1) ? h1 : h0; vl[c] = (c & 1) ? l1 : l0; }
+                            if (reset) { vh[c] = 0u; vl[c] = 0u; }
+                        }
+                        st16(tl + T_AHI + 16 + 16 * q, vh);
+                        st16(tl + T_ALO + 16 + 16 * q, vl);
+                    }
+                }
+                ep_ret += rw;
+                if (reset) {
+                    n_done += 1;
+                    len_sum += ep_after;
+                    ret_sum += ep_ret;
+                    ep_index += 1;
+                    float prm7[7];
+                    reset_env(C, (uint32_t)g, ep_index, s, prm7, d);
+                    P = make_prm(prm7[0], prm7[1], prm7[2], prm7[3], prm7[4], prm7[5], prm7[6]);
+                    ep_step = 0;
+                    ep_ret = 0.0f;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NS; ++i) s[i] = s2[i];
+                    ep_step = ep_after;
+                }
+            }
+            wait_st();
+            const bool bad = !(amax < HALF_MAX);  // also catches a NaN that reached an operand
+            if (__any_sync(0xffffffffu, bad) && lane == 0 && active && p.status) atomicCAS(p.status, DEV_OK, DEV_RANGE);
+
+            // ---- write back (state, parameters, counters, history newest first)
+            if (active) {
+#pragma unroll
+                for (int i = 0; i < NS; ++i) p.state[i * ld + g] = s[i];
+                p.prm[g] = P.m; p.prm[ld + g] = P.Jx; p.prm[2 * ld + g] = P.Jy; p.prm[3 * ld + g] = P.Jz;
+                p.prm[4 * ld + g] = P.kf; p.prm[5 * ld + g] = P.km; p.prm[6 * ld + g] = P.tm;
+#pragma unroll
+                for (int i = 0; i < 6; ++i) p.dist[i * ld + g] = d[i];
+                p.ep_index[g] = ep_index; p.ep_step[g] = ep_step; p.ep_ret[g] = ep_ret;
+                p.n_done[g] = n_done; p.len_sum[g] = len_sum; p.ret_sum[g] = ret_sum;
+            }
+            const uint32_t t_end = t0u + (uint32_t)Tu;
+#pragma unroll 1
+            for (int q = 0; q < 2; ++q) {
+                uint32_t vh[16], vl[16];
+                ld16x2(tl + T_AHI + 16 + 16 * q, vh, tl + T_ALO + 16 + 16 * q, vl);
+                if (active) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const float2 x = join2(vh[c], vl[c]);
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int el = 32 * q + 2 * c + e;
+                            const int sl = el >> 2, cc = el & 3;
+                            const int i0 = (int)((t_end - (uint32_t)sl) & 15u);
+                            const int i = i0 == 0 ? 16 : i0;  // lag of slot sl after the last step
+                            if (i <= nh) p.hist[(4 * (i - 1) + cc) * ld + g] = e ? x.y : x.x;
+                        }
                     }
                 }
             }
+        }
+        // ---- unit done: publish it for the next chunk of this group
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (tid == 0 && sched) {
+            __threadfence();
+            asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(sched + 1 + ug), "r"(uk + 1) : "memory");
+        }
+    }
+    // on an abort, let the last committed MMA batch finish before the memory is released
+    if (mma_warp && *abort_flag && lane == 0 && issued) {
+        const uint32_t b = issued == 1 ? bar_d1 : bar_d2;
+        const uint32_t par = issued == 1 ? ph : ph ^ 1u;
+        for (int i = 0; i < WAIT_LIMIT; ++i) {
+            uint32_t done;
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                         "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(b), "r"(par) : "memory");
+            if (done) break;
         }
     }
     // ---- release tensor memory
@@ -646,16 +696,28 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(*tslot), "r"(T_ALLOC) : "memory");
 }
 
-// Launches T steps on env warps [w0, w1) (12 env warps = 384 envs per CTA, plus 3 MMA warps).
+// Launches T steps on env warps [w0, w1) (12 env warps = 384 envs per CTA, plus 3 MMA warps):
+// one CTA per group of 12 warps, or, with chunk > 0 and `sched` (1 + groups ints of device
+// memory), a persistent grid of at most one CTA per SM walking (group, chunk) units.
 qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, uint32_t t0, int64_t head,
-                                    float sigma, int w0, int w1, cudaStream_t st) {
+                                    float sigma, int w0, int w1, cudaStream_t st, int chunk, int* sched) {
     static bool configured = false;
     if (!configured) {
         QCHECK_CUDA(cudaFuncSetAttribute(k_rollout_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
         configured = true;
     }
-    const int grid = (w1 - w0 + NCW - 1) / NCW;
-    k_rollout_tc<<<grid, NT, SMEM, st>>>(h->dc, h->p, actor, T, t0, head, h->capacity, sigma, w0, w1);
+    const int groups = (w1 - w0 + NCW - 1) / NCW;
+    if (sched && chunk > 0) {
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        QCHECK_CUDA(cudaMemsetAsync(sched, 0, sizeof(int) * (size_t)(1 + groups), st));
+        const int grid = std::min(sms, groups);
+        k_rollout_tc<<<grid, NT, SMEM, st>>>(h->dc, h->p, actor, T, t0, head, h->capacity, sigma, w0, w1,
+                                             groups, std::min(chunk, T), sched);
+    } else {
+        k_rollout_tc<<<groups, NT, SMEM, st>>>(h->dc, h->p, actor, T, t0, head, h->capacity, sigma, w0, w1,
+                                               groups, T, nullptr);
+    }
     QCHECK_LAUNCH("k_rollout_tc");
     return QSIM_OK;
 }

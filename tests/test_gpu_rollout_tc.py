@@ -116,7 +116,7 @@ def test_tc_schedule_invariant_and_deterministic(gpu):
     d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=8, learning_starts=2)
     A = torch.tensor(_actor(d), device="cuda")
     outs = []
-    for parts, chunk in ((1, 0), (1, 0), (3, 2), (2, 1)):
+    for parts, chunk in ((1, 0), (1, 0), (3, 2), (2, 1), (1, 2)):
         h = q.qsim_create(cfg, veh)
         q.qsim_rollout_engine(h, TC)
         q.qsim_rollout_schedule(h, parts, chunk)
@@ -133,6 +133,44 @@ def test_tc_schedule_invariant_and_deterministic(gpu):
                 np.testing.assert_allclose(x, y, rtol=1e-5, atol=1e-6)
             else:
                 assert np.array_equal(x, y)
+
+
+def test_tc_persistent_units_beyond_one_wave(gpu):
+    """65,536 envs = 171 groups of 384 on at most one CTA per SM, 2-step units: chunk k of a
+    group starts after chunk k-1 of that group, on whichever CTA takes it.  Compared with
+    one launch per group for the same 7 steps (FP32-rounding agreement, see above) and, on
+    sampled envs, with the oracle for the last step."""
+    q = gpu
+    n = 65536
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=16, learning_starts=0)
+    actor = _actor(d)
+    A = torch.tensor(actor, device="cuda")
+    outs = []
+    for parts, chunk in ((1, 2), (4, 100)):
+        h = q.qsim_create(cfg, veh)
+        q.qsim_rollout_engine(h, TC)
+        q.qsim_rollout_schedule(h, parts, chunk)
+        q.qsim_rollout(h, A, 64, 7, 0.1)
+        q.qsim_sync(h)
+        info = q.qsim_info_get(h)
+        outs.append([cpu(info[k]).copy() for k in ("records", "state", "hist", "ep_step")])
+        if parts == 1:
+            ids = np.unique([O.replay_index(int(O.philox([i, 0, 4 << 24, 0], [0, 0])[0]), n)
+                             for i in range(256)])
+            e = oracle_envs(info, ids)
+            t0, head0 = info["t_now"], info["head"]
+            q.qsim_rollout(h, A, 64, 1, 0.1)
+            q.qsim_sync(h)
+            ref = O.rollout(d, W.REWARD, e, 1, t0, actor=actor.astype(np.float64), hidden=64,
+                            sigma_e=0.1, n_threads=8)
+            info = q.qsim_info_get(h)
+            compare_records(gpu_records(info, [head0], ids), ref, what="persistent sampled")
+        q.qsim_destroy(h)
+    for x, y in zip(outs[0], outs[1]):
+        if x.dtype == np.float32:
+            np.testing.assert_allclose(x, y, rtol=1e-5, atol=1e-6)
+        else:
+            assert np.array_equal(x, y)
 
 
 def test_tc_engine_other_widths_run_on_simt(gpu):
