@@ -220,7 +220,7 @@ int32_t qsim_rollout_schedule(qsim_handle* h, int32_t parts, int32_t chunk);
 
 /* Rollout kernel variant: packed = 1 uses Blackwell's paired FP32 FMA (fma.rn.f32x2: two
  * single-precision FMAs per instruction, results identical to the scalar kernel), 0 the
- * scalar kernel, -1 automatic (the autotuner decides; scalar until it has run).  Returns the
+ * scalar kernel, -1 automatic (see qsim_rollout_engine).  Returns the
  * setting in effect. */
 int32_t qsim_rollout_packed(qsim_handle* h, int32_t packed);  /* engines 0/1 of qsim_rollout_engine */
 
@@ -230,7 +230,8 @@ int32_t qsim_rollout_packed(qsim_handle* h, int32_t packed);  /* engines 0/1 of 
  * FP32 accuracy, accumulators in tensor memory, 384 envs per block; results agree with 0
  * to FP32 rounding, not bitwise; an actor input or hidden activation of magnitude >= 65504
  * is reported by qsim_sync as QSIM_ESTATE),
- * -1 automatic (the autotuner decides; scalar SIMT until it has run).  Any other value
+ * -1 automatic (the autotuner's choice once it has run; before that the tensor-core engine
+ * at hidden 64 and the paired-FMA SIMT kernel otherwise).  Any other value
  * leaves the setting unchanged.  Returns the setting in effect.  The paper's environment
  * step has no counterpart of this switch: it selects among kernels computing the same step
  * (Sec. III, Eq. 1-4 dynamics, Sec. IV actor). */

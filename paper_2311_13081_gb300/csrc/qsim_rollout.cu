@@ -643,7 +643,8 @@ extern "C" qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t 
     if (n_steps == 0) return QSIM_OK;
     int nw = h->rollout_warps ? h->rollout_warps : default_warps(hidden, h->ld, h->device);
     if (roll_smem(hidden, nw) > 227 * 1024) nw = 2;
-    int engine = h->rollout_packed > 0 ? h->rollout_packed : 0;
+    // automatic (-1): the tensor-core engine where it exists (hidden 64), else paired-FMA SIMT
+    int engine = h->rollout_packed >= 0 ? h->rollout_packed : (hidden == 64 ? 2 : 1);
     if (engine == 2 && hidden != 64) engine = 1;
     int parts = h->rollout_parts, chunk = h->rollout_chunk;
     if (parts <= 0) {

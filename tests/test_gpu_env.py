@@ -11,6 +11,8 @@ from helpers import (STATE_SCALE, assert_close, compare_records, cpu, f64, gpu_r
 
 pytestmark = pytest.mark.gpu
 
+SIMT = 1  # qsim_rollout_engine: the SIMT kernel (paired FMA); the tensor-core engine has its own file
+
 
 def test_philox_streams_bit_exact(gpu):
     q = gpu
@@ -152,6 +154,7 @@ def test_rollout_parity(gpu, hidden, n, warps):
     d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=6, learning_starts=3, episode_len=40,
                              sig_p=0.005, sig_R=0.01, sig_v=0.02, sig_w=0.02)
     h = q.qsim_create(cfg, veh)
+    q.qsim_rollout_engine(h, SIMT)
     try:
         if warps:
             q.qsim_rollout_tune(h, warps)
@@ -192,6 +195,7 @@ def test_rollout_full_size_sampled(gpu):
     n = 65536
     d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=4, learning_starts=0)
     h = q.qsim_create(cfg, veh)
+    q.qsim_rollout_engine(h, SIMT)
     try:
         actor = _actor(d, 64)
         A = torch.tensor(actor, device="cuda")
@@ -219,6 +223,7 @@ def test_rollout_deterministic(gpu):
     outs = []
     for _ in range(2):
         h = q.qsim_create(cfg, veh)
+        q.qsim_rollout_engine(h, SIMT)
         q.qsim_rollout(h, A, 64, 17, 0.1)
         info = q.qsim_info_get(h)
         outs.append((cpu(info["records"]).copy(), cpu(info["state"]).copy()))
@@ -232,6 +237,7 @@ def test_recalc_rewards_parity(gpu):
     n = 40
     d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=30, episode_len=7, learning_starts=0)
     h = q.qsim_create(cfg, veh)
+    q.qsim_rollout_engine(h, SIMT)
     try:
         A = torch.tensor(_actor(d, 64), device="cuda")
         q.qsim_rollout(h, A, 64, 45, 0.3)  # wraps the ring
@@ -265,6 +271,7 @@ def test_partitioned_schedule_is_bitwise_identical(gpu):
     outs = []
     for parts, chunk in ((1, 0), (3, 2), (2, 1)):
         h = q.qsim_create(cfg, veh)
+        q.qsim_rollout_engine(h, SIMT)
         q.qsim_rollout_schedule(h, parts, chunk)
         q.qsim_rollout(h, A, 64, 5, 0.1)
         torch.cuda.synchronize()
