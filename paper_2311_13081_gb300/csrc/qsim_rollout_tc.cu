@@ -416,6 +416,9 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 ep_ret = __ldcg(p.ep_ret + g); ret_sum = __ldcg(p.ret_sum + g);
             }
             const float sigma = sigma_in >= 0.0f ? sigma_in : p.rewardC[7];
+            float Cr[7];  // reward weights, in registers for the whole unit
+#pragma unroll
+            for (int i = 0; i < 7; ++i) Cr[i] = __ldcg(p.rewardC + i);
             float amax = 0.0f;
             // action ring: slot (t0 - i) mod 16 holds a_{t0-i} (global history is newest first);
             // slot k = ring columns 2k, 2k + 1 (packed halves), after the 16 observation columns
@@ -552,13 +555,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
 #pragma unroll
                 for (int i = 0; i < NS; ++i) s2[i] = s[i];
                 rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
-                float rw;
-                {
-                    float Cr[7];
-#pragma unroll
-                    for (int i = 0; i < 7; ++i) Cr[i] = p.rewardC[i];
-                    rw = reward(Cr, s2, a);
-                }
+                const float rw = reward(Cr, s2, a);
                 const bool term = terminated(C, s2);
                 const uint32_t ep_after = ep_step + 1;
                 const bool trunc = !term && (int)ep_after >= C.episode_len;
