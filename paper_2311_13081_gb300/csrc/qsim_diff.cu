@@ -428,8 +428,349 @@ __global__ void __launch_bounds__(VT) k_vjp_backward(VjpArgs a, int g) {
         for (int i = 0; i < 4; ++i) a.g_params[i * ld + e] = gp[i];
 }
 
+// ------------------------------------------------------------- closed loop, warp per env
+// The thread-per-env kernels above leave the GPU nearly idle at a few thousand envs (one
+// warp per SM) and re-read every activation from memory for each output.  For hidden 32 or
+// 64 (and at most 96 actor inputs) the closed loop runs one env per warp instead: every
+// lane keeps the full state and runs RK4 and its vector-Jacobian product redundantly (no
+// communication), while the actor's layers are split across lanes (lane l owns hidden units
+// l, l+32; inputs l, l+32, l+64), with broadcasts by warp shuffles and the weights in shared
+// memory (odd row strides: conflict-free for lane-varying rows and columns alike).
+// The action history and the history-input adjoints live in per-warp rings of 16 x 4
+// floats in shared memory.  Activation records for the weight gradient are written
+// env-major ([step][env][field]: one contiguous row per env).
+constexpr int WV = 4;  // warps (envs) per CTA of the warp-per-env kernels
+
+// Weights in shared memory, one copy each with odd row strides so that both orientations
+// are conflict-free: W1 [H][DA+1], W2 [H][H+1] (lane-varying rows in the forward pass,
+// lane-varying columns in the reverse pass), W3 [4][H], biases.
+struct WarpActor {
+    const float *W1, *b1, *W2, *b2, *W3, *b3;
+    int l1, l2;  // row strides of W1 and W2
+};
+
+__device__ __forceinline__ WarpActor stage_warp_actor(const float* actor, int DA, int H, float* sm) {
+    WarpActor w;
+    const int l1 = DA + 1, l2 = H + 1;
+    float* W1 = sm;
+    float* b1 = W1 + H * l1;
+    float* W2 = b1 + H;
+    float* b2 = W2 + H * l2;
+    float* W3 = b2 + H;
+    float* b3 = W3 + 4 * H;
+    const float* gW1 = actor;
+    const float* gb1 = gW1 + H * DA;
+    const float* gW2 = gb1 + H;
+    const float* gb2 = gW2 + H * H;
+    const float* gW3 = gb2 + H;
+    const float* gb3 = gW3 + 4 * H;
+    for (int i = threadIdx.x; i < H * DA; i += blockDim.x) {
+        const int j = i / DA;
+        W1[j * l1 + (i - j * DA)] = gW1[i];
+    }
+    for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
+        const int j = i / H;
+        W2[j * l2 + (i - j * H)] = gW2[i];
+    }
+    for (int i = threadIdx.x; i < H; i += blockDim.x) { b1[i] = gb1[i]; b2[i] = gb2[i]; }
+    for (int i = threadIdx.x; i < 4 * H; i += blockDim.x) W3[i] = gW3[i];
+    if (threadIdx.x < 4) b3[threadIdx.x] = gb3[threadIdx.x];
+    w.W1 = W1; w.b1 = b1; w.W2 = W2; w.b2 = b2; w.W3 = W3; w.b3 = b3; w.l1 = l1; w.l2 = l2;
+    return w;
+}
+
+__host__ __device__ inline int warp_actor_floats(int DA, int H) {
+    return H * (DA + 1) + H * (H + 1) + 2 * H + 4 * H + 4;
+}
+
+// This lane's actor inputs x[m] = input lane + 32 m: the observation of state s (lanes < 18)
+// then the action history a_{t-i} (zero before the rollout starts or beyond n_hist), read
+// through `hist(step, component)`.
+template <class Hist>
+__device__ __forceinline__ void warp_actor_input(const float* s, int t, int DA, int nh, Hist hist, float* x) {
+    const int lane = threadIdx.x & 31;
+    float o[18];
+    obs_state(s, o);
+    float own = o[0];
+#pragma unroll
+    for (int i = 1; i < 18; ++i) own = lane == i ? o[i] : own;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const int k = lane + 32 * m;
+        float v = 0.0f;
+        if (k < 18) {
+            v = own;
+        } else if (k < DA) {
+            const int i = ((k - 18) >> 2) + 1, c = (k - 18) & 3;
+            if (i <= nh && t - i >= 0) v = hist(t - i, c);
+        }
+        x[m] = v;
+    }
+}
+
+__device__ __forceinline__ float warp_sum_all(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Actor forward for this warp's env: h1, h2 for the lane's hidden units, mu on every lane.
+template <int HPL>
+__device__ __forceinline__ void warp_actor_fwd(const WarpActor& w, int DA, const float* x, float* h1,
+                                               float* h2, float* mu) {
+    constexpr int H = 32 * HPL;
+    const int lane = threadIdx.x & 31;
+    float acc[HPL];
+#pragma unroll
+    for (int j = 0; j < HPL; ++j) acc[j] = w.b1[lane + 32 * j];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const int kend = min(32, DA - 32 * m);
+        for (int kk = 0; kk < kend; ++kk) {
+            const float xk = __shfl_sync(0xffffffffu, x[m], kk);
+            const float* wr = w.W1 + lane * w.l1 + 32 * m + kk;
+#pragma unroll
+            for (int j = 0; j < HPL; ++j) acc[j] = fmaf(wr[32 * j * w.l1], xk, acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < HPL; ++j) { h1[j] = fmaxf(acc[j], 0.0f); acc[j] = w.b2[lane + 32 * j]; }
+#pragma unroll
+    for (int m = 0; m < HPL; ++m)
+        for (int kk = 0; kk < 32; ++kk) {
+            const float hk = __shfl_sync(0xffffffffu, h1[m], kk);
+            const float* wr = w.W2 + lane * w.l2 + 32 * m + kk;
+#pragma unroll
+            for (int j = 0; j < HPL; ++j) acc[j] = fmaf(wr[32 * j * w.l2], hk, acc[j]);
+        }
+#pragma unroll
+    for (int j = 0; j < HPL; ++j) h2[j] = fmaxf(acc[j], 0.0f);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        float pc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < HPL; ++j) pc = fmaf(w.W3[c * H + lane + 32 * j], h2[j], pc);
+        mu[c] = tanhf(warp_sum_all(pc) + w.b3[c]);
+    }
+}
+
+template <int HPL>
+__global__ void __launch_bounds__(32 * WV) k_vjp_forward_w(VjpArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    constexpr int H = 32 * HPL;
+    const int DA = a.DA, ld = a.ld;
+    const WarpActor w = stage_warp_actor(a.actor, DA, H, sm);
+    float* ring = sm + warp_actor_floats(DA, H) + 64 * (threadIdx.x >> 5);  // actions a_tau at (tau & 15)
+    __syncthreads();
+    const int e = blockIdx.x * WV + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (e >= a.n) return;  // warp-uniform
+    float s[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) s[i] = a.s0[i * ld + e];
+    Prm P;
+    load_vehicle_prm(a, e, P);
+    const float d0[6] = {0, 0, 0, 0, 0, 0};
+    const float half = 0.5f * (a.V.rpm_max - a.V.rpm_min);
+    float loss = 0.0f;
+    for (int t = 0; t < a.H; ++t) {
+        if (t % a.ckpt == 0 && lane < NS) {
+            float v = s[0];
+#pragma unroll
+            for (int i = 1; i < NS; ++i) v = lane == i ? s[i] : v;
+            a.ck[(size_t)(t / a.ckpt) * NS * ld + (size_t)lane * ld + e] = v;
+        }
+        float x[3], h1[HPL], h2[HPL], act[4];
+        warp_actor_input(s, t, DA, a.nh, [&](int tau, int c) { return ring[(tau & 15) * 4 + c]; }, x);
+        warp_actor_fwd<HPL>(w, DA, x, h1, h2, act);
+        __syncwarp();
+        if (lane < 4) {
+            const float v = lane == 0 ? act[0] : (lane == 1 ? act[1] : (lane == 2 ? act[2] : act[3]));
+            ring[(t & 15) * 4 + lane] = v;
+            a.A[((size_t)t * 4 + lane) * ld + e] = v;
+            if (a.actions_out) a.actions_out[((size_t)t * 4 + lane) * ld + e] = v;
+        }
+        __syncwarp();
+        float u[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) u[c] = fmaf(act[c] + 1.0f, half, a.V.rpm_min);
+        rk4(a.V, a.dt, a.renorm, s, u, P, d0);
+        loss += state_loss(a, s) + a.w_a * (act[0] * act[0] + act[1] * act[1] + act[2] * act[2] + act[3] * act[3]);
+    }
+    if (a.loss && lane == 0) a.loss[e] = loss;
+}
+
+// Reverse sweep over segment g, one env per warp.
+template <int HPL>
+__global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g) {
+    extern __shared__ __align__(16) float sm[];
+    constexpr int H = 32 * HPL;
+    const int DA = a.DA, ld = a.ld, nh = a.nh;
+    const WarpActor w = stage_warp_actor(a.actor, DA, H, sm);
+    float* adj = sm + warp_actor_floats(DA, H) + 64 * (threadIdx.x >> 5);  // dL/da_tau at (tau & 15)
+    const int e = blockIdx.x * WV + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    const bool live = e < a.n;
+    const int t0 = g * a.ckpt, t1 = min(a.H, t0 + a.ckpt);
+    const bool last = (t1 == a.H);
+    if (live) {
+        // history adjoints carried over from the later segments (zero for the last one)
+        adj[lane] = a.la[(size_t)lane * ld + e];
+        adj[lane + 32] = a.la[(size_t)(lane + 32) * ld + e];
+    }
+    __syncthreads();
+    if (!live) return;  // warp-uniform
+    const float seed = a.seed ? a.seed[e] : 1.0f;
+    Prm P;
+    load_vehicle_prm(a, e, P);
+    const float d0[6] = {0, 0, 0, 0, 0, 0};
+    const float half = 0.5f * (a.V.rpm_max - a.V.rpm_min);
+    float s[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) s[i] = a.ck[(size_t)g * NS * ld + (size_t)i * ld + e];
+    for (int t = t0; t < t1; ++t) {
+        float* ss = a.segs + (size_t)(t - t0) * NS * ld + e;
+        if (lane < NS) {
+            float v = s[0];
+#pragma unroll
+            for (int i = 1; i < NS; ++i) v = lane == i ? s[i] : v;
+            ss[(size_t)lane * ld] = v;
+        }
+        float u[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) u[c] = fmaf(a.A[((size_t)t * 4 + c) * ld + e] + 1.0f, half, a.V.rpm_min);
+        rk4(a.V, a.dt, a.renorm, s, u, P, d0);
+    }
+    __syncwarp();
+    float lam[NS], gp[7];
+    if (last) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) lam[i] = 0.0f;
+        state_loss_grad(a, s, lam);
+#pragma unroll
+        for (int i = 0; i < NS; ++i) lam[i] *= seed;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) gp[i] = 0.0f;
+    } else {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) lam[i] = a.lam[i * ld + e];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) gp[i] = a.gp[i * ld + e];
+    }
+    const size_t NR = (size_t)DA + 4 * H + 4;
+    for (int t = t1 - 1; t >= t0; --t) {
+        float st[NS];
+        const float* ss = a.segs + (size_t)(t - t0) * NS * ld + e;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) st[i] = ss[(size_t)i * ld];
+        float act[4], u[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            act[c] = a.A[((size_t)t * 4 + c) * ld + e];
+            u[c] = fmaf(act[c] + 1.0f, half, a.V.rpm_min);
+        }
+        float gs[NS], gu[4] = {0, 0, 0, 0};
+        rk4_vjp(a.V, a.dt, a.renorm, st, u, P, lam, gs, gu, gp);
+        float ga[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ga[c] = gu[c] * half + seed * 2.0f * a.w_a * act[c] + adj[(t & 15) * 4 + c];
+        __syncwarp();
+        if (lane < 4) adj[(t & 15) * 4 + lane] = 0.0f;  // slot now belongs to step t - 16
+        // actor forward at step t (its inputs: the state and the previous actions)
+        float x[3], h1[HPL], h2[HPL], mu[4];
+        warp_actor_input(st, t, DA, nh, [&](int tau, int c) { return a.A[((size_t)tau * 4 + c) * ld + e]; }, x);
+        warp_actor_fwd<HPL>(w, DA, x, h1, h2, mu);
+        // reverse: output layer, layer 2, layer 1, inputs
+        float dz3[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dz3[c] = ga[c] * (1.0f - mu[c] * mu[c]);
+        float dz2[HPL], dz1[HPL];
+#pragma unroll
+        for (int j = 0; j < HPL; ++j) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc = fmaf(w.W3[c * H + lane + 32 * j], dz3[c], acc);
+            dz2[j] = h2[j] > 0.0f ? acc : 0.0f;
+        }
+        {
+            float acc[HPL];
+#pragma unroll
+            for (int i = 0; i < HPL; ++i) acc[i] = 0.0f;
+#pragma unroll
+            for (int m = 0; m < HPL; ++m)
+                for (int jj = 0; jj < 32; ++jj) {
+                    const float dj = __shfl_sync(0xffffffffu, dz2[m], jj);
+                    const float* wr = w.W2 + (32 * m + jj) * w.l2 + lane;
+#pragma unroll
+                    for (int i = 0; i < HPL; ++i) acc[i] = fmaf(wr[32 * i], dj, acc[i]);
+                }
+#pragma unroll
+            for (int i = 0; i < HPL; ++i) dz1[i] = h1[i] > 0.0f ? acc[i] : 0.0f;
+        }
+        float dx[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int m = 0; m < HPL; ++m)
+            for (int jj = 0; jj < 32; ++jj) {
+                const float dj = __shfl_sync(0xffffffffu, dz1[m], jj);
+                const float* wr = w.W1 + (32 * m + jj) * w.l1 + lane;
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    if (lane + 32 * q < DA) dx[q] = fmaf(wr[32 * q], dj, dx[q]);
+            }
+        // observation part -> state adjoint (every lane), history part -> earlier actions
+        float go[18];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) go[k] = __shfl_sync(0xffffffffu, dx[0], k);
+        obs_vjp(st, go, gs);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int k = lane + 32 * q;
+            if (k >= 18 && k < DA) {
+                const int i = ((k - 18) >> 2) + 1, c = (k - 18) & 3;
+                if (t - i >= 0) adj[((t - i) & 15) * 4 + c] += dx[q];
+            }
+        }
+        // activation record of (step t, env e): x | h1 | h2 | dZ1 | dZ2 | dZ3
+        float* R = a.rec + (size_t)(t - t0) * NR * ld + (size_t)e * NR;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (lane + 32 * q < DA) R[lane + 32 * q] = x[q];
+#pragma unroll
+        for (int j = 0; j < HPL; ++j) {
+            R[DA + lane + 32 * j] = h1[j];
+            R[DA + H + lane + 32 * j] = h2[j];
+            R[DA + 2 * H + lane + 32 * j] = dz1[j];
+            R[DA + 3 * H + lane + 32 * j] = dz2[j];
+        }
+        if (lane < 4)
+            R[DA + 4 * H + lane] = lane == 0 ? dz3[0] : (lane == 1 ? dz3[1] : (lane == 2 ? dz3[2] : dz3[3]));
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < NS; ++i) lam[i] = gs[i];
+        if (t >= 1) {
+            float lg[NS];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) lg[i] = 0.0f;
+            state_loss_grad(a, st, lg);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) lam[i] = fmaf(seed, lg[i], lam[i]);
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) a.lam[i * ld + e] = lam[i];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) a.gp[i * ld + e] = gp[i];
+        if (g == 0 && a.g_params)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a.g_params[i * ld + e] = gp[i];
+    }
+    a.la[(size_t)lane * ld + e] = adj[lane];
+    a.la[(size_t)(lane + 32) * ld + e] = adj[lane + 32];
+}
+
 // Partial actor-weight gradient of segment g over env chunk blockIdx.x (closed loop).
-__global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g) {
+// Records are field-major (fs = ld, es = 1: the thread-per-env kernels) or env-major
+// (fs = 1, es = NR: the warp-per-env kernels).
+__global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g, int fs, int es) {
     extern __shared__ __align__(16) float sm[];
     const int ld = a.ld, DA = a.DA, H = a.hid;
     const int t0 = g * a.ckpt, t1 = min(a.H, t0 + a.ckpt);
@@ -437,7 +778,9 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g) {
     const int ne = min(a.chunk, a.n - e0);
     if (ne <= 0) return;
     const size_t NR = (size_t)DA + 4 * H + 4;
-    float* P = a.part + (size_t)blockIdx.x * a.PA;
+    // the chunk's partial gradient accumulates in shared memory over the segment's steps and
+    // is written out once
+    float* P = sm + GEMM_SMEM;
     float* gW1 = P;
     float* gb1 = gW1 + H * DA;
     float* gW2 = gb1 + H;
@@ -445,36 +788,38 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g) {
     float* gW3 = gb2 + H;
     float* gb3 = gW3 + 4 * H;
     for (int t = t0; t < t1; ++t) {
-        const float* R = a.rec + (size_t)(t - t0) * NR * ld + e0;
+        const float* R = a.rec + (size_t)(t - t0) * NR * ld + (size_t)e0 * es;
         const float* O = R;
-        const float* H1 = R + (size_t)DA * ld;
-        const float* H2 = H1 + (size_t)H * ld;
-        const float* dZ1 = H2 + (size_t)H * ld;
-        const float* dZ2 = dZ1 + (size_t)H * ld;
-        const float* dZ3 = dZ2 + (size_t)H * ld;
+        const float* H1 = R + (size_t)DA * fs;
+        const float* H2 = H1 + (size_t)H * fs;
+        const float* dZ1 = H2 + (size_t)H * fs;
+        const float* dZ2 = dZ1 + (size_t)H * fs;
+        const float* dZ3 = dZ2 + (size_t)H * fs;
         const bool first = (t == t0);
-        cta_gemm(H, DA, ne, Mat{dZ1, ld, 1}, Mat{O, 1, ld}, sm, [&](int m, int n, float v) {
+        cta_gemm(H, DA, ne, Mat{dZ1, fs, es}, Mat{O, es, fs}, sm, [&](int m, int n, float v) {
             float* p = gW1 + m * DA + n;
             *p = first ? v : *p + v;
         });
-        cta_gemm(H, H, ne, Mat{dZ2, ld, 1}, Mat{H1, 1, ld}, sm, [&](int m, int n, float v) {
+        cta_gemm(H, H, ne, Mat{dZ2, fs, es}, Mat{H1, es, fs}, sm, [&](int m, int n, float v) {
             float* p = gW2 + m * H + n;
             *p = first ? v : *p + v;
         });
-        cta_gemm(4, H, ne, Mat{dZ3, ld, 1}, Mat{H2, 1, ld}, sm, [&](int m, int n, float v) {
+        cta_gemm(4, H, ne, Mat{dZ3, fs, es}, Mat{H2, es, fs}, sm, [&](int m, int n, float v) {
             float* p = gW3 + m * H + n;
             *p = first ? v : *p + v;
         });
         for (int j = threadIdx.x; j < 2 * H + 4; j += LT) {
-            const float* src = j < H ? dZ1 + (size_t)j * ld : (j < 2 * H ? dZ2 + (size_t)(j - H) * ld
-                                                                         : dZ3 + (size_t)(j - 2 * H) * ld);
+            const float* src = j < H ? dZ1 + (size_t)j * fs : (j < 2 * H ? dZ2 + (size_t)(j - H) * fs
+                                                                         : dZ3 + (size_t)(j - 2 * H) * fs);
             float* dst = j < H ? gb1 + j : (j < 2 * H ? gb2 + (j - H) : gb3 + (j - 2 * H));
             float s = 0.0f;
-            for (int q = 0; q < ne; ++q) s += ldcg(src + q);
+            for (int q = 0; q < ne; ++q) s += ldcg(src + (size_t)q * es);
             *dst = first ? s : *dst + s;
         }
         __syncthreads();
     }
+    float* out = a.part + (size_t)blockIdx.x * a.PA;
+    for (int i = threadIdx.x; i < a.PA; i += LT) out[i] = P[i];
 }
 
 // g_actor += sum over chunks (fixed order).
@@ -499,7 +844,7 @@ static WsLayout ws_layout(const qsim_vjp_desc& d, int DA, int PA, int nchunk) {
     auto take = [&](size_t floats) { size_t o = off; off += align_up(floats); return o; };
     w.ck = take(nseg * NS * ld);
     w.A = take((size_t)d.H * 4 * ld);
-    w.la = take(d.mode == 1 ? (size_t)d.H * 4 * ld : 0);
+    w.la = take(d.mode == 1 ? (size_t)std::max(d.H, 16) * 4 * ld : 0);  // >= the warp path's 64-float ring
     w.segs = take((size_t)d.ckpt * NS * ld);
     w.lam = take(NS * ld);
     w.gp = take(8 * ld);
@@ -511,7 +856,7 @@ static WsLayout ws_layout(const qsim_vjp_desc& d, int DA, int PA, int nchunk) {
     return w;
 }
 
-static constexpr int kChunk = 64;
+static constexpr int kChunk = 32;  // envs per weight-gradient CTA
 
 }  // namespace qsim
 
@@ -579,19 +924,52 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
         QCHECK_CUDA(cudaFuncSetAttribute(k_vjp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     const int grid = (d->n + VT - 1) / VT;
-    k_vjp_forward<<<grid, VT, smem, cs>>>(a);
+    // closed loop at hidden 32 / 64: one env per warp
+    const bool warp_path = d->mode == 1 && (a.hid == 32 || a.hid == 64) && a.DA <= 96;
+    const int gridw = (d->n + WV - 1) / WV;
+    const size_t smem_fw = sizeof(float) * (size_t)(warp_actor_floats(a.DA, a.hid) + 64 * WV);
+    const size_t smem_bw = smem_fw;
+    if (warp_path) {
+        static bool configured[2] = {false, false};
+        const int hi = a.hid == 64;
+        if (!configured[hi]) {
+            auto fw = hi ? k_vjp_forward_w<2> : k_vjp_forward_w<1>;
+            auto bw = hi ? k_vjp_backward_w<2> : k_vjp_backward_w<1>;
+            QCHECK_CUDA(cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            QCHECK_CUDA(cudaFuncSetAttribute(bw, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            configured[hi] = true;
+        }
+        if (a.hid == 64) k_vjp_forward_w<2><<<gridw, 32 * WV, smem_fw, cs>>>(a);
+        else k_vjp_forward_w<1><<<gridw, 32 * WV, smem_fw, cs>>>(a);
+    } else {
+        k_vjp_forward<<<grid, VT, smem, cs>>>(a);
+    }
     QCHECK_LAUNCH("k_vjp_forward");
     const bool want_grad = g_actions || g_actor || g_params;
     if (!want_grad) return QSIM_OK;
     if (d->mode == 1) {
-        QCHECK_CUDA(cudaMemsetAsync(a.la, 0, sizeof(float) * (size_t)d->H * 4 * d->ld, cs));
+        QCHECK_CUDA(cudaMemsetAsync(a.la, 0, sizeof(float) * (size_t)std::max(d->H, 16) * 4 * d->ld, cs));
         if (g_actor) QCHECK_CUDA(cudaMemsetAsync(g_actor, 0, sizeof(float) * (size_t)a.PA, cs));
     }
+    const int NR = a.DA + 4 * a.hid + 4;
+    const size_t smem_wg = sizeof(float) * (size_t)(GEMM_SMEM + a.PA);
+    if (d->mode == 1 && g_actor) {
+        static size_t wg_configured = 0;
+        if (smem_wg > 48 * 1024 && smem_wg > wg_configured) {
+            QCHECK_CUDA(cudaFuncSetAttribute(k_vjp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_wg));
+            wg_configured = smem_wg;
+        }
+    }
     for (int g = a.nseg - 1; g >= 0; --g) {
-        k_vjp_backward<<<grid, VT, smem, cs>>>(a, g);
+        if (warp_path) {
+            if (a.hid == 64) k_vjp_backward_w<2><<<gridw, 32 * WV, smem_bw, cs>>>(a, g);
+            else k_vjp_backward_w<1><<<gridw, 32 * WV, smem_bw, cs>>>(a, g);
+        } else {
+            k_vjp_backward<<<grid, VT, smem, cs>>>(a, g);
+        }
         QCHECK_LAUNCH("k_vjp_backward");
         if (d->mode == 1 && g_actor) {
-            k_vjp_wgrad<<<a.nchunk, LT, sizeof(float) * GEMM_SMEM, cs>>>(a, g);
+            k_vjp_wgrad<<<a.nchunk, LT, smem_wg, cs>>>(a, g, warp_path ? 1 : a.ld, warp_path ? NR : 1);
             QCHECK_LAUNCH("k_vjp_wgrad");
             k_vjp_wreduce<<<(a.PA + 255) / 256, 256, 0, cs>>>(a);
             QCHECK_LAUNCH("k_vjp_wreduce");
