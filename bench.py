@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--only-learner", type=int, default=0, metavar="RUNS",
                     help="only the batched-learner sample with RUNS runs (for profiling)")
     ap.add_argument("--learner-steps", type=int, default=20)
+    ap.add_argument("--only-diff", action="store_true",
+                    help="only the differentiation sample (c3 shape), for profiling")
     ap.add_argument("--warps", type=int, default=0,
                     help="pin the rollout's warps per block and skip the autotuner (profiling)")
     ap.add_argument("--parts", type=int, default=1, help="with --warps: env partitions")
@@ -446,6 +448,11 @@ def main():
     import paper_2311_13081_gb300 as q
     import workloads as W
 
+    if args.only_diff:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        q.load()
+        print(json.dumps({"differentiation_c3": measure_diff(torch, q, W)}))
+        return
     if args.only_learner:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         q.load()
