@@ -175,6 +175,21 @@ def measure_ffma(torch, q):
     return {"ffma": flops / (ms * 1e-3) / 1e12, "ffma2": flops / (ms2 * 1e-3) / 1e12}
 
 
+def measure_mma_rate(torch, q):
+    """SM cycles per tcgen05.mma (kind::f16, M 128, K 16) in a chain of 64, by accumulator
+    width N and by the number of warps issuing chains into disjoint columns."""
+    cyc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    res = {}
+    for n_cols, n_warps in ((64, 1), (128, 1), (256, 1), (64, 2), (128, 4)):
+        q.qsim_mma_probe(64, n_cols, n_warps, cyc)  # warm-up
+        q.qsim_mma_probe(64, n_cols, n_warps, cyc)
+        torch.cuda.synchronize()
+        c = int(cyc.item())
+        res[f"N{n_cols // n_warps}_x{n_warps}warps"] = {
+            "cycles": c, "cycles_per_mma": c / (64 * n_warps) if c > 0 else None}
+    return res
+
+
 def measure_dynamics(torch, q, veh):
     """Paper's simulator benchmark shape: 8,192 envs x 1e6 RK4 steps, no policy."""
     res = {}
@@ -542,6 +557,7 @@ def main():
     extras = {}
     if rank == 0 and not args.no_extras:
         extras["fp32_fma_probe_tflops"] = measure_ffma(torch, q)
+        extras["tcgen05_mma_issue_probe"] = measure_mma_rate(torch, q)
         extras["reward_recalc"] = measure_recalc(torch, q, h, n, horizon, hbm)
         st = q.qsim_stats_get(h)
         extras["episodes"] = st

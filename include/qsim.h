@@ -249,6 +249,15 @@ int32_t qsim_rollout_autotune(qsim_handle* h, const float* actor, int32_t hidden
  * device scratch word.  Used to confirm the FP32 roofline peak. */
 qsim_status qsim_ffma_probe(int32_t n_blocks, int32_t iters, float* out, void* stream);
 
+/* Tensor-core issue-rate probe (one block): n_warps (1..4) warps each issue a chain of n_mma
+ * (1..4096) tcgen05.mma instructions (kind::f16, M 128, N = n_cols / n_warps (a multiple of
+ * 16, n_cols <= 256), K 16, zero operands) into disjoint accumulator columns; *cycles
+ * (device int64) receives the SM cycles from the first issue until every chain has
+ * completed, or -1 if the completion wait ran out.  Shows that one issuing thread completes
+ * one such MMA per ~65 cycles for any N <= 128 while chains of several warps overlap, which
+ * shapes the tensor-core rollout (no counterpart in the paper). */
+qsim_status qsim_mma_probe(int32_t n_mma, int32_t n_cols, int32_t n_warps, int64_t* cycles, void* stream);
+
 /* Recompute every stored reward from (s', a) with the current reward constants (Sec. VI
  * reward recalculation). */
 qsim_status qsim_recalc_rewards(qsim_handle* h, void* stream);

@@ -122,6 +122,7 @@ _SIGS = {
     "qsim_rollout_packed": (C.c_int32, [P, C.c_int32]),
     "qsim_rollout_engine": (C.c_int32, [P, C.c_int32]),
     "qsim_ffma_probe": (C.c_int, [C.c_int32, C.c_int32, P, P]),
+    "qsim_mma_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P]),
     "qsim_recalc_rewards": (C.c_int, [P, P]),
     "qsim_set_reward": (C.c_int, [P, P, C.c_float, P]),
     "qsim_stats_get": (C.c_int, [P, C.POINTER(QsimStats), P]),
@@ -365,6 +366,11 @@ def qsim_rollout_engine(h, engine=-2) -> int:
     """0 SIMT, 1 SIMT paired FMA, 2 tensor cores (hidden 64), -1 automatic; other values
     only query."""
     return int(_lib.qsim_rollout_engine(h, engine))
+
+
+def qsim_mma_probe(n_mma, n_cols, n_warps, cycles, stream=None):
+    load()
+    _chk(_lib.qsim_mma_probe(n_mma, n_cols, n_warps, _ptr(cycles), _stream(stream)))
 
 
 def qsim_ffma_probe(n_blocks, iters, out, stream=None):

@@ -7,9 +7,11 @@
 // 82 -> 64 -> 64 products run:
 //   * a tile is 128 envs = the MMA's M = the 128 TMEM lanes; thread r of the tile owns env
 //     r and TMEM lane r.  A CTA holds three tiles of 4 compute warps each plus one MMA warp
-//     per tile (warp specialisation).  The SM executes one tcgen05.mma every ~70 cycles
-//     whatever N (<= 128) and whichever warp issues it, so the design minimises MMA
-//     instructions: fp16 operands give K = 16 per instruction, and every operand is kept
+//     per tile (warp specialisation).  A chain of tcgen05.mma issued by one thread completes
+//     one instruction per ~65 cycles whatever N (<= 128) -- chains of several warps proceed
+//     in parallel -- so a tile's MMA latency per step is its instruction count x ~65 cycles
+//     and the design minimises MMA instructions: fp16 operands give K = 16 per instruction,
+//     and every operand is kept
 //     as two halves, x = x_hi + x_lo (x_hi = fp16(x), x_lo = fp16(x - x_hi)), so that
 //     A.W ~ A_hi.W_hi + A_hi.W_lo + A_lo.W_hi is FP32-accurate (the dropped A_lo.W_lo term
 //     and the rounding of the lo halves are ~2^-22 relative): 18 MMAs for layer 1 and 12
@@ -722,4 +724,66 @@ qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, u
 // Env warps per CTA of the tensor-core kernel (one CTA per SM).
 int rollout_tc_warps_per_cta() { return NCW; }
 
+// ------------------------------------------------------------------ MMA issue-rate probe
+// One CTA: n_warps warps, lane 0 of each issues n_mma tcgen05.mma (kind::f16, M 128, N =
+// n_cols / n_warps, K 16, A in TMEM, zero operands) into its own accumulator columns, then
+// commits; cycles from the first issue to the completion of every chain -> out[0].
+__global__ void __launch_bounds__(128) k_mma_probe(int n_mma, int n_cols, int n_warps, long long* out) {
+    extern __shared__ __align__(1024) unsigned char smb[];
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smb + 16384);
+    const uint32_t bar = smem_addr(smb + 16384 + 64);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < 16384 / 4; i += blockDim.x) reinterpret_cast<float*>(smb)[i] = 0.0f;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(n_warps));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(smem_addr(tslot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tm = *tslot;
+    const int N = n_cols / n_warps;
+    const long long c0 = clock64();
+    if (warp < n_warps && lane == 0) {
+        const uint32_t idesc = (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(TILE >> 4) << 24);
+        const uint64_t b = sdesc(smem_addr(smb), 2);  // N rows x 16 halves, zeros
+        for (int i = 0; i < n_mma; ++i)
+            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}"
+                         :: "r"(tm + (uint32_t)(warp * N)), "r"(tm + 256u), "l"(b), "r"(idesc), "r"((uint32_t)i));
+        mma_commit(bar);
+    }
+    if (threadIdx.x == 0) {
+        bool ok = false;
+        for (int i = 0; i < WAIT_LIMIT && !ok; ++i) {
+            uint32_t done;
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                         "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar) : "memory");
+            ok = done != 0;
+        }
+        out[0] = ok ? clock64() - c0 : -1;
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tm) : "memory");
+}
+
 }  // namespace qsim
+
+extern "C" qsim_status qsim_mma_probe(int32_t n_mma, int32_t n_cols, int32_t n_warps, int64_t* cycles,
+                                      void* stream) {
+    using namespace qsim;
+    if (!cycles || n_mma < 1 || n_mma > 4096 || n_warps < 1 || n_warps > 4 || n_cols < 16 * n_warps ||
+        n_cols > 256 || (n_cols / n_warps) % 16 != 0 || n_cols % n_warps != 0)
+        return fail(QSIM_EINVAL, "qsim_mma_probe: bad arguments");
+    k_mma_probe<<<1, 128, 16384 + 128, (cudaStream_t)stream>>>(n_mma, n_cols, n_warps,
+                                                                reinterpret_cast<long long*>(cycles));
+    QCHECK_LAUNCH("k_mma_probe");
+    return QSIM_OK;
+}
