@@ -32,7 +32,8 @@ namespace cg = cooperative_groups;
 namespace qsim {
 
 
-constexpr int SMEM_MAIN = GEMM_SMEM > smlp::floats() ? GEMM_SMEM : smlp::floats();
+constexpr int SMEM_ENGINE = smlp::floats() > smlp::floats2() ? smlp::floats() : smlp::floats2();
+constexpr int SMEM_MAIN = GEMM_SMEM > SMEM_ENGINE ? GEMM_SMEM : SMEM_ENGINE;
 
 struct LearnHyper {
     float gamma, tau, lr, beta1, beta2, eps, sigma_t, noise_clip;
@@ -734,8 +735,8 @@ __device__ __noinline__ void td3_update(RunDesc& R, int64_t head, int64_t size, 
     cluster_sync_all(nS);
 }
 
-// One TD3 update with every network pass resident in shared memory (hidden <= 64): same
-// phases and cluster reduction as td3_update.  HT/DAT/DCT fix the hidden width and the
+// One TD3 update with every network pass resident in shared memory (hidden <= 64, or the
+// 128-wide engine shape for HT = 128): same phases and cluster reduction as td3_update.  HT/DAT/DCT fix the hidden width and the
 // actor/critic input widths at compile time (0: taken from the run descriptor), so that the
 // common shapes get fully unrolled shared-memory GEMMs.
 template <int HT, int DAT, int DCT>
@@ -748,7 +749,8 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
     const int H = HT ? HT : R.H, DA = DAT ? DAT : R.DA, DC = DCT ? DCT : R.DC;
     const LearnHyper& hp = R.hp;
     const int j0 = rk * Bc;
-    const Buf b = carve(sm);
+    Buf b = HT == 128 ? carve2(sm) : carve(sm);  // the 64-wide shape is never re-bound
+    const int MC = b.mc;
     float* red = sm + SMEM_MAIN;
     // a9: gather
     gather_all(R, j0, Bc, u, head, size, t_now, S, sm);
@@ -783,6 +785,7 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
         const float* W = c ? R.c2 : R.c1;
         float* q = c ? S.q2 : S.q1;
         stage(W, DC, H, 1, b);
+        if constexpr (HT == 128) bind_grads(b, c ? S.g2 : S.g1, DC, H, 1);
         for (int r0 = 0; r0 < Bc; r0 += MC) {
             const int mc = min(MC, Bc - r0);
             forward(DC, H, 1, S.oc, DC, r0, mc, b, q, 1, false);
@@ -846,6 +849,7 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
     }
     __syncthreads();
     stage(R.actor, DA, H, 4, b);
+    if constexpr (HT == 128) bind_grads(b, S.ga, DA, H, 4);
     for (int r0 = 0; r0 < Bc; r0 += MC) {
         const int mc = min(MC, Bc - r0);
         forward(DA, H, 4, S.oa, DA, r0, mc, b, S.mu, 4, true);
@@ -943,6 +947,7 @@ __global__ void __launch_bounds__(LT) k_train(RunDesc* runs, const int* order, c
                 n_upd = t_now >= R.start_updates ? R.hp.updates_per_step : 0;
             }
             const bool resident = R.H <= smlp::HP && R.DC <= smlp::INP && R.DA <= smlp::INP;
+            const bool resident128 = R.H == 128 && R.DA == 82 && R.DC == 90;
             for (int k = 0; k < n_upd; ++k) {
                 if (resident) {
                     // specialised shapes: hidden 64 or 32 over 16 actions of history, and the
@@ -960,6 +965,10 @@ __global__ void __launch_bounds__(LT) k_train(RunDesc* runs, const int* order, c
                     else
                         td3_update_smem<0, 0, 0>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S,
                                                  my, scr_stride, rk, nS, sm);
+                } else if (resident128) {
+                    // hidden 128 with 16 actions of history: the 128-wide engine shape
+                    td3_update_smem<128, 82, 90>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S, my,
+                                                 scr_stride, rk, nS, sm);
                 } else
                     td3_update(R, head, size, t_now, (uint32_t)u, t_a, t_c, S, my, scr_stride,
                                blockIdx.x - rk, rk, nS, sm);

@@ -1,10 +1,13 @@
-// qsim_smlp.cuh -- shared-memory-resident MLP engine of the learner (hidden width <= 64).
+// qsim_smlp.cuh -- shared-memory-resident MLP engine of the learner (hidden width <= 128).
 //
 // One network pass of a CTA: the network's weights are staged into shared memory once (a
-// straight row-major copy), then the CTA's samples are processed in chunks of up to 64 rows
-// whose activations stay in shared memory between layers; weight gradients accumulate in
-// shared memory across chunks and are written out once.  Compared with the global-scratch
-// path this replaces ~30 L2 round trips per update with one weight stage per pass.
+// straight row-major copy), then the CTA's samples are processed in chunks of rows whose
+// activations stay in shared memory between layers; weight gradients accumulate across
+// chunks and are written out once.  Compared with the global-scratch path this replaces
+// ~30 L2 round trips per update with one weight stage per pass.  Two shapes: hidden <= 64
+// (64-row chunks, gradient accumulators in shared memory) and hidden <= 128 (32-row
+// chunks, gradients accumulated directly in the CTA's own gradient output, which stays in
+// L2: there is no room for both next to the 128-wide weights).
 //
 // Layouts (floats): everything row-major with padded row strides chosen == 4 (mod 32) so
 // that the GEMMs' 128-bit shared loads are conflict-free: input chunk Xs[r][k], hidden
@@ -15,23 +18,33 @@
 namespace qsim {
 namespace smlp {
 
-constexpr int HP = 64;    // largest hidden width handled here
+constexpr int HP = 64;    // hidden bound of the 64-wide shape
 constexpr int INP = 104;  // row stride of the input chunk (critic input <= 100), multiple of 8
 constexpr int AS = 68;    // row stride of hidden activations (== 4 mod 32: conflict-free)
 constexpr int LD1 = 100;  // row stride of W1 [j][k] (>= input width, == 4 mod 32)
 constexpr int LD2 = 68;   // row stride of W2 [j][k]
 constexpr int MC = 64;    // rows per chunk
+// the 128-wide shape
+constexpr int HP2 = 128, AS2 = 132, LD22 = 132, MC2 = 32;
 
 struct Buf {
     float *Xs, *H1s, *H2s, *dZ2s, *dZ1s, *dZ3s;
     float *W1s, *b1, *W2s, *b2, *W3s, *b3;
     float *gW1, *gb1, *gW2, *gb2, *gW3, *gb3;
+    int hp, as, ld2, mc;  // hidden bound, activation and W2 row strides, rows per chunk
+    int g1, g2, g3;       // row strides of the gradient accumulators gW1, gW2, gW3
+    bool gsm;             // accumulators in shared memory (else the gradient output itself)
 };
 
 __host__ __device__ constexpr int floats() {
     return MC * INP + 4 * MC * AS + MC * 4 +                // activations
            HP * LD1 + HP + HP * LD2 + HP + 4 * HP + 4 +    // weights
            HP * INP + HP + HP * HP + HP + 4 * HP + 4 + 64; // gradient accumulators (+ slack)
+}
+
+__host__ __device__ constexpr int floats2() {
+    return MC2 * INP + 4 * MC2 * AS2 + MC2 * 4 +                  // activations
+           HP2 * LD1 + HP2 + HP2 * LD22 + HP2 + 4 * HP2 + 4 + 64;  // weights (+ slack)
 }
 
 __device__ __forceinline__ Buf carve(float* sm) {
@@ -55,7 +68,45 @@ __device__ __forceinline__ Buf carve(float* sm) {
     b.gb2 = p; p += HP;
     b.gW3 = p; p += 4 * HP;
     b.gb3 = p;
+    b.hp = HP; b.as = AS; b.ld2 = LD2; b.mc = MC;
+    b.g1 = INP; b.g2 = HP; b.g3 = HP;
+    b.gsm = true;
     return b;
+}
+
+// The 128-wide shape; the gradient accumulators are bound per network by bind_grads.
+__device__ __forceinline__ Buf carve2(float* sm) {
+    Buf b;
+    float* p = sm;
+    b.Xs = p; p += MC2 * INP;
+    b.H1s = p; p += MC2 * AS2;
+    b.H2s = p; p += MC2 * AS2;
+    b.dZ2s = p; p += MC2 * AS2;
+    b.dZ1s = p; p += MC2 * AS2;
+    b.dZ3s = p; p += MC2 * 4;
+    b.W1s = p; p += HP2 * LD1;
+    b.b1 = p; p += HP2;
+    b.W2s = p; p += HP2 * LD22;
+    b.b2 = p; p += HP2;
+    b.W3s = p; p += 4 * HP2;
+    b.b3 = p;
+    b.gW1 = b.gb1 = b.gW2 = b.gb2 = b.gW3 = b.gb3 = nullptr;
+    b.hp = HP2; b.as = AS2; b.ld2 = LD22; b.mc = MC2;
+    b.g1 = b.g2 = b.g3 = 0;
+    b.gsm = false;
+    return b;
+}
+
+// Point the accumulators of a 128-wide engine at the gradient output G (W1[H][in] b1
+// W2[H][H] b2 W3[out][H] b3, global, owned by this CTA); the shared-memory shape keeps its own.
+__device__ __forceinline__ void bind_grads(Buf& b, float* G, int in, int H, int out) {
+    if (b.gsm) return;
+    b.gW1 = G; b.g1 = in;
+    b.gb1 = G + H * in;
+    b.gW2 = b.gb1 + H; b.g2 = H;
+    b.gb2 = b.gW2 + H * H;
+    b.gW3 = b.gb2 + H; b.g3 = H;
+    b.gb3 = b.gW3 + out * H;
 }
 
 // C(m, n) = sum_k A(m, k) B(k, n) with A row-major [m][k] (lda, K a multiple of 4, padded
@@ -287,12 +338,12 @@ __device__ __forceinline__ void stage(const float* W, int in, int H, int out, co
             b.b1[i - e1] = v;
         } else if (i < e3) {
             const int r = (i - e2) / H;
-            b.W2s[r * LD2 + (i - e2 - r * H)] = v;
+            b.W2s[r * b.ld2 + (i - e2 - r * H)] = v;
         } else if (i < e4) {
             b.b2[i - e3] = v;
         } else if (i < e5) {
             const int o = (i - e4) / H;
-            b.W3s[o * HP + (i - e4 - o * H)] = v;
+            b.W3s[o * b.hp + (i - e4 - o * H)] = v;
         } else {
             b.b3[i - e5] = v;
         }
@@ -324,15 +375,16 @@ __device__ __forceinline__ void forward(int in, int H, int out, const float* X, 
                      [&](int i) { return (i / K4) * INP + i % K4; }, [&](int i) { return i % K4 < in; });
     }
     __syncthreads();
+    const int as = b.as;
     gemm_nt(mc, H, K4, b.Xs, INP, b.W1s, LD1,
-            [&](int m, int n, float v) { b.H1s[m * AS + n] = fmaxf(v + b.b1[n], 0.0f); });
-    gemm_nt(mc, H, H, b.H1s, AS, b.W2s, LD2,
-            [&](int m, int n, float v) { b.H2s[m * AS + n] = fmaxf(v + b.b2[n], 0.0f); });
+            [&](int m, int n, float v) { b.H1s[m * as + n] = fmaxf(v + b.b1[n], 0.0f); });
+    gemm_nt(mc, H, H, b.H1s, as, b.W2s, b.ld2,
+            [&](int m, int n, float v) { b.H2s[m * as + n] = fmaxf(v + b.b2[n], 0.0f); });
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int item = warp; item < mc * out; item += LT / 32) {
         const int r = item / out, o = item - r * out;
         float acc = 0.0f;
-        for (int j = lane; j < H; j += 32) acc = fmaf(b.W3s[o * HP + j], b.H2s[r * AS + j], acc);
+        for (int j = lane; j < H; j += 32) acc = fmaf(b.W3s[o * b.hp + j], b.H2s[r * as + j], acc);
         acc = warp_sum(acc) + b.b3[o];
         if (lane == 0) Y[(size_t)(r0 + r) * ldy + o] = tanh_out ? tanhf(acc) : acc;
     }
@@ -344,12 +396,13 @@ __device__ __forceinline__ void forward(int in, int H, int out, const float* X, 
 // writes dLoss/dX for columns [x_lo, in) to dX (global [rows][ldx]) when dX != nullptr.
 __device__ __forceinline__ void backward(int in, int H, int out, int r0, int mc, const Buf& b,
                                          bool first, bool want_w, float* dX, int ldx, int x_lo) {
+    const int as = b.as;
     if (want_w) {
         for (int i = threadIdx.x; i < out * H; i += LT) {
             const int o = i / H, j = i - o * H;
             float s = 0.0f;
-            for (int r = 0; r < mc; ++r) s = fmaf(b.dZ3s[r * 4 + o], b.H2s[r * AS + j], s);
-            b.gW3[o * HP + j] = first ? s : b.gW3[o * HP + j] + s;
+            for (int r = 0; r < mc; ++r) s = fmaf(b.dZ3s[r * 4 + o], b.H2s[r * as + j], s);
+            b.gW3[o * b.g3 + j] = first ? s : b.gW3[o * b.g3 + j] + s;
         }
         if (threadIdx.x < out) {
             float s = 0.0f;
@@ -360,30 +413,30 @@ __device__ __forceinline__ void backward(int in, int H, int out, int r0, int mc,
     for (int i = threadIdx.x; i < mc * H; i += LT) {
         const int r = i / H, j = i - r * H;
         float v = 0.0f;
-        for (int o = 0; o < out; ++o) v = fmaf(b.dZ3s[r * 4 + o], b.W3s[o * HP + j], v);
-        b.dZ2s[r * AS + j] = b.H2s[r * AS + j] > 0.0f ? v : 0.0f;
+        for (int o = 0; o < out; ++o) v = fmaf(b.dZ3s[r * 4 + o], b.W3s[o * b.hp + j], v);
+        b.dZ2s[r * as + j] = b.H2s[r * as + j] > 0.0f ? v : 0.0f;
     }
     __syncthreads();
     if (want_w) {
-        gemm_km(H, H, mc, b.dZ2s, AS, b.H1s, AS, [&](int m, int n, float v) {
-            b.gW2[m * HP + n] = first ? v : b.gW2[m * HP + n] + v;
+        gemm_km(H, H, mc, b.dZ2s, as, b.H1s, as, [&](int m, int n, float v) {
+            b.gW2[m * b.g2 + n] = first ? v : b.gW2[m * b.g2 + n] + v;
         });
         for (int j = threadIdx.x; j < H; j += LT) {
             float s = 0.0f;
-            for (int r = 0; r < mc; ++r) s += b.dZ2s[r * AS + j];
+            for (int r = 0; r < mc; ++r) s += b.dZ2s[r * as + j];
             b.gb2[j] = first ? s : b.gb2[j] + s;
         }
     }
-    gemm_mk(mc, H, H, b.dZ2s, AS, b.W2s, LD2, [&](int m, int n, float v) {
-        b.dZ1s[m * AS + n] = b.H1s[m * AS + n] > 0.0f ? v : 0.0f;
+    gemm_mk(mc, H, H, b.dZ2s, as, b.W2s, b.ld2, [&](int m, int n, float v) {
+        b.dZ1s[m * as + n] = b.H1s[m * as + n] > 0.0f ? v : 0.0f;
     });
     if (want_w) {
-        gemm_km(H, in, mc, b.dZ1s, AS, b.Xs, INP, [&](int m, int n, float v) {
-            b.gW1[m * INP + n] = first ? v : b.gW1[m * INP + n] + v;
+        gemm_km(H, in, mc, b.dZ1s, as, b.Xs, INP, [&](int m, int n, float v) {
+            b.gW1[m * b.g1 + n] = first ? v : b.gW1[m * b.g1 + n] + v;
         });
         for (int j = threadIdx.x; j < H; j += LT) {
             float s = 0.0f;
-            for (int r = 0; r < mc; ++r) s += b.dZ1s[r * AS + j];
+            for (int r = 0; r < mc; ++r) s += b.dZ1s[r * as + j];
             b.gb1[j] = first ? s : b.gb1[j] + s;
         }
     }
@@ -392,7 +445,7 @@ __device__ __forceinline__ void backward(int in, int H, int out, int r0, int mc,
         for (int i = threadIdx.x; i < mc * nc; i += LT) {
             const int r = i / nc, c = x_lo + (i - r * nc);
             float s = 0.0f;
-            for (int j = 0; j < H; ++j) s = fmaf(b.dZ1s[r * AS + j], b.W1s[j * LD1 + c], s);
+            for (int j = 0; j < H; ++j) s = fmaf(b.dZ1s[r * as + j], b.W1s[j * LD1 + c], s);
             dX[(size_t)(r0 + r) * ldx + c] = s;
         }
     }
@@ -401,6 +454,10 @@ __device__ __forceinline__ void backward(int in, int H, int out, int r0, int mc,
 
 // Writes the accumulated gradient in the parameter layout of W (global).
 __device__ __forceinline__ void store_grads(float* G, int in, int H, int out, const Buf& b) {
+    if (!b.gsm) {  // the accumulators were the output
+        __syncthreads();
+        return;
+    }
     float* gW1 = G;
     float* gb1 = gW1 + H * in;
     float* gW2 = gb1 + H;
@@ -413,7 +470,7 @@ __device__ __forceinline__ void store_grads(float* G, int in, int H, int out, co
     }
     for (int i = threadIdx.x; i < H * H; i += LT) {
         const int r = i / H, c = i - r * H;
-        gW2[i] = b.gW2[r * HP + c];
+        gW2[i] = b.gW2[r * b.g2 + c];
     }
     for (int i = threadIdx.x; i < H; i += LT) {
         gb1[i] = b.gb1[i];
@@ -421,7 +478,7 @@ __device__ __forceinline__ void store_grads(float* G, int in, int H, int out, co
     }
     for (int i = threadIdx.x; i < out * H; i += LT) {
         const int o = i / H, j = i - o * H;
-        gW3[i] = b.gW3[o * HP + j];
+        gW3[i] = b.gW3[o * b.g3 + j];
     }
     if (threadIdx.x < out) gb3[threadIdx.x] = b.gb3[threadIdx.x];
     __syncthreads();

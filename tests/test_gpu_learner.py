@@ -83,7 +83,7 @@ def make_run(q, n_env=3, cap=64, hidden=32, batch=64, cluster=1, layout=0, steps
 
 @pytest.mark.parametrize("cluster,layout,hidden,batch", [(1, 0, 32, 64), (2, 0, 64, 64),
                                                          (4, 1, 32, 128), (1, 2, 16, 32),
-                                                         (8, 0, 128, 256)])
+                                                         (8, 0, 128, 256), (1, 0, 128, 128)])
 def test_ac_update_parity(gpu, cluster, layout, hidden, batch):
     q = gpu
     d, h, a, hp = make_run(q, hidden=hidden, batch=batch, cluster=cluster, layout=layout)
