@@ -131,6 +131,24 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------------- multi-GPU
+def rank_workload(W, rank):
+    """The c2 env set of one rank (weak scaling): every rank simulates its own 65,536 envs
+    with its own random streams (run id = rank), so no data crosses ranks."""
+    d = W.config("c2")
+    d.update(learning_starts=0, seed=0, run_id=rank)
+    return d
+
+
+def max_over_ranks(torch, dist, x, world, device):
+    """Largest of a per-rank time over all ranks -- the only collective of the bench."""
+    if world <= 1:
+        return float(x)
+    tt = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def flush_l2(buf):
     buf.zero_()
 
@@ -482,8 +500,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     q.load()
     n, horizon = args.envs, args.horizon
-    d = W.config("c2")
-    d.update(learning_starts=0, seed=0, run_id=rank)
+    d = rank_workload(W, rank)
     veh = q.make_params(d)
     cfg = q.make_config(d, n, horizon, reward=W.REWARD, sigma_e=0.1)
     h = q.qsim_create(cfg, veh)
@@ -522,11 +539,8 @@ def main():
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     packed_used = q.qsim_rollout_engine(h, -2)
     parts_used = q.qsim_rollout_schedule(h, -1, -1)
-    t_dev = sum(ms) / 1e3
+    t_dev = max_over_ranks(torch, dist, sum(ms) / 1e3, world, "cuda")
     if world > 1:
-        tt = torch.tensor([t_dev], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
         dist.barrier()
     env_steps = n * horizon * args.steps * world
     value = env_steps / t_dev
@@ -542,6 +556,8 @@ def main():
     host_stats = torch.empty(3, info["ld"], dtype=torch.int32).pin_memory()
     stats_dev = torch.stack([info["n_done"], info["len_sum"], info["ret_sum"].view(torch.int32)])
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     w0 = time.perf_counter()
     for k in range(args.steps):
         dev_actor.copy_(host_actor, non_blocking=True)
@@ -549,8 +565,8 @@ def main():
         stats_dev = torch.stack([info["n_done"], info["len_sum"], info["ret_sum"].view(torch.int32)])
         host_stats.copy_(stats_dev, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - w0
-    e2e = {"value": env_steps / max(e2e_t, 1e-9) if world == 1 else None, "unit": "env-steps/s",
+    e2e_t = max_over_ranks(torch, dist, time.perf_counter() - w0, world, "cuda")
+    e2e = {"value": env_steps / max(e2e_t, 1e-9), "unit": "env-steps/s",
            "h2d_bytes_per_step": host_actor.numel() * 4,
            "d2h_bytes_per_step": host_stats.numel() * 4}
 
