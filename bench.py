@@ -431,6 +431,15 @@ def cpu_baseline(n_envs=4096, horizon=1000, chunk=50):
 
 
 # ------------------------------------------------------------------------------ main arms
+def arm_config(n, horizon, **extra):
+    """The workload the headline is quoted on (both arms report it)."""
+    c = {"workload": f"c2 batched rollout: {n} domain-randomised quadrotors x {horizon} steps per "
+                     f"bench step, actor 82-64-64-4, replay {n}x{horizon} in HBM",
+         "envs_per_gpu": n, "steps_per_bench_step": horizon}
+    c.update(extra)
+    return c
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -460,10 +469,11 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "c2 rollout sample: 4096 domain-randomised envs x 40 steps "
-                       "per bench step (of 65,536 x 1,000)", "envs": n, "steps_per_bench_step": T},
+            "config": arm_config(args.envs, args.horizon),
             "cpu_baseline": {"value": v, "unit": "env-steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{n} envs x {T} steps per bench step, {cores} threads"},
+                             "sample": f"{n} of the {args.envs} envs x {T} of the {args.horizon} steps "
+                                       f"per bench step (a bounded sample of the workload; "
+                                       f"env-steps/s is per env-step), {cores} threads"},
             "e2e": {"value": v, "unit": "env-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -624,14 +634,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_dev / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"c2 batched rollout: {n} domain-randomised quadrotors x "
-                                   f"{horizon} steps per bench step, actor 82-64-64-4, "
-                                   f"replay {n}x{horizon} in HBM",
-                       "envs_per_gpu": n, "steps_per_bench_step": horizon,
-                       "l2": "flushed before every timed step (512 MB write)",
-                       "rollout_warps_per_block": tuned,
-                       "rollout_engine": packed_used,
-                       "rollout_partitions": parts_used},
+            "config": arm_config(n, horizon, l2="flushed before every timed step (512 MB write)",
+                                 rollout_warps_per_block=tuned, rollout_engine=packed_used,
+                                 rollout_partitions=parts_used),
             "roofline": roofline,
             "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
             "cpu_baseline": cpu, "step_ms": ms, "wall_s": wall,
