@@ -76,7 +76,12 @@ constexpr int OFF_BAR = OFF_B3 + 16;  // per tile: A1 ready, D1 full, A2 ready, 
 constexpr int OFF_TSLOT = OFF_BAR + 32 * TILES;
 constexpr int OFF_ABORT = OFF_TSLOT + 16;
 constexpr int OFF_UNIT = OFF_ABORT + 16;
-constexpr int SMEM = OFF_UNIT + 16;
+// precomputed B descriptors of layer 1 (hi, lo): [0..1] the observation K-steps, [2 + b0]
+// the lag window starting at block b0 (b0 = 0..15); layer 2 per tile: (A hi, A lo, B hi,
+// B lo) for each of its 4 K-steps
+constexpr int OFF_DESC = (OFF_UNIT + 16 + 7) & ~7;
+constexpr int N_DESC1 = 2 * (2 + 16), N_DESC2 = TILES * 4 * 4;
+constexpr int SMEM = OFF_DESC + 8 * (N_DESC1 + N_DESC2);
 static_assert(SMEM <= 227 * 1024, "tensor-core rollout: shared memory");
 static_assert(SZ_W1 % 128 == 0 && OFF_A2 % 128 == 0 && SZ_A2 % 128 == 0, "alignment");
 
@@ -284,6 +289,35 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
             *abort_flag = 0;
         }
+        if (tid < 2 + 16) {
+            // layer-1 B descriptors: observation K-steps (copy E) and the 16 lag windows
+            uint64_t* d1 = reinterpret_cast<uint64_t*>(smb + OFF_DESC);
+            const uint32_t sW1 = smem_addr(W1s);
+            uint32_t wbase;
+            int kk;
+            if (tid < 2) {
+                wbase = sW1;
+                kk = 16 * tid;
+            } else {
+                const int b0 = tid - 2;
+                wbase = sW1 + (uint32_t)((b0 & 1) * 2 * SZ_W1);
+                kk = (b0 & 1) ? 36 + 4 * b0 : 32 + 4 * b0;
+            }
+            d1[2 * tid] = sdesc(wbase + (uint32_t)(kk / 8) * 128u, KC1);
+            d1[2 * tid + 1] = sdesc(wbase + (uint32_t)SZ_W1 + (uint32_t)(kk / 8) * 128u, KC1);
+        } else if (tid >= 32 && tid < 32 + TILES * 4) {
+            // layer-2 descriptors of tile k, K-step j
+            const int k = (tid - 32) >> 2, j = (tid - 32) & 3;
+            uint64_t* d2 = reinterpret_cast<uint64_t*>(smb + OFF_DESC) + N_DESC1 + 16 * k + 4 * j;
+            const uint32_t ko = (uint32_t)(2 * j) * 128u;
+            const uint32_t a_hi = smem_addr(smb + OFF_A2 + (2 * k) * SZ_A2);
+            const uint32_t a_lo = smem_addr(smb + OFF_A2 + (2 * k + 1) * SZ_A2);
+            const uint32_t w2 = smem_addr(W2s);
+            d2[0] = sdesc(a_hi + ko, KC2);
+            d2[1] = sdesc(a_lo + ko, KC2);
+            d2[2] = sdesc(w2 + ko, KC2);
+            d2[3] = sdesc(w2 + (uint32_t)SZ_W2 + ko, KC2);
+        }
         if (warp == NCW) {
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                          :: "r"(smem_addr(tslot)), "r"(T_ALLOC) : "memory");
@@ -337,8 +371,9 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
         const int64_t headu = head0 + (int64_t)uk * chunk;
         if (mma_warp) {
             // ================= MMA warp of this tile: lane 0 issues, the warp follows the waits
-            const uint32_t sW1 = smem_addr(W1s), sW2 = smem_addr(W2s);
-            const uint32_t sA2hi = smem_addr(A2hi), sA2lo = smem_addr(A2lo);
+            // (descriptors from the table built at setup: the issue loops are MMAs only)
+            const uint64_t* d1 = reinterpret_cast<const uint64_t*>(smb + OFF_DESC);
+            const uint64_t* d2 = d1 + N_DESC1 + 16 * tile;
 #pragma unroll 1
             for (int tt = 0; tt < Tu; ++tt) {
                 const uint32_t t = t0u + (uint32_t)tt;
@@ -346,22 +381,12 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 if (!warp_wait(bar_a1, ph, abort_flag, p.status)) break;
                 fence_after();
                 if (lane == 0) {
-#pragma unroll 1
+#pragma unroll
                     for (int j = 0; j < KA / 16; ++j) {
-                        // W1 copy and first element of this K-step's 16-element window
-                        uint32_t wbase;
-                        int kk;
-                        if (j < 2) {
-                            wbase = sW1;
-                            kk = 16 * j;
-                        } else {
-                            const int i0 = (int)((t - 1u - (uint32_t)(4 * (j - 2))) & 15u) + 1;  // lag of slot 4(j-2)
-                            const int b0 = 16 - i0;
-                            wbase = sW1 + (uint32_t)((b0 & 1) * 2 * SZ_W1);
-                            kk = (b0 & 1) ? 36 + 4 * b0 : 32 + 4 * b0;
-                        }
-                        const uint64_t bhi = sdesc(wbase + (uint32_t)(kk / 8) * 128u, KC1);
-                        const uint64_t blo = sdesc(wbase + (uint32_t)SZ_W1 + (uint32_t)(kk / 8) * 128u, KC1);
+                        // B window of K-step j: the observation block, or the lag window whose
+                        // first block b0 holds the lag of ring slot 4(j-2)
+                        const int e = j < 2 ? j : 2 + 15 - (int)((t - 1u - (uint32_t)(4 * (j - 2))) & 15u);
+                        const uint64_t bhi = d1[2 * e], blo = d1[2 * e + 1];
                         mma_tt(tmem + T_D, tmem + T_AHI + 8 * j, bhi, j > 0);
                         mma_tt(tmem + T_D, tmem + T_AHI + 8 * j, blo, 1);
                         mma_tt(tmem + T_D, tmem + T_ALO + 8 * j, bhi, 1);
@@ -373,11 +398,9 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 if (!warp_wait(bar_a2, ph, abort_flag, p.status)) break;
                 fence_after();
                 if (lane == 0) {
-#pragma unroll 1
+#pragma unroll
                     for (int j = 0; j < H / 16; ++j) {
-                        const uint32_t ko = (uint32_t)(2 * j) * 128u;
-                        const uint64_t ahi = sdesc(sA2hi + ko, KC2), alo = sdesc(sA2lo + ko, KC2);
-                        const uint64_t bhi = sdesc(sW2 + ko, KC2), blo = sdesc(sW2 + (uint32_t)SZ_W2 + ko, KC2);
+                        const uint64_t ahi = d2[4 * j], alo = d2[4 * j + 1], bhi = d2[4 * j + 2], blo = d2[4 * j + 3];
                         mma_ss(tmem + T_D, ahi, bhi, j > 0);
                         mma_ss(tmem + T_D, ahi, blo, 1);
                         mma_ss(tmem + T_D, alo, bhi, 1);
@@ -534,8 +557,12 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                             float h0, h1;
                             f2unpack(z2, h0, h1);
                             const unsigned long long hh = f2pack(fmaxf(h0, 0.0f), fmaxf(h1, 0.0f));
-#pragma unroll
-                            for (int o = 0; o < 4; ++o) acc[o] = f2fma(w3p[4 * i + o], hh, acc[o]);
+                            const ulonglong2 w01 = reinterpret_cast<const ulonglong2*>(w3p)[2 * i];
+                            const ulonglong2 w23 = reinterpret_cast<const ulonglong2*>(w3p)[2 * i + 1];
+                            acc[0] = f2fma(w01.x, hh, acc[0]);
+                            acc[1] = f2fma(w01.y, hh, acc[1]);
+                            acc[2] = f2fma(w23.x, hh, acc[2]);
+                            acc[3] = f2fma(w23.y, hh, acc[3]);
                         }
                     }
                     float pp[4];
