@@ -45,7 +45,7 @@ BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, fl
 # Set to None whenever the kernel changes until it is captured again.
 NCU_DRAM_BYTES_PER_ENV_STEP = (46.710016e6 + 289.403648e6) / (32768 * 100)
 # same for the tensor-core kernel k_rollout_tc (profiles/k_rollout_tc_c2_65536x1000.md)
-NCU_DRAM_BYTES_PER_ENV_STEP_TC = (35.362048e6 + 98.369536e6) / (65536 * 20)
+NCU_DRAM_BYTES_PER_ENV_STEP_TC = (35.502592e6 + 98.719744e6) / (65536 * 20)
 
 
 def parse():

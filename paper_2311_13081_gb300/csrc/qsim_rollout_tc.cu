@@ -68,8 +68,7 @@ constexpr int SZ_A2 = TILE * H * 2;
 constexpr int OFF_W1 = 0;                   // [E hi, E lo, O hi, O lo]
 constexpr int OFF_W2 = OFF_W1 + 4 * SZ_W1;  // [hi, lo]
 constexpr int OFF_A2 = OFF_W2 + 2 * SZ_W2;  // tile k: hi at + 2k SZ_A2, lo at + (2k+1) SZ_A2
-constexpr int OFF_B1 = OFF_A2 + TILES * 2 * SZ_A2;
-constexpr int OFF_B2 = OFF_B1 + 4 * H;
+constexpr int OFF_B2 = OFF_A2 + TILES * 2 * SZ_A2;  // b1 is a column of W1
 constexpr int OFF_W3 = OFF_B2 + 4 * H;  // [H/2][4] float2: (W3[o][2i], W3[o][2i+1])
 constexpr int OFF_B3 = OFF_W3 + 16 * H;
 constexpr int OFF_BAR = OFF_B3 + 16;  // per tile: A1 ready, D1 full, A2 ready, D2 full
@@ -122,19 +121,6 @@ __device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint3
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar));
-}
-
-// Bounded wait for the completion of phase `parity` of an mbarrier; gives up early once the
-// CTA's abort flag is set.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    for (int i = 0; i < WAIT_LIMIT; ++i) {
-        uint32_t done;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-        if (done) return true;
-        if ((i & 255) == 255 && *abort_flag) return false;
-    }
-    return false;
 }
 
 // The whole warp waits (try_wait suspends it in hardware between polls), kept uniform by a
@@ -221,7 +207,6 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
     extern __shared__ __align__(1024) unsigned char smb[];
     __half* W1s = reinterpret_cast<__half*>(smb + OFF_W1);
     __half* W2s = reinterpret_cast<__half*>(smb + OFF_W2);
-    float* sB1 = reinterpret_cast<float*>(smb + OFF_B1);
     float* sB2 = reinterpret_cast<float*>(smb + OFF_B2);
     const float4* sW3 = reinterpret_cast<const float4*>(smb + OFF_W3);  // [H/2][2]: outputs (0,1), (2,3)
     float* sB3 = reinterpret_cast<float*>(smb + OFF_B3);
@@ -270,7 +255,6 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
             W2s[H * H + cano16(n, k, KC2)] = __float2half_rn(w - __half2float(hi));
         }
         for (int i = tid; i < H; i += NT) {
-            sB1[i] = gb1[i];
             sB2[i] = gb2[i];
             if (i < H / 2)
 #pragma unroll
