@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--learner-steps", type=int, default=20)
     ap.add_argument("--only-diff", action="store_true",
                     help="only the differentiation sample (c3 shape), for profiling")
+    ap.add_argument("--only-track", action="store_true",
+                    help="only the Lissajous tracking sample, for profiling")
     ap.add_argument("--warps", type=int, default=0,
                     help="pin the rollout's warps per block and skip the autotuner (profiling)")
     ap.add_argument("--parts", type=int, default=1, help="with --warps: env partitions")
@@ -227,6 +230,61 @@ def measure_dynamics(torch, q, veh):
                     "tflops": n * steps * FLOP_DYN / (ms * 1e-3) / 1e12,
                     "finite": bool(torch.isfinite(out[:, :n]).all())}
     return res
+
+
+def measure_track(torch, q, W, fp32_peak, n=65536, steps=1000, hidden=64):
+    """Simulated Lissajous tracking (Sec. V): every env flies the deterministic actor for
+    `steps` steps (10 s) along the figure-eight, cycle times 15, 5.5 and 3.5 s over the
+    envs, domain-randomised vehicles.  The actor is random (PyTorch-style init) with its
+    output layer scaled down around the hover action, so flights last a while; no trained
+    weights exist here, so the errors say nothing about the paper's controller."""
+    d = W.config("c2")
+    cfg = q.make_config(d, n, 0, reward=W.REWARD, sigma_e=0.0)
+    h = q.qsim_create(cfg, q.make_params(d))
+    try:
+        ld = q.qsim_info_get(h)["ld"]
+        g = torch.Generator().manual_seed(11)
+        da = 18 + 4 * d["n_hist"]
+        parts = []
+        for fan_in, shape in ((da, (hidden, da)), (da, (hidden,)), (hidden, (hidden, hidden)),
+                              (hidden, (hidden,)), (hidden, (4, hidden))):
+            b = fan_in ** -0.5
+            parts.append((torch.rand(shape, generator=g) * 2 - 1).mul(b).flatten())
+        parts[-1] *= 0.05
+        parts.append(torch.full((4,), math.atanh(W.hover_action())))
+        actor = torch.cat(parts).float().cuda()
+        per = torch.tensor([(15.0, 5.5, 3.5)[i % 3] for i in range(ld)], device="cuda")
+        sq = torch.empty((2, ld), dtype=torch.float64, device="cuda")
+        ok = torch.empty(ld, dtype=torch.int32, device="cuda")
+        q.qsim_track(h, actor, hidden, 100, per, sq, ok)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record()
+        for _ in range(reps):
+            q.qsim_track(h, actor, hidden, steps, per, sq, ok)
+        e1.record()
+        e1.synchronize()
+        q.qsim_sync(h)
+        ms = e0.elapsed_time(e1) / reps
+        okc = ok[:n].double().cpu()
+        sqc = sq[:, :n].cpu()
+        res = {"workload": f"{n} envs x {steps} steps, cycle times 15 / 5.5 / 3.5 s",
+               "env_steps_per_s": n * steps / (ms * 1e-3), "ms": ms,
+               "fp32_tflops": n * steps * (FLOP_ACTOR(da, hidden) + FLOP_DYN + FLOP_MISC)
+               / (ms * 1e-3) / 1e12, "fp32_peak": fp32_peak, "kernel": "k_rollout<64, 4, 1, 1>"}
+        for j, T in enumerate((15.0, 5.5, 3.5)):
+            sel = torch.arange(n) % 3 == j
+            k = okc[sel]
+            flown = k > 0
+            rmse = torch.sqrt(sqc[0, sel][flown] / k[flown])
+            res[f"T{T:g}"] = {"mean_steps_completed": float(k.mean()),
+                              "flights_completed": float((k == steps).double().mean()),
+                              "median_rmse_m": float(rmse.median()) if flown.any() else None}
+        res["fp32_frac"] = res["fp32_tflops"] / fp32_peak
+        return res
+    finally:
+        q.qsim_destroy(h)
 
 
 def measure_recalc(torch, q, h, n, horizon, hbm):
@@ -496,6 +554,12 @@ def main():
         q.load()
         print(json.dumps({"differentiation_c3": measure_diff(torch, q, W)}))
         return
+    if args.only_track:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        q.load()
+        fp32_peak = device_peaks(torch, q)[2]
+        print(json.dumps({"lissajous_tracking": measure_track(torch, q, W, fp32_peak)}))
+        return
     if args.only_learner:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         q.load()
@@ -593,6 +657,7 @@ def main():
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_extras:
         extras["dynamics_only"] = measure_dynamics(torch, q, veh)
+        extras["lissajous_tracking"] = measure_track(torch, q, W, fp32_peak)
         extras["learner_batched"] = measure_training(torch, q, W)
         extras["learner_single_run_c1"] = measure_c1(torch, q, W)
         extras["differentiation_c3"] = measure_diff(torch, q, W)

@@ -201,10 +201,33 @@ qsim_status qsim_step(qsim_handle* h, const float* actions, float* obs_a, float*
  * layout W1[h][in] b1 W2[h][h] b2 W3[4][h] b3, device) with Gaussian exploration of
  * std-dev sigma_e (sigma_e < 0: the handle's current value) or uniform warm-up actions
  * while t < learning_starts, then RK4 dynamics, reward, termination, reset and the
- * transition write.  hidden must be 64 for the warp-tiled kernel; other widths run on
- * the generic tile path. */
+ * transition write.  hidden is 32, 64 or 128 (every width runs on the SIMT kernel; 64
+ * also on the tensor-core kernel, see qsim_rollout_engine). */
 qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t hidden, int32_t n_steps,
                          float sigma_e, void* stream);
+
+/* Simulated trajectory tracking (Sec. V "Trajectory tracking"): every env of the set flies
+ * the deterministic actor (no exploration, no observation noise) along the figure-eight
+ * target p*(t) = (A cos(2 pi t / T), (A / 2) sin(4 pi t / T), z0) for n_steps steps of dt,
+ * with its own domain-randomised parameters and disturbances (the set's current ones).  As
+ * Sec. IV prescribes for set-points, the actor observes its position and velocity offset
+ * by the target's p*(t) and velocity v*(t) (the time derivative of p*), each component
+ * clipped to +-clip_p (m) and +-clip_v (m/s).  Start: on the target with its velocity, level, not rotating, motors at
+ * the env's hover speed sqrt(m g / (4 k_f)) clipped to the RPM range, empty action history.
+ * After each step the error e = p - p*(t + dt) is accumulated; a non-finite state or any
+ * |e_i| > term_pos (the config's termination box) ends that env's flight, whose error is
+ * not counted.  The env set itself (states, counters, replay) is not modified.
+ *   actor     device, layout as in qsim_rollout; hidden 32, 64 or 128 (SIMT kernel)
+ *   period    device float [ld]: cycle time T > 0 of each env, s (T <= 0, infinite or NaN
+ *             flies no step)
+ *   sq_err    device double [2][ld] out: sum of |e|^2 and sum of e_x^2 + e_y^2 over the
+ *             completed steps; RMSE = sqrt(sq_err / steps_ok) (the paper's e and e_xy)
+ *   steps_ok  device int32 [ld] out: steps completed before the flight ended (<= n_steps)
+ * Pointers must be 4-byte aligned (sq_err 8-byte); amplitude, z0 and the clips finite,
+ * clips >= 0; otherwise QSIM_EINVAL. */
+qsim_status qsim_track(qsim_handle* h, const float* actor, int32_t hidden, int32_t n_steps,
+                       const float* period, float amplitude, float z0, float clip_p,
+                       float clip_v, double* sq_err, int32_t* steps_ok, void* stream);
 
 /* Warps per block for the rollout kernel (0 = autotuned choice).  Returns the value in
  * effect. */

@@ -114,6 +114,13 @@ class Diff(C.Structure):
                 ("act_out", _P)]
 
 
+class Track(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_steps", C.c_int32), ("hidden", C.c_int32),
+                ("pad_", C.c_int32), ("prm", _P), ("dist", _P), ("period", _P), ("actor", _P),
+                ("amp", C.c_double), ("z0", C.c_double), ("clip_p", C.c_double),
+                ("clip_v", C.c_double), ("sq_err", _P), ("steps_ok", _P), ("traj", _P)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -128,7 +135,7 @@ def lib():
         L.or_reward.restype = C.c_double
         L.or_reward.argtypes = [C.POINTER(RewardC), _P, _P]
         for fn in ("or_net_size", "or_actor_in", "or_critic_in", "or_rollout", "or_td3_update",
-                   "or_recalc_rewards", "or_diff_run"):
+                   "or_recalc_rewards", "or_diff_run", "or_track_run"):
             getattr(L, fn).restype = C.c_int
         L.or_net_size.argtypes = [C.c_int, C.c_int, C.c_int]
         L.or_actor_in.argtypes = [C.POINTER(Cfg)]
@@ -152,6 +159,9 @@ def lib():
         L.or_recalc_rewards.argtypes = [C.POINTER(RewardC), C.POINTER(Buffer), _P]
         L.or_curriculum.argtypes = [_P, _P, _P, C.c_int]
         L.or_diff_run.argtypes = [C.POINTER(Cfg), C.POINTER(Diff)]
+        L.or_lissajous.restype = None
+        L.or_lissajous.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, _P, _P]
+        L.or_track_run.argtypes = [C.POINTER(Cfg), C.POINTER(Track), C.c_int]
         L.or_philox.argtypes = [_P, _P, _P]
     return _lib
 
@@ -441,4 +451,35 @@ def diff_run(cfg, s0, prm, H, weights, mode=0, actions=None, actor=None, hidden=
              int(hidden), 0, _p(out["loss"]), _p(out["g_actions"]), _p(out["g_actor"]),
              _p(out["g_prm"]), _p(out["traj"]), _p(out["act_out"]))
     lib().or_diff_run(C.byref(c), C.byref(d))
+    return out
+
+
+# ---------------------------------------------------------------------------------------
+# Simulated trajectory tracking (Sec. V)
+# ---------------------------------------------------------------------------------------
+def lissajous(t: float, T: float, A: float = 1.0, z0: float = 0.0):
+    """Figure-eight target of Sec. V and its velocity at time t (s), cycle time T (s)."""
+    p, v = np.zeros(3), np.zeros(3)
+    lib().or_lissajous(float(t), float(T), float(A), float(z0), _p(p), _p(v))
+    return p, v
+
+
+def track(cfg, prm, dist, period, actor, hidden, n_steps, amp=1.0, z0=0.0, clip_p=0.2,
+          clip_v=1.0, traj=False, n_threads=1) -> dict:
+    """Fly n envs (params ``prm`` [n][8], disturbances ``dist`` [n][6]) along the target.
+
+    Returns sq_err [n][2] (sums of |e|^2 and e_x^2 + e_y^2 over the completed steps),
+    steps_ok [n] and, if requested, the states traj [n][n_steps + 1][17]."""
+    c = make_cfg(cfg)
+    prm = _f64(prm)
+    n = prm.shape[0]
+    dist = _f64(dist, (n, NDIST))
+    per = _f64(period, (n,))
+    aw = _f64(actor)
+    out = dict(sq_err=np.zeros((n, 2)), steps_ok=np.zeros(n, np.int32),
+               traj=np.full((n, n_steps + 1, NS), np.nan) if traj else None)
+    J = Track(n, int(n_steps), int(hidden), 0, _p(prm), _p(dist), _p(per), _p(aw), float(amp),
+              float(z0), float(clip_p), float(clip_v), _p(out["sq_err"]), _p(out["steps_ok"]),
+              _p(out["traj"]))
+    lib().or_track_run(C.byref(c), C.byref(J), int(n_threads))
     return out

@@ -536,6 +536,118 @@ int or_rollout(const or_cfg* c, const or_reward_c* C, or_envs* e, const double* 
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Trajectory tracking in simulation (Sec. V "Trajectory tracking").  The trained        */
+/* position controller is steered along a moving target by offsetting its observation:  */
+/* Sec. IV reaches any position / velocity set-point by shifting the current position   */
+/* and velocity, clipped so that the errors stay within those seen in training.  The     */
+/* target of Sec. V is the figure-eight Lissajous curve                                  */
+/*   p*(t) = (A cos(2 pi t / T), (A / 2) sin(4 pi t / T), z0)                            */
+/* (A = 1 m in the paper); v*(t) is its time derivative.                                 */
+/* ------------------------------------------------------------------------------------ */
+void or_lissajous(double t, double T, double A, double z0, double* p, double* v) {
+    const double w = 2.0 * M_PI / T;
+    p[0] = A * cos(w * t);
+    p[1] = 0.5 * A * sin(2.0 * w * t);
+    p[2] = z0;
+    v[0] = -A * w * sin(w * t);
+    v[1] = A * w * cos(2.0 * w * t);
+    v[2] = 0.0;
+}
+
+typedef struct track_job {
+    const or_cfg* c;
+    const or_track* J;
+    int k0, k1;
+} track_job;
+
+static void track_env(const or_cfg* c, const or_track* J, int k) {
+    const double* prm = J->prm + OR_NPRM * k;
+    const double* dist = J->dist + OR_NDIST * k;
+    const double T = J->period[k];
+    J->sq_err[2 * k] = 0.0;
+    J->sq_err[2 * k + 1] = 0.0;
+    J->steps_ok[k] = 0;
+    if (!(T > 0.0) || !isfinite(T)) return; /* no target: no flight */
+    or_net actor = {or_actor_in(c), J->hidden, 4};
+    double* h1 = (double*)malloc(sizeof(double) * (size_t)J->hidden * 2);
+    double* h2 = h1 + J->hidden;
+    double s[OR_NS], pr[3], vr[3], hist[4 * OR_HMAX];
+    memset(s, 0, sizeof(s));
+    memset(hist, 0, sizeof(hist));
+    /* start (reading): on the target with its velocity, level, not rotating, motors at
+     * the hover speed of this env's mass and thrust coefficient, no action history */
+    or_lissajous(0.0, T, J->amp, J->z0, pr, vr);
+    for (int i = 0; i < 3; ++i) { s[i] = pr[i]; s[7 + i] = vr[i]; }
+    s[3] = 1.0;
+    double hover = clampd(sqrt(prm[0] * c->g / (4.0 * prm[4])), c->rpm_min, c->rpm_max);
+    for (int i = 0; i < 4; ++i) s[13 + i] = hover;
+    if (J->traj) memcpy(J->traj + (size_t)k * (J->n_steps + 1) * OR_NS, s, sizeof(s));
+    double e3 = 0.0, exy = 0.0;
+    int ok = 0;
+    for (int kk = 0; kk < J->n_steps; ++kk) {
+        /* shifted, clipped observation; no observation noise, no exploration (reading) */
+        or_lissajous(kk * c->dt, T, J->amp, J->z0, pr, vr);
+        double sh[OR_NS], o[18 + 4 * OR_HMAX], mu[4], a[4], u[4], s2[OR_NS];
+        memcpy(sh, s, sizeof(sh));
+        for (int i = 0; i < 3; ++i) {
+            sh[i] = clampd(s[i] - pr[i], -J->clip_p, J->clip_p);
+            sh[7 + i] = clampd(s[7 + i] - vr[i], -J->clip_v, J->clip_v);
+        }
+        or_obs_actor(c, sh, hist, NULL, o);
+        or_mlp_forward(&actor, J->actor, o, h1, h2, mu, 1);
+        for (int i = 0; i < 4; ++i) {
+            a[i] = clampd(mu[i], -1.0, 1.0);
+            u[i] = c->rpm_min + 0.5 * (a[i] + 1.0) * (c->rpm_max - c->rpm_min);
+        }
+        or_rk4(c, s, u, prm, dist, c->dt, c->renorm_q, s2);
+        /* tracking error against the target at the new time; a non-finite state or an
+         * error outside the training termination box ends the flight (reading) */
+        or_lissajous((kk + 1) * c->dt, T, J->amp, J->z0, pr, vr);
+        double e[3] = {s2[0] - pr[0], s2[1] - pr[1], s2[2] - pr[2]};
+        if (J->traj) memcpy(J->traj + ((size_t)k * (J->n_steps + 1) + kk + 1) * OR_NS, s2, sizeof(s2));
+        if (!finite_state(s2) || fabs(e[0]) > c->term_pos || fabs(e[1]) > c->term_pos ||
+            fabs(e[2]) > c->term_pos)
+            break;
+        e3 += e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+        exy += e[0] * e[0] + e[1] * e[1];
+        ok += 1;
+        memmove(hist + 4, hist, sizeof(double) * 4 * (OR_HMAX - 1));
+        memcpy(hist, a, sizeof(double) * 4);
+        memcpy(s, s2, sizeof(s));
+    }
+    J->sq_err[2 * k] = e3;
+    J->sq_err[2 * k + 1] = exy;
+    J->steps_ok[k] = ok;
+    free(h1);
+}
+
+static void* track_thread(void* arg) {
+    track_job* t = (track_job*)arg;
+    for (int k = t->k0; k < t->k1; ++k) track_env(t->c, t->J, k);
+    return NULL;
+}
+
+int or_track_run(const or_cfg* c, const or_track* J, int n_threads) {
+    if (n_threads < 1) n_threads = 1;
+    if (n_threads > J->n) n_threads = J->n > 0 ? J->n : 1;
+    track_job* jobs = (track_job*)calloc((size_t)n_threads, sizeof(track_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    for (int i = 0; i < n_threads; ++i) {
+        track_job t = {c, J, (int)((int64_t)J->n * i / n_threads),
+                       (int)((int64_t)J->n * (i + 1) / n_threads)};
+        jobs[i] = t;
+    }
+    if (n_threads == 1) {
+        track_thread(&jobs[0]);
+    } else {
+        for (int i = 0; i < n_threads; ++i) pthread_create(&th[i], NULL, track_thread, &jobs[i]);
+        for (int i = 0; i < n_threads; ++i) pthread_join(th[i], NULL);
+    }
+    free(jobs); free(th);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* TD3 update with an asymmetric (privileged) critic (Sec. IV; TD3).                    */
 /* ------------------------------------------------------------------------------------ */
 static int64_t pmod(int64_t a, int64_t m) { int64_t r = a % m; return r < 0 ? r + m : r; }

@@ -126,6 +126,21 @@ typedef struct or_diff {
     double* act_out;        /* [n][H][4] (may be NULL) */
 } or_diff;
 
+/* Simulated trajectory tracking (Sec. V): n envs with their own parameters follow the
+ * Lissajous target of cycle time period[k] for n_steps steps. */
+typedef struct or_track {
+    int32_t n, n_steps, hidden, pad_;
+    const double* prm;      /* [n][8] */
+    const double* dist;     /* [n][6] */
+    const double* period;   /* [n] cycle time T, s */
+    const double* actor;    /* actor params */
+    double amp, z0, clip_p, clip_v;
+    double* sq_err;         /* [n][2]: sum |e|^2, sum e_x^2 + e_y^2 over completed steps */
+    int32_t* steps_ok;      /* [n] steps completed before the flight ended */
+    double* traj;           /* [n][n_steps + 1][17] (may be NULL): start, then the state after
+                               each step up to the one that ended the flight */
+} or_track;
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -164,6 +179,8 @@ int or_td3_update(const or_cfg* c, or_td3* L, const or_buffer* b, or_td3_diag* d
 int or_recalc_rewards(const or_reward_c* C, or_buffer* b, const double* cur_state);
 void or_curriculum(const double* factor, const double* target, double* C, int n);
 int or_diff_run(const or_cfg* c, or_diff* d);
+void or_lissajous(double t, double T, double A, double z0, double* p, double* v);
+int or_track_run(const or_cfg* c, const or_track* J, int n_threads);
 #ifdef __cplusplus
 }
 #endif

@@ -116,6 +116,8 @@ _SIGS = {
     "qsim_observe": (C.c_int, [P, P, P, P]),
     "qsim_step": (C.c_int, [P, P, P, P, P, P, P, P]),
     "qsim_rollout": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_float, P]),
+    "qsim_track": (C.c_int, [P, P, C.c_int32, C.c_int32, P, C.c_float, C.c_float, C.c_float,
+                             C.c_float, P, P, P]),
     "qsim_rollout_tune": (C.c_int32, [P, C.c_int32]),
     "qsim_rollout_autotune": (C.c_int32, [P, P, C.c_int32, C.c_int32, P]),
     "qsim_rollout_schedule": (C.c_int32, [P, C.c_int32, C.c_int32]),
@@ -341,6 +343,14 @@ def qsim_step(h, actions, obs_a=None, obs_c=None, reward=None, terminated=None, 
 
 def qsim_rollout(h, actor, hidden, n_steps, sigma_e=-1.0, stream=None):
     _chk(_lib.qsim_rollout(h, _ptr(actor), hidden, n_steps, sigma_e, _stream(stream)))
+
+
+def qsim_track(h, actor, hidden, n_steps, period, sq_err, steps_ok, amplitude=1.0, z0=0.0,
+               clip_p=0.2, clip_v=1.0, stream=None):
+    """Lissajous tracking flight of every env (period float32 [ld], sq_err float64 [2][ld],
+    steps_ok int32 [ld]; device tensors)."""
+    _chk(_lib.qsim_track(h, _ptr(actor), hidden, n_steps, _ptr(period), amplitude, z0, clip_p,
+                         clip_v, _ptr(sq_err), _ptr(steps_ok), _stream(stream)))
 
 
 def qsim_rollout_tune(h, warps_per_block=0) -> int:

@@ -19,7 +19,13 @@
 // Shared memory: actor weights once per CTA + per warp an obs tile [82][32] and a hidden
 // tile [H][32].  Replay records go out as field-major streaming stores, 128 B per warp per
 // field.
+//
+// The same kernel, instantiated with TRACK = true, flies the deterministic actor along the
+// figure-eight target of Sec. V ("Trajectory tracking") instead: the observation's
+// position and velocity are offset by the target's and clipped, and the squared tracking
+// error is accumulated; there is no exploration, reward, replay write or reset.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 
 #include "qsim_internal.h"
@@ -52,12 +58,42 @@ __device__ __forceinline__ int wpos(int o) {
     return (r >> 2) * 32 + ty * 4 + (r & 3);
 }
 
-template <int H, int NW, bool PK>
+// Arguments of the tracking instantiation.
+struct TrackArgs {
+    const float* period;  // [ld] cycle time T of each env's target, s
+    float amp, z0;        // target amplitude A and height
+    float clip_p, clip_v; // observation offsets clipped to +-clip per component
+    double* sq_err;       // [2][ld] out: sums of |e|^2 and e_x^2 + e_y^2
+    int32_t* steps_ok;    // [ld] out: steps completed before the flight ended
+};
+
+// Figure-eight target of Sec. V at step k: p* = (A cos th, (A/2) sin 2 th, z0) with
+// th = 2 pi k dt / T, and its time derivative v*.  The cycle fraction k dt / T is formed in
+// double precision and reduced to [0, 1) before the single-precision sin / cos, so the
+// phase stays exact over long flights.
+__device__ __forceinline__ void lissajous(int k, float dt, float T, float A, float z0, float* pr,
+                                          float* vr) {
+    const double x = (double)k * (double)dt / (double)T;
+    const float f1 = (float)(x - floor(x));
+    const float f2 = (float)(2.0 * x - floor(2.0 * x));
+    float s1, c1, s2, c2;
+    sincospif(2.0f * f1, &s1, &c1);
+    sincospif(2.0f * f2, &s2, &c2);
+    const float aw = A * (6.283185307179586f / T);  // A * 2 pi / T
+    pr[0] = A * c1;
+    pr[1] = 0.5f * A * s2;
+    pr[2] = z0;
+    vr[0] = -aw * s1;
+    vr[1] = aw * c2;
+    vr[2] = 0.0f;
+}
+
+template <int H, int NW, bool PK, bool TRACK = false>
 __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
                                                      const float* __restrict__ actor, int T,
                                                      uint32_t t0, int64_t head0,
                                                      int64_t capacity, float sigma_in,
-                                                     int warp0, int warp_end) {
+                                                     int warp0, int warp_end, TrackArgs tr) {
     using L = RollLayout<H>;
     constexpr int OP = H / 8;  // outputs per lane
     constexpr int NQ = OP / 4; // float4 chunks per lane per weight row
@@ -114,6 +150,29 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
     for (int i = 0; i < 6; ++i) d[i] = p.dist[i * ld + g];
     Prm P = make_prm(p.prm[g], p.prm[ld + g], p.prm[2 * ld + g], p.prm[3 * ld + g],
                      p.prm[4 * ld + g], p.prm[5 * ld + g], p.prm[6 * ld + g]);
+    // tracking: start on the target with its velocity, level, not rotating, motors at this
+    // env's hover speed, empty action history
+    float Tp = 1.0f;
+    double e3 = 0.0, exy = 0.0;
+    int n_ok = 0;
+    bool alive = true;
+    if constexpr (TRACK) {
+        Tp = tr.period[g];
+        alive = Tp > 0.0f && isfinite(Tp);
+        float pr[3], vr[3];
+        lissajous(0, C.dt, alive ? Tp : 1.0f, tr.amp, tr.z0, pr, vr);
+        const float hover = clampf(sqrtf(P.m * C.veh.g / (4.0f * P.kf)), C.veh.rpm_min, C.veh.rpm_max);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            s[i] = pr[i];
+            s[7 + i] = vr[i];
+            s[10 + i] = 0.0f;
+        }
+        s[3] = 1.0f; s[4] = 0.0f; s[5] = 0.0f; s[6] = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s[13 + i] = hover;
+        if (!alive) Tp = 1.0f;
+    }
     uint32_t ep_index = p.ep_index[g], ep_step = p.ep_step[g];
     uint32_t n_done = p.n_done[g], len_sum = p.len_sum[g];
     float ep_ret = p.ep_ret[g], ret_sum = p.ret_sum[g];
@@ -122,6 +181,9 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
     for (int i = 0; i < 7; ++i) Cr[i] = p.rewardC[i];
     const float sigma = sigma_in >= 0.0f ? sigma_in : p.rewardC[7];
     const int nh = C.n_hist;
+    if constexpr (TRACK) {
+        for (int k = 18; k < 18 + 4 * HMAX; ++k) sObs[k * 32 + lane] = 0.0f;
+    } else
     // history (newest first in global) -> ring slot (t0 - i) mod 16
     for (int i = 1; i <= nh; ++i) {
         const int slot = (int)((t0 - (uint32_t)i) & 15u);
@@ -138,7 +200,15 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
         {
             float o[18];
             obs_state(s, o);
-            if (C.any_noise) {
+            if constexpr (TRACK) {
+                float pr[3], vr[3];
+                lissajous(tt, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    o[k] = clampf(o[k] - pr[k], -tr.clip_p, tr.clip_p);
+                    o[12 + k] = clampf(o[12 + k] - vr[k], -tr.clip_v, tr.clip_v);
+                }
+            } else if (C.any_noise) {
                 float nz[18];
                 obs_noise(C, (uint32_t)g, t, nz);
 #pragma unroll
@@ -149,7 +219,7 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
         }
         __syncwarp();
         float a[4];
-        if ((int64_t)t < (int64_t)C.learning_starts) {
+        if (!TRACK && (int64_t)t < (int64_t)C.learning_starts) {
             const uint4 r = draw(C, (uint32_t)g, t, TAG_WARM, 0);
             a[0] = 2.0f * u01(r.x) - 1.0f;
             a[1] = 2.0f * u01(r.y) - 1.0f;
@@ -358,7 +428,7 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
                     mu[j] = tanhf(keep + __shfl_xor_sync(0xffffffffu, send, 1) + smem[L::B3 + j]);
                 }
             }
-            if (sigma > 0.0f) {
+            if (!TRACK && sigma > 0.0f) {
                 const uint4 r0 = draw(C, (uint32_t)g, t, TAG_EXPL, 0);
                 const uint4 r1 = draw(C, (uint32_t)g, t, TAG_EXPL, 1);
                 a[0] = clampf(fmaf(sigma, gauss(r0.x, r0.y), mu[0]), -1.0f, 1.0f);
@@ -376,6 +446,32 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
 #pragma unroll
         for (int i = 0; i < NS; ++i) s2[i] = s[i];
         rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
+        if constexpr (TRACK) {
+            // error against the target at the new time; a non-finite state or an error
+            // outside the training termination box ends the flight (the lane then holds its
+            // last state while its warp finishes the steps)
+            float pr[3], vr[3];
+            lissajous(tt + 1, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+            const float ex = s2[0] - pr[0], ey = s2[1] - pr[1], ez = s2[2] - pr[2];
+            const bool crash = !finite_state(s2) || fabsf(ex) > C.term_pos ||
+                               fabsf(ey) > C.term_pos || fabsf(ez) > C.term_pos;
+            if (alive && crash) alive = false;
+            if (alive) {
+                const double exy2 = (double)ex * ex + (double)ey * ey;
+                exy += exy2;
+                e3 += exy2 + (double)ez * ez;
+                n_ok += 1;
+#pragma unroll
+                for (int i = 0; i < NS; ++i) s[i] = s2[i];
+            }
+            if (nh > 0) {
+                const int hs = 18 + 4 * (int)(t & 15u);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sObs[(hs + c) * 32 + lane] = a[c];
+            }
+            __syncwarp();
+            continue;
+        }
         const float r = reward(Cr, s2, a);
         const bool term = terminated(C, s2);
         const uint32_t ep_after = ep_step + 1;
@@ -427,6 +523,12 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
         __syncwarp();
     }
 
+    if constexpr (TRACK) {
+        tr.sq_err[g] = e3;
+        tr.sq_err[ld + g] = exy;
+        tr.steps_ok[g] = n_ok;
+        return;
+    }
     // ---- write back
     const uint32_t t_end = t0 + (uint32_t)T;
 #pragma unroll
@@ -446,7 +548,7 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
 }
 
 using RollFn = void (*)(EnvCfg, EnvPtrs, const float*, int, uint32_t, int64_t, int64_t, float,
-                        int, int);
+                        int, int, TrackArgs);
 
 template <int H, bool PK>
 static RollFn pick(int nw) {
@@ -595,7 +697,7 @@ qsim_status launch_rollout(qsim_handle* h, const float* actor, int hidden, int T
     if (parts == 1 && chunk == T) {
         const int grid = (warps + nw - 1) / nw;
         fn<<<grid, nw * 32, smem, st>>>(h->dc, h->p, actor, T, t0, h->head, h->capacity, sigma, 0,
-                                         warps);
+                                         warps, TrackArgs{});
         QCHECK_LAUNCH("k_rollout");
         return QSIM_OK;
     }
@@ -610,7 +712,8 @@ qsim_status launch_rollout(qsim_handle* h, const float* actor, int hidden, int T
             if (w1 <= w0) continue;
             const int grid = (w1 - w0 + nw - 1) / nw;
             fn<<<grid, nw * 32, smem, h->part_stream[p]>>>(h->dc, h->p, actor, tc, t0 + (uint32_t)t,
-                                                            h->head + t, h->capacity, sigma, w0, w1);
+                                                            h->head + t, h->capacity, sigma, w0, w1,
+                                                            TrackArgs{});
             QCHECK_LAUNCH("k_rollout");
         }
     }
@@ -742,4 +845,42 @@ extern "C" int32_t qsim_rollout_schedule(qsim_handle* h, int32_t parts, int32_t 
     if (parts >= 0 && parts <= 4) h->rollout_parts = parts;
     if (chunk >= 0) h->rollout_chunk = chunk;
     return h->rollout_parts;
+}
+
+namespace qsim {
+template <int H>
+static RollFn track_fn() { return k_rollout<H, 4, true, true>; }
+}  // namespace qsim
+
+extern "C" qsim_status qsim_track(qsim_handle* h, const float* actor, int32_t hidden,
+                                  int32_t n_steps, const float* period, float amplitude, float z0,
+                                  float clip_p, float clip_v, double* sq_err, int32_t* steps_ok,
+                                  void* stream) {
+    if (!h || !actor || !period || !sq_err || !steps_ok)
+        return fail(QSIM_EINVAL, "qsim_track: null pointer");
+    if (hidden != 32 && hidden != 64 && hidden != 128)
+        return fail(QSIM_EINVAL, "qsim_track: hidden=%d not in {32,64,128}", hidden);
+    if (n_steps < 0) return fail(QSIM_EINVAL, "qsim_track: n_steps < 0");
+    if (!(std::fabs(amplitude) <= 1e6f) || !(std::fabs(z0) <= 1e6f) || !(clip_p >= 0.0f) ||
+        !(clip_v >= 0.0f) || !(clip_p <= 1e30f) || !(clip_v <= 1e30f))
+        return fail(QSIM_EINVAL, "qsim_track: amplitude, z0 and clips must be finite, clips >= 0");
+    const float* ptrs[3] = {actor, period, reinterpret_cast<const float*>(steps_ok)};
+    for (const float* q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) % 4) return fail(QSIM_EINVAL, "qsim_track: misaligned pointer");
+    if (reinterpret_cast<uintptr_t>(sq_err) % 8) return fail(QSIM_EINVAL, "qsim_track: misaligned pointer");
+    constexpr int nw = 4;
+    RollFn fn = hidden == 32 ? track_fn<32>() : (hidden == 64 ? track_fn<64>() : track_fn<128>());
+    const size_t smem = roll_smem(hidden, nw);
+    static bool configured[3] = {};
+    const int hi = hidden == 32 ? 0 : (hidden == 64 ? 1 : 2);
+    if (!configured[hi]) {
+        QCHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured[hi] = true;
+    }
+    const int warps = h->ld / 32;
+    TrackArgs tr{period, amplitude, z0, clip_p, clip_v, sq_err, steps_ok};
+    fn<<<(warps + nw - 1) / nw, nw * 32, smem, (cudaStream_t)stream>>>(
+        h->dc, h->p, actor, n_steps, 0u, 0, 0, 0.0f, 0, warps, tr);
+    QCHECK_LAUNCH("k_rollout<track>");
+    return QSIM_OK;
 }
