@@ -536,14 +536,13 @@ int or_rollout(const or_cfg* c, const or_reward_c* C, or_envs* e, const double* 
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Trajectory tracking in simulation (Sec. V "Trajectory tracking").  The trained        */
-/* position controller is steered along a moving target by offsetting its observation:  */
-/* Sec. IV reaches any position / velocity set-point by shifting the current position   */
-/* and velocity, clipped so that the errors stay within those seen in training.  The     */
-/* target of Sec. V is the figure-eight Lissajous curve                                  */
-/*   p*(t) = (A cos(2 pi t / T), (A / 2) sin(4 pi t / T), z0)                            */
-/* (A = 1 m in the paper); v*(t) is its time derivative.                                 */
-/* ------------------------------------------------------------------------------------ */
+/* Trajectory tracking in simulation (Sec. V "Trajectory tracking").  The trained
+ * position controller is steered along a moving target by offsetting its observation:
+ * Sec. IV reaches any position / velocity set-point by shifting the current position and
+ * velocity, with the offsets clipped to the size the controller met in training.  The
+ * target of Sec. V is the figure-eight Lissajous curve
+ *   p*(t) = (A cos(2 pi t / T), (A / 2) sin(4 pi t / T), z0)
+ * (A = 1 m in the paper); v*(t) is its time derivative. */
 void or_lissajous(double t, double T, double A, double z0, double* p, double* v) {
     const double w = 2.0 * M_PI / T;
     p[0] = A * cos(w * t);
