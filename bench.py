@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--learner-steps", type=int, default=20)
     ap.add_argument("--only-diff", action="store_true",
                     help="only the differentiation sample (c3 shape), for profiling")
+    ap.add_argument("--only-ablation", action="store_true",
+                    help="only the ablation-study sample (ten variants in one launch)")
     ap.add_argument("--only-track", action="store_true",
                     help="only the Lissajous tracking sample, for profiling")
     ap.add_argument("--warps", type=int, default=0,
@@ -285,6 +287,51 @@ def measure_track(torch, q, W, fp32_peak, n=65536, steps=1000, hidden=64):
         return res
     finally:
         q.qsim_destroy(h)
+
+
+def measure_ablation(torch, q, W, seeds=5, steps=3000):
+    """The ablation study's ten variants (Sec. VI) x `seeds` seeds as runs of ONE persistent
+    training launch (1 env per run, width 64, batch 256, 1,000 warm-up steps, then one
+    update per env step).  Reports the launch's throughput and, per variant, the mean
+    length and return of the episodes completed so far: at a few thousand steps these are
+    early-training numbers, not the paper's 300,000-step checkpoint."""
+    names = list(W.ABLATIONS)
+    runs, envs, tags = [], [], []
+    for i, name in enumerate(names):
+        for k in range(seeds):
+            r = i * seeds + k
+            c, cur, recalc = W.ablation(name)
+            c.update(seed=k, run_id=r)
+            cfg = q.make_config(c, 1, steps, reward=W.REWARD, sigma_e=0.1, curriculum=cur,
+                                recalc_rewards=recalc)
+            h = q.qsim_create(cfg, q.make_params(c))
+            runs.append(q.ac_create(q.make_ac_config(dict(W.TD3), cluster=0), h))
+            envs.append(h)
+            tags.append(name)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        q.ac_train(runs, envs, steps, persistent=1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        updates = len(runs) * (steps - 1000)
+        res = {"runs": len(runs), "steps_per_run": steps, "s": dt,
+               "env_steps_per_s": len(runs) * steps / dt, "updates_per_s": updates / dt,
+               "variants": {}}
+        for name in names:
+            st = [q.qsim_stats_get(h) for h, t in zip(envs, tags) if t == name]
+            eps = sum(x["episodes"] for x in st)
+            res["variants"][name] = {
+                "episodes": eps,
+                "mean_length": (sum(x["mean_length"] * x["episodes"] for x in st) / eps
+                                if eps else None),
+                "mean_return": (sum(x["mean_return"] * x["episodes"] for x in st) / eps
+                                if eps else None)}
+        return res
+    finally:
+        for a, h in zip(runs, envs):
+            q.ac_destroy(a)
+            q.qsim_destroy(h)
 
 
 def measure_recalc(torch, q, h, n, horizon, hbm):
@@ -554,6 +601,11 @@ def main():
         q.load()
         print(json.dumps({"differentiation_c3": measure_diff(torch, q, W)}))
         return
+    if args.only_ablation:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        q.load()
+        print(json.dumps({"ablation_study": measure_ablation(torch, q, W)}))
+        return
     if args.only_track:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         q.load()
@@ -662,6 +714,7 @@ def main():
         extras["learner_single_run_c1"] = measure_c1(torch, q, W)
         extras["differentiation_c3"] = measure_diff(torch, q, W)
         extras["asymmetric_curriculum_c5"] = measure_c5(torch, q, W)
+        extras["ablation_study"] = measure_ablation(torch, q, W)
     step_s = sum(ms) / args.steps * 1e-3
     hbm_ach = n * horizon * BYTES_STEP / step_s / 1e9
     if packed_used == 2:

@@ -51,7 +51,9 @@ typedef enum qsim_status {
 typedef enum qsim_critic_layout {
     QSIM_CRITIC_HIST = 0,    /* actor obs (noise-free) + 4 normalised motor speeds        */
     QSIM_CRITIC_PRIV = 1,    /* ... + true mass, inertia, thrust coeff., motor T (rel.)  */
-    QSIM_CRITIC_PAPER28 = 2  /* {p, R, v, omega, omega_m, f_r, tau_r}: the 28-D vector   */
+    QSIM_CRITIC_PAPER28 = 2, /* {p, R, v, omega, omega_m, f_r, tau_r}: the 28-D vector   */
+    QSIM_CRITIC_ACTOR = 3    /* the actor's own observation, noise included: no privileged
+                                information (Sec. VI ablation of the asymmetric critic)  */
 } qsim_critic_layout;
 
 /* Nominal vehicle (Sec. IV "standard dynamics of a quadrotor subject to motor delays";
@@ -78,7 +80,10 @@ typedef struct qsim_config {
     int32_t renorm_q;        /* renormalise q after each RK4 step (1) or not (0) */
     int32_t learning_starts; /* global steps with uniform random actions (TD3 warm-up) */
     int32_t replay_capacity; /* time slots per env in the replay ring (0 = no buffer) */
-    int32_t reserved0;
+    int32_t motor_lag_off;   /* 1: no motor model (Sec. VI ablation "rotor delay"): the
+                                rotors run at the clipped set-point from the start of each
+                                step; 0: first-order lag.  Env-set kernels only
+                                (qsim_dynamics_* and qsim_rollout_vjp always model the lag) */
     float dt;                /* integration step, s (0.01 = 100 Hz) */
     uint32_t run_id;         /* random-stream id of this run */
     uint64_t seed;           /* Philox key */
@@ -184,7 +189,8 @@ qsim_status qsim_set_counters(qsim_handle* h, int64_t t_now, int64_t head, int64
 qsim_status qsim_sync(qsim_handle* h);
 
 /* Actor and critic observations of the current states (Sec. IV: o_a = {p, R, v, omega,
- * H} with noise of the current step; o_c privileged and noise-free).  obs_a
+ * H} with noise of the current step; o_c privileged and noise-free, except in the
+ * symmetric layout QSIM_CRITIC_ACTOR, where o_c = o_a).  obs_a
  * [obs_dim][ld], obs_c [critic_obs_dim][ld] (either may be NULL); device pointers. */
 qsim_status qsim_observe(qsim_handle* h, float* obs_a, float* obs_c, void* stream);
 

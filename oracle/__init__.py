@@ -56,6 +56,7 @@ class Cfg(C.Structure):
         ("sig_w", C.c_double),
         ("term_pos", C.c_double),
         ("seed", C.c_uint64), ("run_id", C.c_uint32), ("learning_starts", C.c_int32),
+        ("motor_lag_off", C.c_int32), ("pad_", C.c_int32),
     ]
 
 

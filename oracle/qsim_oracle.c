@@ -73,6 +73,7 @@ int or_actor_in(const or_cfg* c) { return 18 + 4 * c->n_hist; }
 static int critic_obs_dim(const or_cfg* c) {
     if (c->critic_layout == OR_CRITIC_PAPER28) return 28;      /* {p,R,v,w,w_m,f_r,tau_r} */
     if (c->critic_layout == OR_CRITIC_PRIV) return or_actor_in(c) + 4 + OR_NPRIV;
+    if (c->critic_layout == OR_CRITIC_ACTOR) return or_actor_in(c);  /* symmetric critic */
     return or_actor_in(c) + 4;                                  /* actor obs + motor speeds */
 }
 /* The critic sees its observation followed by the action (Q(o_c, a)). */
@@ -307,6 +308,7 @@ void or_obs_critic(const or_cfg* c, const double* s, const double* hist, const d
     }
     int da = or_actor_in(c);
     or_obs_actor(c, s, hist, NULL, o);
+    if (c->critic_layout == OR_CRITIC_ACTOR) return; /* symmetric: the actor's observation */
     for (int i = 0; i < 4; ++i) o[da + i] = rpm_norm(c, s[13 + i]);
     if (c->critic_layout == OR_CRITIC_PRIV)
         for (int k = 0; k < OR_NPRIV; ++k) o[da + 4 + k] = priv[k];
@@ -412,6 +414,18 @@ static void mlp_backward(const or_net* net, const double* P, const double* x, co
 /* -> RPM set-point -> RK4 -> reward -> termination -> transition record -> history ->  */
 /* reset when the episode ended.                                                        */
 /* ------------------------------------------------------------------------------------ */
+/* One env step of the dynamics at set-point u.  With the motor model ablated (Sec. VI,
+ * "rotor delay" removed) the rotors run at the clipped set-point from the start of the
+ * step, so the lag term of the motor equation is zero throughout. */
+static void step_dynamics(const or_cfg* c, const double* s, const double* u, const double* prm,
+                          const double* dist, double* s2) {
+    double sm[OR_NS];
+    memcpy(sm, s, sizeof(sm));
+    if (c->motor_lag_off)
+        for (int i = 0; i < 4; ++i) sm[13 + i] = clampd(u[i], c->rpm_min, c->rpm_max);
+    or_rk4(c, sm, u, prm, dist, c->dt, c->renorm_q, s2);
+}
+
 typedef struct roll_job {
     const or_cfg* c;
     const or_reward_c* C;
@@ -476,7 +490,7 @@ static void roll_env(const roll_job* J, int k) {
         for (int i = 0; i < 4; ++i)
             u[i] = c->rpm_min + 0.5 * (a[i] + 1.0) * (c->rpm_max - c->rpm_min);
         double s2[OR_NS];
-        or_rk4(c, s, u, prm, dist, c->dt, c->renorm_q, s2);
+        step_dynamics(c, s, u, prm, dist, s2);
         double r = or_reward(J->C, s2, a);
         uint32_t ep_before = e->ep_step[k];
         e->ep_step[k] += 1;
@@ -598,7 +612,7 @@ static void track_env(const or_cfg* c, const or_track* J, int k) {
             a[i] = clampd(mu[i], -1.0, 1.0);
             u[i] = c->rpm_min + 0.5 * (a[i] + 1.0) * (c->rpm_max - c->rpm_min);
         }
-        or_rk4(c, s, u, prm, dist, c->dt, c->renorm_q, s2);
+        step_dynamics(c, s, u, prm, dist, s2);
         /* tracking error against the target at the new time; a non-finite state or an
          * error outside the training termination box ends the flight (reading) */
         or_lissajous((kk + 1) * c->dt, T, J->amp, J->z0, pr, vr);
@@ -732,9 +746,16 @@ int or_td3_update(const or_cfg* c, or_td3* L, const or_buffer* b, or_td3_diag* d
         or_obs_noise(c, (uint32_t)env, (uint64_t)(t_rec + 1), n2);
         or_obs_actor(c, s, hist, n1, oa + (size_t)j * DA);
         or_obs_actor(c, s2, hist2, n2, oa2 + (size_t)j * DA);
-        or_obs_critic(c, s, hist, priv, oc + (size_t)j * DC);
+        if (c->critic_layout == OR_CRITIC_ACTOR) {
+            /* ablation of the asymmetric actor-critic: the critic sees exactly what the
+             * actor sees, observation noise included */
+            memcpy(oc + (size_t)j * DC, oa + (size_t)j * DA, sizeof(double) * (size_t)DA);
+            memcpy(oc2 + (size_t)j * DC, oa2 + (size_t)j * DA, sizeof(double) * (size_t)DA);
+        } else {
+            or_obs_critic(c, s, hist, priv, oc + (size_t)j * DC);
+            or_obs_critic(c, s2, hist2, priv, oc2 + (size_t)j * DC);
+        }
         for (int cc = 0; cc < 4; ++cc) oc[(size_t)j * DC + DC - 4 + cc] = a[cc];
-        or_obs_critic(c, s2, hist2, priv, oc2 + (size_t)j * DC);
         rr[j] = b->r[rk];
         term[j] = (int)(fl & 1u);
     }

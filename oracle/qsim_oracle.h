@@ -23,7 +23,7 @@
 #define OR_NPRIV 6
 #define OR_HMAX 16    /* longest action history */
 
-enum { OR_CRITIC_HIST = 0, OR_CRITIC_PRIV = 1, OR_CRITIC_PAPER28 = 2 };
+enum { OR_CRITIC_HIST = 0, OR_CRITIC_PRIV = 1, OR_CRITIC_PAPER28 = 2, OR_CRITIC_ACTOR = 3 };
 
 typedef struct or_cfg {
     /* nominal vehicle */
@@ -48,6 +48,8 @@ typedef struct or_cfg {
     uint64_t seed;
     uint32_t run_id;
     int32_t learning_starts;
+    /* ablation of the motor model: 1 = the rotors run at their set-point at once */
+    int32_t motor_lag_off, pad_;
 } or_cfg;
 
 /* Reward constants, in the order of the reward formula: C_rp C_rq C_rv C_rw C_ra C_rab C_rs */

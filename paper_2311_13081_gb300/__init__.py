@@ -42,7 +42,7 @@ class QsimConfig(C.Structure):
     _fields_ = [("n_envs", C.c_int32), ("n_hist", C.c_int32), ("episode_len", C.c_int32),
                 ("critic_layout", C.c_int32), ("renorm_q", C.c_int32),
                 ("learning_starts", C.c_int32), ("replay_capacity", C.c_int32),
-                ("reserved0", C.c_int32), ("dt", C.c_float), ("run_id", C.c_uint32),
+                ("motor_lag_off", C.c_int32), ("dt", C.c_float), ("run_id", C.c_uint32),
                 ("seed", C.c_uint64),
                 ("init_p", C.c_float), ("init_att", C.c_float), ("init_v", C.c_float),
                 ("init_w", C.c_float), ("init_rpm_lo", C.c_float), ("init_rpm_hi", C.c_float),
@@ -222,6 +222,7 @@ def make_config(d: dict, n_envs: int, replay_capacity: int = 0, reward=None, sig
     c.n_envs, c.replay_capacity = int(n_envs), int(replay_capacity)
     for k in ("n_hist", "episode_len", "critic_layout", "renorm_q", "learning_starts"):
         setattr(c, k, int(d[k]))
+    c.motor_lag_off = int(d.get("motor_lag_off", 0))
     c.dt, c.run_id, c.seed = d["dt"], int(d.get("run_id", 0)), int(d.get("seed", 0))
     for k in ("init_p", "init_att", "init_v", "init_w", "init_rpm_lo", "init_rpm_hi", "dr_mass",
               "dr_J", "dr_kf", "tm_lo", "tm_hi", "dist_f", "dist_tau", "sig_p", "sig_R", "sig_v",

@@ -37,6 +37,7 @@ struct EnvCfg {
     int any_noise;
     float term_pos;
     int n_hist, episode_len, critic_layout, learning_starts;
+    int no_lag;  // motor model ablated: rotors at the set-point at once
     int obs_dim, cobs_dim, n_priv, F;  // F: floats per transition record
     uint32_t key0, key1, run_id;
     int n, ld;
@@ -179,6 +180,16 @@ __device__ __forceinline__ void rk4(const Vehicle& V, float dt, int renorm, floa
     if (renorm) {
         const float inv = rsqrtf(s[3] * s[3] + s[4] * s[4] + s[5] * s[5] + s[6] * s[6]);
         s[3] *= inv; s[4] *= inv; s[5] *= inv; s[6] *= inv;
+    }
+}
+
+// Motor-model ablation (Sec. VI, the study without rotor delay): the rotors run at the
+// clipped set-point from the start of the step, so the lag term of the motor equation is
+// zero in every RK4 stage.
+__device__ __forceinline__ void motor_lag_off(const EnvCfg& C, const float* u, float* s) {
+    if (C.no_lag) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s[13 + i] = clampf(u[i], C.veh.rpm_min, C.veh.rpm_max);
     }
 }
 

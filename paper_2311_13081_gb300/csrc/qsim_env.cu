@@ -48,6 +48,7 @@ static int critic_obs_dim(const qsim_config& c) {
     const int da = 18 + 4 * c.n_hist;
     if (c.critic_layout == QSIM_CRITIC_PAPER28) return 28;
     if (c.critic_layout == QSIM_CRITIC_PRIV) return da + 4 + NPRIV;
+    if (c.critic_layout == QSIM_CRITIC_ACTOR) return da;
     return da + 4;
 }
 
@@ -72,7 +73,8 @@ EnvCfg make_env_cfg(const qsim_config& c, const qsim_params& v, int n, int ld) {
     C.learning_starts = c.learning_starts;
     C.obs_dim = 18 + 4 * c.n_hist;
     C.cobs_dim = critic_obs_dim(c);
-    C.n_priv = c.critic_layout == QSIM_CRITIC_HIST ? 0 : NPRIV;
+    C.n_priv = (c.critic_layout == QSIM_CRITIC_PRIV || c.critic_layout == QSIM_CRITIC_PAPER28) ? NPRIV : 0;
+    C.no_lag = c.motor_lag_off ? 1 : 0;
     C.F = 23 + C.n_priv;
     C.key0 = (uint32_t)(c.seed & 0xffffffffu);
     C.key1 = (uint32_t)(c.seed >> 32);
@@ -209,7 +211,10 @@ __global__ void k_observe(EnvCfg C, EnvPtrs p, uint32_t t, float* obs_a, float* 
     const Prm P = load_prm(p.prm, ld, e);
     priv_vals(C, P, d, pv);
     if (obs_a) write_actor_obs(C, s, (uint32_t)e, t, p.hist + e, ld, obs_a + e, ld);
-    if (obs_c) write_critic_obs(C, s, pv, p.hist + e, ld, obs_c + e, ld);
+    if (obs_c) {
+        if (C.critic_layout == 3) write_actor_obs(C, s, (uint32_t)e, t, p.hist + e, ld, obs_c + e, ld);
+        else write_critic_obs(C, s, pv, p.hist + e, ld, obs_c + e, ld);
+    }
 }
 
 // One env step with external actions (thread per env).
@@ -234,6 +239,7 @@ __global__ void k_step(EnvCfg C, EnvPtrs p, const float* __restrict__ actions, u
     float s2[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) s2[i] = s[i];
+    motor_lag_off(C, u, s2);
     rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
     const float r = reward(Cr, s2, a);
     const uint32_t ep_before = p.ep_step[e];
@@ -289,7 +295,10 @@ __global__ void k_step(EnvCfg C, EnvPtrs p, const float* __restrict__ actions, u
     if (trunc_out) trunc_out[e] = trunc ? 1 : 0;
     priv_vals(C, P, d, pv);
     if (obs_a) write_actor_obs(C, s2, (uint32_t)e, t + 1, p.hist + e, ld, obs_a + e, ld);
-    if (obs_c) write_critic_obs(C, s2, pv, p.hist + e, ld, obs_c + e, ld);
+    if (obs_c) {
+        if (C.critic_layout == 3) write_actor_obs(C, s2, (uint32_t)e, t + 1, p.hist + e, ld, obs_c + e, ld);
+        else write_critic_obs(C, s2, pv, p.hist + e, ld, obs_c + e, ld);
+    }
 }
 
 // Reward recalculation over every stored record (HBM streaming: reads s', a, flags,
@@ -466,7 +475,7 @@ static qsim_status validate_cfg(const qsim_config* c, const qsim_params* v) {
     if (c->n_hist < 0 || c->n_hist > HMAX)
         return fail(QSIM_EINVAL, "qsim_create: n_hist=%d not in 0..16", c->n_hist);
     if (c->episode_len < 1) return fail(QSIM_EINVAL, "qsim_create: episode_len < 1");
-    if (c->critic_layout < 0 || c->critic_layout > 2)
+    if (c->critic_layout < 0 || c->critic_layout > 3)
         return fail(QSIM_EINVAL, "qsim_create: bad critic_layout");
     if (c->replay_capacity < 0 || (c->replay_capacity > 0 && c->replay_capacity < 2))
         return fail(QSIM_EINVAL, "qsim_create: replay_capacity must be 0 or >= 2");

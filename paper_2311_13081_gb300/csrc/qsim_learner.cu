@@ -340,6 +340,7 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
         action_to_rpm(C.veh, a, u);
 #pragma unroll
         for (int i = 0; i < NS; ++i) s2[i] = s[i];
+        motor_lag_off(C, u, s2);
         rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
         const float r = reward(Cr, s2, a);
         const bool term = terminated(C, s2);
@@ -474,15 +475,18 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
             float* oax = w == 0 ? oa : oa2;
             float o[18];
             obs_state(st, o);
-            // critic observations (noise-free)
+            // critic observations (noise-free; the symmetric layout 3 copies the actor's
+            // noisy observation below)
+            if (C.critic_layout != 3) {
 #pragma unroll
-            for (int q = 0; q < 18; ++q) ocx[q] = o[q];
-            const int rpm_at = C.critic_layout == 2 ? 18 : DA;
+                for (int q = 0; q < 18; ++q) ocx[q] = o[q];
+                const int rpm_at = C.critic_layout == 2 ? 18 : DA;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) ocx[rpm_at + i] = rpm_norm(C.veh, st[13 + i]);
-            if (C.critic_layout != 0) {
+                for (int i = 0; i < 4; ++i) ocx[rpm_at + i] = rpm_norm(C.veh, st[13 + i]);
+                if (C.critic_layout != 0) {
 #pragma unroll
-                for (int q = 0; q < 6; ++q) ocx[rpm_at + 4 + q] = pv[q];
+                    for (int q = 0; q < 6; ++q) ocx[rpm_at + 4 + q] = pv[q];
+                }
             }
             if (w == 0) {
 #pragma unroll
@@ -498,6 +502,10 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
             }
 #pragma unroll
             for (int q = 0; q < 18; ++q) oax[q] = o[q];
+            if (C.critic_layout == 3) {
+#pragma unroll
+                for (int q = 0; q < 18; ++q) ocx[q] = o[q];
+            }
         } else {
             // history: o_a has a_{t-1..t-NH}, o_a' has a_t, a_{t-1..t-NH+1}; zeros before the
             // episode start.  Warp w handles lags i = w-1, w+5, w+11.

@@ -445,6 +445,7 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
         action_to_rpm(C.veh, a, u);
 #pragma unroll
         for (int i = 0; i < NS; ++i) s2[i] = s[i];
+        motor_lag_off(C, u, s2);
         rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
         if constexpr (TRACK) {
             // error against the target at the new time; a non-finite state or an error

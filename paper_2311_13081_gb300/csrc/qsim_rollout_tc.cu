@@ -567,6 +567,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 action_to_rpm(C.veh, a, u);
 #pragma unroll
                 for (int i = 0; i < NS; ++i) s2[i] = s[i];
+                motor_lag_off(C, u, s2);
                 rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
                 const float rw = reward(Cr, s2, a);
                 const bool term = terminated(C, s2);

@@ -93,13 +93,15 @@ def test_create_resets_like_oracle(gpu):
         q.qsim_destroy(h)
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2])
-def test_step_and_observe_parity(gpu, layout):
+@pytest.mark.parametrize("layout,lag_off", [(0, 0), (1, 0), (2, 0), (3, 1)])
+def test_step_and_observe_parity(gpu, layout, lag_off):
+    """Every critic layout (3: the symmetric critic of the ablation study, whose o_c is the
+    noisy o_a); the last case also with the motor model ablated."""
     q = gpu
     n = 70
     d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=16, critic_layout=layout,
                              episode_len=9, sig_p=0.01, sig_R=0.02, sig_v=0.03, sig_w=0.04,
-                             dist_f=0.01, dist_tau=1e-4)
+                             dist_f=0.01, dist_tau=1e-4, motor_lag_off=lag_off)
     h = q.qsim_create(cfg, veh)
     try:
         info = q.qsim_info_get(h)
@@ -133,7 +135,7 @@ def test_step_and_observe_parity(gpu, layout):
                 o_ref = O.obs_actor(d, e["s"][k], e["hist"][k], O.obs_noise(d, k, t0 + 1))
                 assert_close(f64(oa)[:, k], o_ref, 1.0, what="obs_a")
                 pv = O.priv(d, e["prm"][k], e["dist"][k])
-                c_ref = O.obs_critic(d, e["s"][k], e["hist"][k], pv)
+                c_ref = o_ref if layout == 3 else O.obs_critic(d, e["s"][k], e["hist"][k], pv)
                 assert_close(f64(oc)[:, k], c_ref, 1.0, what="obs_c")
         st = q.qsim_stats_get(h)
         assert st["episodes"] > 0 and st["mean_length"] <= 9
@@ -147,12 +149,16 @@ def _actor(d, hidden, seed=0):
     return O.init_params(dd, 0, O.actor_in(d), hidden, 4).astype(np.float32)
 
 
-@pytest.mark.parametrize("hidden,n,warps", [(64, 300, 0), (64, 1000, 4), (32, 100, 0),
-                                            (128, 200, 2), (64, 64, 10)])
-def test_rollout_parity(gpu, hidden, n, warps):
+@pytest.mark.parametrize("hidden,n,warps,lag_off", [(64, 300, 0, 0), (64, 1000, 4, 0),
+                                                    (32, 100, 0, 0), (128, 200, 2, 0),
+                                                    (64, 64, 10, 0), (64, 300, 0, 1)])
+def test_rollout_parity(gpu, hidden, n, warps, lag_off):
+    """Widths, warps per block, ragged env counts; the last case without the motor model
+    (the ablation study's variant without rotor delay)."""
     q = gpu
     d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=6, learning_starts=3, episode_len=40,
-                             sig_p=0.005, sig_R=0.01, sig_v=0.02, sig_w=0.02)
+                             sig_p=0.005, sig_R=0.01, sig_v=0.02, sig_w=0.02,
+                             motor_lag_off=lag_off)
     h = q.qsim_create(cfg, veh)
     q.qsim_rollout_engine(h, SIMT)
     try:

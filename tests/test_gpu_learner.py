@@ -63,11 +63,12 @@ def check_update(ai, Lref, dg, hp, what):
 
 
 def make_run(q, n_env=3, cap=64, hidden=32, batch=64, cluster=1, layout=0, steps=40, seed=0,
-             episode_len=12):
+             episode_len=12, **over):
     d, cfg, veh = lib_config(q, "c2" if layout == 1 else "c1", n_envs=n_env, capacity=cap,
                              critic_layout=layout, episode_len=episode_len, learning_starts=0,
                              seed=seed, sig_p=0.003, sig_R=0.003, sig_v=0.01, sig_w=0.01,
-                             dist_f=0.002 if layout == 2 else 0.0, dist_tau=1e-5 if layout == 2 else 0.0)
+                             dist_f=0.002 if layout == 2 else 0.0, dist_tau=1e-5 if layout == 2 else 0.0,
+                             **over)
     h = q.qsim_create(cfg, veh)
     hp = dict(W.TD3)
     hp.update(hidden=hidden, batch=batch)
@@ -83,7 +84,8 @@ def make_run(q, n_env=3, cap=64, hidden=32, batch=64, cluster=1, layout=0, steps
 
 @pytest.mark.parametrize("cluster,layout,hidden,batch", [(1, 0, 32, 64), (2, 0, 64, 64),
                                                          (4, 1, 32, 128), (1, 2, 16, 32),
-                                                         (8, 0, 128, 256), (1, 0, 128, 128)])
+                                                         (8, 0, 128, 256), (1, 0, 128, 128),
+                                                         (2, 3, 64, 64)])
 def test_ac_update_parity(gpu, cluster, layout, hidden, batch):
     q = gpu
     d, h, a, hp = make_run(q, hidden=hidden, batch=batch, cluster=cluster, layout=layout)
@@ -113,10 +115,13 @@ def test_ac_update_parity(gpu, cluster, layout, hidden, batch):
         q.qsim_destroy(h)
 
 
-def test_train_iteration_parity(gpu):
-    """One ac_train step = one env step (generic tile path) + one update, vs the oracle."""
+@pytest.mark.parametrize("lag_off,layout", [(0, 0), (1, 3)])
+def test_train_iteration_parity(gpu, lag_off, layout):
+    """One ac_train step = one env step (generic tile path) + one update, vs the oracle;
+    also with the motor model ablated and the symmetric critic."""
     q = gpu
-    d, h, a, hp = make_run(q, n_env=5, cap=32, hidden=32, batch=32, cluster=2, steps=20)
+    d, h, a, hp = make_run(q, n_env=5, cap=32, hidden=32, batch=32, cluster=2, steps=20,
+                           layout=layout, motor_lag_off=lag_off)
     try:
         for it in range(3):
             info = q.qsim_info_get(h)
@@ -297,3 +302,43 @@ def test_graph_plan_equals_persistent_training(gpu):
         for a, h in zip(r1 + r2, e1 + e2):
             q.ac_destroy(a)
             q.qsim_destroy(h)
+
+
+def test_ablation_study_runs_in_one_persistent_launch(gpu):
+    """The ablation study's ten variants (different critic layouts, history lengths, motor
+    models, noise, disturbances, curricula) as runs of one persistent training launch give
+    bit for bit what each run gives when launched on its own."""
+    q = gpu
+
+    def make(r, name):
+        c, cur, recalc = W.ablation(name)
+        c.update(seed=r, run_id=r, learning_starts=8)
+        cur = dict(cur, interval=12)
+        cfg = q.make_config(c, 1, 40, reward=W.REWARD, sigma_e=0.1, curriculum=cur,
+                            recalc_rewards=recalc)
+        h = q.qsim_create(cfg, q.make_params(c))
+        hp = dict(W.TD3)
+        hp.update(hidden=32, batch=32)
+        return q.ac_create(q.make_ac_config(hp, cluster=1), h), h
+
+    def snap(a, h):
+        return (cpu(q.ac_info_get(a)["c1"]).copy(), cpu(q.ac_info_get(a)["actor"]).copy(),
+                cpu(q.qsim_info_get(h)["records"]).copy())
+
+    names = list(W.ABLATIONS)
+    pairs = [make(r, name) for r, name in enumerate(names)]
+    q.ac_train([a for a, _ in pairs], [h for _, h in pairs], 30, persistent=1)
+    torch.cuda.synchronize()
+    together = [snap(a, h) for a, h in pairs]
+    for a, h in pairs:
+        q.ac_destroy(a)
+        q.qsim_destroy(h)
+    for r, name in enumerate(names):
+        a, h = make(r, name)
+        q.ac_train([a], [h], 30, persistent=1)
+        torch.cuda.synchronize()
+        alone = snap(a, h)
+        for x, y in zip(alone, together[r]):
+            assert np.array_equal(x, y), name
+        q.ac_destroy(a)
+        q.qsim_destroy(h)

@@ -73,6 +73,11 @@ def test_tc_rollout_parity_short_history(gpu):
     _run_parity(gpu, 300, (4, 1, 2), n_hist=5)
 
 
+def test_tc_rollout_parity_without_motor_lag(gpu):
+    """The ablation study's variant without rotor delay on the tensor-core engine."""
+    _run_parity(gpu, 300, (2, 1, 3, 1), motor_lag_off=1)
+
+
 def test_tc_rollout_parity_without_history(gpu):
     """No action history (18-input actor): every lag block of W1 is zero."""
     _run_parity(gpu, 200, (3, 1), n_hist=0)

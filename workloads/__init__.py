@@ -67,6 +67,43 @@ CURRICULUM = dict(interval=100_000,
                   sigma_factor=(0.01 / 0.5) ** (1.0 / 3.0), sigma_min=0.02)
 
 
+# Ablation study (Sec. VI): the full method and the variants that each remove one
+# component (the last removes two).  The observation-noise and disturbance scales of the
+# full method are the builder's values (the paper's are in the unavailable supplement).
+ABLATION_BASE = dict(critic_layout=0, sig_p=0.002, sig_R=0.01, sig_v=0.01, sig_w=0.01,
+                     dist_f=0.0027, dist_tau=1.0e-6, motor_lag_off=0, learning_starts=1000)
+ABLATIONS = {
+    "all_components": {},
+    "observation_noise": dict(sig_p=0.0, sig_R=0.0, sig_v=0.0, sig_w=0.0),
+    "reward_recalculation": dict(recalc_rewards=0),
+    "exploration_noise_decay": dict(sigma_factor=1.0),
+    "disturbances": dict(dist_f=0.0, dist_tau=0.0),
+    "asymmetric_actor_critic": dict(critic_layout=3),
+    "action_history": dict(n_hist=0),
+    "curriculum": dict(curriculum=False),
+    "rotor_delay": dict(motor_lag_off=1),
+    "aac_and_curriculum": dict(critic_layout=3, curriculum=False),
+}
+
+
+def ablation(name: str):
+    """(sim config, curriculum, recalc_rewards) of one variant of the ablation study.
+    Without the curriculum the reward constants keep their initial values while the
+    exploration noise still decays; without the decay the noise stays at its start value."""
+    c = config("c2")
+    c.update(ABLATION_BASE)
+    v = dict(ABLATIONS[name])
+    cur = dict(CURRICULUM)
+    if v.pop("curriculum", True) is False:
+        cur["factor"] = [1.0] * 7
+        cur["target"] = list(REWARD)
+    if "sigma_factor" in v:
+        cur["sigma_factor"] = v.pop("sigma_factor")
+    recalc = v.pop("recalc_rewards", 1)
+    c.update(v)
+    return c, cur, recalc
+
+
 def config(name: str = "c1") -> dict:
     """Full simulation config (vehicle + sim + preset overrides) as a plain dict."""
     c = dict(VEHICLE)
