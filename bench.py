@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--learner-steps", type=int, default=20)
     ap.add_argument("--only-diff", action="store_true",
                     help="only the differentiation sample (c3 shape), for profiling")
+    ap.add_argument("--only-c1", action="store_true",
+                    help="only the single-run learner sample (1 env, batch 256), for profiling")
     ap.add_argument("--only-ablation", action="store_true",
                     help="only the ablation-study sample (ten variants in one launch)")
     ap.add_argument("--only-track", action="store_true",
@@ -600,6 +602,11 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         q.load()
         print(json.dumps({"differentiation_c3": measure_diff(torch, q, W)}))
+        return
+    if args.only_c1:
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        q.load()
+        print(json.dumps({"learner_single_run_c1": measure_c1(torch, q, W)}))
         return
     if args.only_ablation:
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
