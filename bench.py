@@ -360,6 +360,7 @@ def measure_training(torch, q, W, n_runs=512, steps=20, prefill=20):
     updates, persistent batched launch vs the plain one-run-per-launch form."""
     res = {}
     widths, batches = (32, 64, 128), (128, 256, 512)
+    cluster = 1
     for mode in ("persistent", "plain"):
         runs, envs = [], []
         flops = 0.0
@@ -372,7 +373,7 @@ def measure_training(torch, q, W, n_runs=512, steps=20, prefill=20):
             h = q.qsim_create(cfg, q.make_params(d))
             hp = dict(W.TD3)
             hp.update(hidden=hid, batch=B)
-            a = q.ac_create(q.make_ac_config(hp, cluster=1), h)
+            a = q.ac_create(q.make_ac_config(hp, cluster=cluster), h)
             runs.append(a)
             envs.append(h)
             da, dc = 82, 90
@@ -382,6 +383,9 @@ def measure_training(torch, q, W, n_runs=512, steps=20, prefill=20):
         q.ac_train(runs, envs, prefill, persistent=1)  # fills buffers past the history window
         torch.cuda.synchronize()
         if mode == "persistent":
+            # the autotuner picks the CTAs per run; the plain form then uses the same size
+            cluster = q.ac_train_autotune(runs, envs, 4)
+            torch.cuda.synchronize()
             plan = q.ac_plan_create(runs, envs, steps)  # persistent launch captured in a graph
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -401,7 +405,7 @@ def measure_training(torch, q, W, n_runs=512, steps=20, prefill=20):
             q.qsim_destroy(h)
     res["speedup_vs_plain"] = res["plain"]["s"] / res["persistent"]["s"]
     res["config"] = {"runs": n_runs, "steps_per_run": steps, "envs_per_run": 8,
-                     "updates_per_step": 1}
+                     "updates_per_step": 1, "cluster_autotuned": cluster}
     return res
 
 
@@ -414,6 +418,7 @@ def measure_c1(torch, q, W, steps=2000):
     hp = dict(W.TD3)
     a = q.ac_create(q.make_ac_config(hp), h)
     q.ac_train([a], [h], 100, persistent=1)
+    cluster = q.ac_train_autotune([a], [h], 20)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     q.ac_train([a], [h], steps, persistent=1)
@@ -422,7 +427,7 @@ def measure_c1(torch, q, W, steps=2000):
     q.ac_destroy(a)
     q.qsim_destroy(h)
     return {"steps": steps, "s": dt, "updates_per_s": steps / dt,
-            "projected_9000_updates_s": 9000 * dt / steps}
+            "projected_9000_updates_s": 9000 * dt / steps, "cluster_autotuned": cluster}
 
 
 def measure_diff(torch, q, W, n=4096, H=200, ckpt=20):

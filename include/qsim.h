@@ -372,6 +372,19 @@ qsim_status ac_update_static(ac_handle* a, qsim_handle* env, int32_t n_updates, 
  * persistent = 0: the same kernel launched per run and per step (the plain form). */
 qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
                      int64_t steps_per_run, int32_t persistent, void* stream);
+
+/* Autotuner of the batched launch: times the persistent ac_train over trial_steps steps
+ * for every cluster size S in {1, 2, 4, 8, 16} (CTAs per run) that divides every run's
+ * batch with at least 16 samples per CTA (S = 1 always qualifies), after one untimed call
+ * with the current setting, with CUDA events on `stream`, and sets every run's cluster
+ * size to the fastest (what ac_config.cluster = S would have chosen).  The trials are real
+ * training steps: every run advances by (1 + number of candidates) x trial_steps steps.
+ * Results depend on S only through the order of the cross-CTA gradient reduction (FP32
+ * rounding); for a fixed S they are reproducible bit for bit.  Returns the chosen S, or a
+ * negative qsim_status (the runs keep their previous setting).  Synchronises the stream.
+ * The paper has no counterpart: it trains one run on a CPU. */
+int32_t ac_train_autotune(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
+                          int32_t trial_steps, void* stream);
 qsim_status ac_sync(ac_handle* a);
 
 /* Graph-captured batched training.  ac_plan_create builds, once, everything ac_train's

@@ -135,6 +135,7 @@ _SIGS = {
     "ac_update": (C.c_int, [P, P, C.c_int32, P]),
     "ac_update_static": (C.c_int, [P, P, C.c_int32, P]),
     "ac_train": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int32, P]),
+    "ac_train_autotune": (C.c_int32, [P, P, C.c_int32, C.c_int32, P]),
     "ac_sync": (C.c_int, [P]),
     "ac_plan_create": (C.c_int, [P, P, C.c_int32, C.c_int32, C.POINTER(P)]),
     "ac_plan_run": (C.c_int, [P, C.c_int32, P]),
@@ -450,6 +451,17 @@ def ac_train(runs, envs, steps_per_run, persistent=1, stream=None):
     ea = (P * n)(*[e.value if isinstance(e, P) else e for e in envs])
     _chk(_lib.ac_train(C.cast(ra, P), C.cast(ea, P), n, steps_per_run, persistent,
                        _stream(stream)))
+
+
+def ac_train_autotune(runs, envs, trial_steps=4, stream=None) -> int:
+    """Time the persistent launch at every admissible cluster size; keep the fastest."""
+    n = len(runs)
+    ra = (P * n)(*[r.value if isinstance(r, P) else r for r in runs])
+    ea = (P * n)(*[e.value if isinstance(e, P) else e for e in envs])
+    r = _lib.ac_train_autotune(C.cast(ra, P), C.cast(ea, P), n, trial_steps, _stream(stream))
+    if r < 0:
+        _chk(r)
+    return r
 
 
 def ac_plan_create(runs, envs, steps_per_chunk):

@@ -1414,6 +1414,58 @@ extern "C" qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs
     return launch_train(A, E, (int)steps_per_run, 1, nS, st, nullptr, max_clusters);
 }
 
+// Autotuner of the batched launch: the cluster size S (CTAs per run) is timed on the runs
+// themselves, every candidate that divides each run's batch with >= 16 samples per CTA.
+extern "C" int32_t ac_train_autotune(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
+                                     int32_t trial_steps, void* stream) {
+    if (!runs || !envs || n_runs < 1 || trial_steps < 1)
+        return fail(QSIM_EINVAL, "ac_train_autotune: bad argument");
+    for (int i = 0; i < n_runs; ++i)
+        if (!runs[i] || !envs[i]) return fail(QSIM_EINVAL, "ac_train_autotune: null handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> saved(n_runs);
+    for (int i = 0; i < n_runs; ++i) saved[i] = runs[i]->cfg.cluster;
+    auto restore = [&]() { for (int i = 0; i < n_runs; ++i) runs[i]->cfg.cluster = saved[i]; };
+    // one untimed call with the current setting: first-launch costs stay out of the trials
+    qsim_status s0 = ac_train(runs, envs, n_runs, trial_steps, 1, stream);
+    if (s0 != QSIM_OK) return s0;
+    cudaEvent_t e0, e1;
+    QCHECK_CUDA(cudaEventCreate(&e0));
+    QCHECK_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_s = 0;
+    for (int cand : {1, 2, 4, 8, 16}) {
+        bool ok = true;
+        for (int i = 0; i < n_runs; ++i) {
+            const int b = runs[i]->batch;
+            if (b % cand || (cand > 1 && b / cand < 16)) ok = false;
+        }
+        if (!ok) continue;
+        for (int i = 0; i < n_runs; ++i) runs[i]->cfg.cluster = cand;
+        cudaEventRecord(e0, st);
+        const qsim_status r = ac_train(runs, envs, n_runs, trial_steps, 1, stream);
+        cudaEventRecord(e1, st);
+        if (r != QSIM_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            restore();
+            return r;
+        }
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_s = cand;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    QCHECK_LAUNCH("ac_train_autotune");
+    for (int i = 0; i < n_runs; ++i) runs[i]->cfg.cluster = best_s;
+    return best_s;
+}
+
 // ------------------------------------------------------------ graph-captured plans
 struct ac_plan {
     std::vector<ac_handle*> A;

@@ -342,3 +342,37 @@ def test_ablation_study_runs_in_one_persistent_launch(gpu):
             assert np.array_equal(x, y), name
         q.ac_destroy(a)
         q.qsim_destroy(h)
+
+
+def test_train_autotune_picks_an_admissible_cluster(gpu):
+    """The batched-launch autotuner times the admissible cluster sizes on the runs themselves
+    (batch 64: 1, 2 and 4 CTAs per run), keeps the fastest, and the runs advance by the trial
+    steps (one untimed call plus one per candidate); training then goes on at that size."""
+    q = gpu
+    runs, envs = [], []
+    for r in range(3):
+        d, cfg, veh = lib_config(q, "c1", n_envs=2, capacity=64, learning_starts=4,
+                                 episode_len=15, seed=r, run_id=r)
+        h = q.qsim_create(cfg, veh)
+        hp = dict(W.TD3)
+        hp.update(hidden=[32, 64, 32][r], batch=64)
+        runs.append(q.ac_create(q.make_ac_config(hp, cluster=0), h))
+        envs.append(h)
+    try:
+        q.ac_train(runs, envs, 10, persistent=1)
+        torch.cuda.synchronize()
+        t0 = [q.qsim_info_get(h)["t_now"] for h in envs]
+        S = q.ac_train_autotune(runs, envs, 3)
+        assert S in (1, 2, 4)
+        assert [q.qsim_info_get(h)["t_now"] for h in envs] == [t + 3 * 4 for t in t0]
+        q.ac_train(runs, envs, 5, persistent=1)
+        torch.cuda.synchronize()
+        for a in runs:
+            ai = q.ac_info_get(a)
+            assert all(bool(torch.isfinite(ai[k]).all()) for k in NETS)
+        with pytest.raises(q.QsimError):
+            q.ac_train_autotune(runs, envs, 0)
+    finally:
+        for a, h in zip(runs, envs):
+            q.ac_destroy(a)
+            q.qsim_destroy(h)
