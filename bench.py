@@ -404,6 +404,9 @@ def measure_training(torch, q, W, n_runs=512, steps=20, prefill=20):
             q.ac_destroy(a)
             q.qsim_destroy(h)
     res["speedup_vs_plain"] = res["plain"]["s"] / res["persistent"]["s"]
+    fp32_peak = device_peaks(torch, q)[2]
+    res["persistent"]["fp32_frac"] = res["persistent"]["tflops"] / fp32_peak
+    res["fp32_peak"] = fp32_peak
     res["config"] = {"runs": n_runs, "steps_per_run": steps, "envs_per_run": 8,
                      "updates_per_step": 1, "cluster_autotuned": cluster}
     return res
