@@ -260,23 +260,32 @@ def measure_track(torch, q, W, fp32_peak, n=65536, steps=1000, hidden=64):
         per = torch.tensor([(15.0, 5.5, 3.5)[i % 3] for i in range(ld)], device="cuda")
         sq = torch.empty((2, ld), dtype=torch.float64, device="cuda")
         ok = torch.empty(ld, dtype=torch.int32, device="cuda")
-        q.qsim_track(h, actor, hidden, 100, per, sq, ok)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 3
-        e0.record()
-        for _ in range(reps):
-            q.qsim_track(h, actor, hidden, steps, per, sq, ok)
-        e1.record()
-        e1.synchronize()
-        q.qsim_sync(h)
-        ms = e0.elapsed_time(e1) / reps
+        # the SIMT kernel first (for comparison), then the default engine (tensor cores)
+        times = {}
+        for engine in (1, -1):
+            q.qsim_rollout_engine(h, engine)
+            q.qsim_track(h, actor, hidden, 100, per, sq, ok)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record()
+            for _ in range(reps):
+                q.qsim_track(h, actor, hidden, steps, per, sq, ok)
+            e1.record()
+            e1.synchronize()
+            q.qsim_sync(h)
+            times[engine] = e0.elapsed_time(e1) / reps
+        ms = times[-1]
         okc = ok[:n].double().cpu()
         sqc = sq[:, :n].cpu()
         res = {"workload": f"{n} envs x {steps} steps, cycle times 15 / 5.5 / 3.5 s",
                "env_steps_per_s": n * steps / (ms * 1e-3), "ms": ms,
-               "fp32_tflops": n * steps * (FLOP_ACTOR(da, hidden) + FLOP_DYN + FLOP_MISC)
-               / (ms * 1e-3) / 1e12, "fp32_peak": fp32_peak, "kernel": "k_rollout<64, 4, 1, 1>"}
+               "fp32_equivalent_tflops": n * steps * (FLOP_ACTOR(da, hidden) + FLOP_DYN + FLOP_MISC)
+               / (ms * 1e-3) / 1e12, "fp32_peak": fp32_peak, "kernel": "k_rollout_tc<true>",
+               "simt_kernel": {"kernel": "k_rollout<64, 4, 1, 1>", "ms": times[1],
+                               "env_steps_per_s": n * steps / (times[1] * 1e-3),
+                               "fp32_frac": n * steps * (FLOP_ACTOR(da, hidden) + FLOP_DYN + FLOP_MISC)
+                               / (times[1] * 1e-3) / 1e12 / fp32_peak}}
         for j, T in enumerate((15.0, 5.5, 3.5)):
             sel = torch.arange(n) % 3 == j
             k = okc[sel]
@@ -285,7 +294,6 @@ def measure_track(torch, q, W, fp32_peak, n=65536, steps=1000, hidden=64):
             res[f"T{T:g}"] = {"mean_steps_completed": float(k.mean()),
                               "flights_completed": float((k == steps).double().mean()),
                               "median_rmse_m": float(rmse.median()) if flown.any() else None}
-        res["fp32_frac"] = res["fp32_tflops"] / fp32_peak
         return res
     finally:
         q.qsim_destroy(h)

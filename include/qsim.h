@@ -223,7 +223,11 @@ qsim_status qsim_rollout(qsim_handle* h, const float* actor, int32_t hidden, int
  * After each step the error e = p - p*(t + dt) is accumulated; a non-finite state or any
  * |e_i| > term_pos (the config's termination box) ends that env's flight, whose error is
  * not counted.  The env set itself (states, counters, replay) is not modified.
- *   actor     device, layout as in qsim_rollout; hidden 32, 64 or 128 (SIMT kernel)
+ *   actor     device, layout as in qsim_rollout; hidden 32, 64 or 128.  Hidden 64 flies on
+ *             the tensor-core kernel (its state in scratch allocated on `stream` with
+ *             cudaMallocAsync for the call) unless qsim_rollout_engine pins engine 0 or 1;
+ *             the other widths, and pinned SIMT engines, on the SIMT kernel.  The two
+ *             engines agree to FP32 rounding, not bitwise.
  *   period    device float [ld]: cycle time T > 0 of each env, s (T <= 0, infinite or NaN
  *             flies no step)
  *   sq_err    device double [2][ld] out: sum of |e|^2 and sum of e_x^2 + e_y^2 over the

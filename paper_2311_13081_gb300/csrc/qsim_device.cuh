@@ -193,6 +193,36 @@ __device__ __forceinline__ void motor_lag_off(const EnvCfg& C, const float* u, f
     }
 }
 
+// Arguments of the trajectory-tracking instantiations of the env-step kernels.
+struct TrackArgs {
+    const float* period;  // [ld] cycle time T of each env's target, s
+    float amp, z0;        // target amplitude A and height
+    float clip_p, clip_v; // observation offsets clipped to +-clip per component
+    double* sq_err;       // [2][ld] out: sums of |e|^2 and e_x^2 + e_y^2
+    int32_t* steps_ok;    // [ld] out: steps completed before the flight ended
+};
+
+// Figure-eight target of Sec. V at step k: p* = (A cos th, (A/2) sin 2 th, z0) with
+// th = 2 pi k dt / T, and its time derivative v*.  The cycle fraction k dt / T is formed in
+// double precision and reduced to [0, 1) before the single-precision sin / cos, so the
+// phase stays exact over long flights.
+__device__ __forceinline__ void lissajous(int k, float dt, float T, float A, float z0, float* pr,
+                                          float* vr) {
+    const double x = (double)k * (double)dt / (double)T;
+    const float f1 = (float)(x - floor(x));
+    const float f2 = (float)(2.0 * x - floor(2.0 * x));
+    float s1, c1, s2, c2;
+    sincospif(2.0f * f1, &s1, &c1);
+    sincospif(2.0f * f2, &s2, &c2);
+    const float aw = A * (6.283185307179586f / T);  // A * 2 pi / T
+    pr[0] = A * c1;
+    pr[1] = 0.5f * A * s2;
+    pr[2] = z0;
+    vr[0] = -aw * s1;
+    vr[1] = aw * c2;
+    vr[2] = 0.0f;
+}
+
 // Rotation matrix of q, row-major.
 __device__ __forceinline__ void rotmat(const float* q, float* R) {
     const float w = q[0], x = q[1], y = q[2], z = q[3];

@@ -58,36 +58,6 @@ __device__ __forceinline__ int wpos(int o) {
     return (r >> 2) * 32 + ty * 4 + (r & 3);
 }
 
-// Arguments of the tracking instantiation.
-struct TrackArgs {
-    const float* period;  // [ld] cycle time T of each env's target, s
-    float amp, z0;        // target amplitude A and height
-    float clip_p, clip_v; // observation offsets clipped to +-clip per component
-    double* sq_err;       // [2][ld] out: sums of |e|^2 and e_x^2 + e_y^2
-    int32_t* steps_ok;    // [ld] out: steps completed before the flight ended
-};
-
-// Figure-eight target of Sec. V at step k: p* = (A cos th, (A/2) sin 2 th, z0) with
-// th = 2 pi k dt / T, and its time derivative v*.  The cycle fraction k dt / T is formed in
-// double precision and reduced to [0, 1) before the single-precision sin / cos, so the
-// phase stays exact over long flights.
-__device__ __forceinline__ void lissajous(int k, float dt, float T, float A, float z0, float* pr,
-                                          float* vr) {
-    const double x = (double)k * (double)dt / (double)T;
-    const float f1 = (float)(x - floor(x));
-    const float f2 = (float)(2.0 * x - floor(2.0 * x));
-    float s1, c1, s2, c2;
-    sincospif(2.0f * f1, &s1, &c1);
-    sincospif(2.0f * f2, &s2, &c2);
-    const float aw = A * (6.283185307179586f / T);  // A * 2 pi / T
-    pr[0] = A * c1;
-    pr[1] = 0.5f * A * s2;
-    pr[2] = z0;
-    vr[0] = -aw * s1;
-    vr[1] = aw * c2;
-    vr[2] = 0.0f;
-}
-
 template <int H, int NW, bool PK, bool TRACK = false>
 __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
                                                      const float* __restrict__ actor, int T,
@@ -640,6 +610,8 @@ static qsim_status ensure_streams(qsim_handle* h) {
 
 qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, uint32_t t0, int64_t head,
                                     float sigma, int w0, int w1, cudaStream_t st, int chunk, int* sched);
+qsim_status launch_track_tc(qsim_handle* h, const float* actor, int T, const TrackArgs& tr, int chunk,
+                            cudaStream_t st);
 int rollout_tc_warps_per_cta();
 
 // Launches T steps of the rollout as `parts` env partitions x chunks of `chunk` steps.
@@ -869,6 +841,10 @@ extern "C" qsim_status qsim_track(qsim_handle* h, const float* actor, int32_t hi
     for (const float* q : ptrs)
         if (reinterpret_cast<uintptr_t>(q) % 4) return fail(QSIM_EINVAL, "qsim_track: misaligned pointer");
     if (reinterpret_cast<uintptr_t>(sq_err) % 8) return fail(QSIM_EINVAL, "qsim_track: misaligned pointer");
+    TrackArgs tr{period, amplitude, z0, clip_p, clip_v, sq_err, steps_ok};
+    // hidden 64 flies on the tensor-core kernel unless the handle pins a SIMT engine
+    if (hidden == 64 && h->rollout_packed != 0 && h->rollout_packed != 1)
+        return launch_track_tc(h, actor, n_steps, tr, kTcChunk, (cudaStream_t)stream);
     constexpr int nw = 4;
     RollFn fn = hidden == 32 ? track_fn<32>() : (hidden == 64 ? track_fn<64>() : track_fn<128>());
     const size_t smem = roll_smem(hidden, nw);
@@ -879,7 +855,6 @@ extern "C" qsim_status qsim_track(qsim_handle* h, const float* actor, int32_t hi
         configured[hi] = true;
     }
     const int warps = h->ld / 32;
-    TrackArgs tr{period, amplitude, z0, clip_p, clip_v, sq_err, steps_ok};
     fn<<<(warps + nw - 1) / nw, nw * 32, smem, (cudaStream_t)stream>>>(
         h->dc, h->p, actor, n_steps, 0u, 0, 0, 0.0f, 0, warps, tr);
     QCHECK_LAUNCH("k_rollout<track>");

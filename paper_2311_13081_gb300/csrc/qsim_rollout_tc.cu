@@ -200,10 +200,16 @@ using namespace tcr;
 // of a group once chunk k-1 of that group has been published (a bounded wait); every unit
 // it waits for was taken earlier by a running CTA, so the wait always ends.  Without
 // `sched`, CTA b runs group b for all T steps.
+// TRACK = true flies the deterministic actor along the figure-eight target of Sec. V
+// instead (qsim_track): the observation's position and velocity are offset by the target's
+// and clipped, the squared tracking error is accumulated, and there is no reward, record
+// or reset; the flight's state, action ring and running sums live in per-call scratch
+// (p) and in tr, carried from unit to unit like the training state.
+template <bool TRACK>
 __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const float* __restrict__ actor,
                                                       int T, uint32_t t0, int64_t head0, int64_t capacity,
                                                       float sigma_in, int warp0, int warp_end,
-                                                      int n_groups, int chunk, int* sched) {
+                                                      int n_groups, int chunk, int* sched, TrackArgs tr) {
     extern __shared__ __align__(1024) unsigned char smb[];
     __half* W1s = reinterpret_cast<__half*>(smb + OFF_W1);
     __half* W2s = reinterpret_cast<__half*>(smb + OFF_W2);
@@ -429,6 +435,25 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
 #pragma unroll
             for (int i = 0; i < 7; ++i) Cr[i] = __ldcg(p.rewardC + i);
             float amax = 0.0f;
+            // tracking: this env's cycle time and the flight's running sums; ep_index holds
+            // the flight's state (1 while it lasts)
+            float Tp = 1.0f;
+            double e3 = 0.0, exy = 0.0;
+            int n_ok = 0;
+            bool alive = false;
+            if constexpr (TRACK) {
+                if (active) {
+                    Tp = __ldcg(tr.period + g);
+                    e3 = __ldcg(tr.sq_err + g);
+                    exy = __ldcg(tr.sq_err + ld + g);
+                    n_ok = __ldcg(tr.steps_ok + g);
+                    alive = ep_index != 0u;
+                }
+                if (!(Tp > 0.0f && isfinite(Tp))) {
+                    Tp = 1.0f;
+                    alive = false;
+                }
+            }
             // action ring: slot (t0 - i) mod 16 holds a_{t0-i} (global history is newest first);
             // slot k = ring columns 2k, 2k + 1 (packed halves), after the 16 observation columns
 #pragma unroll 1
@@ -469,6 +494,15 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     {
                         float o[32];
                         obs_state(s, o);
+                        if constexpr (TRACK) {
+                            float pr[3], vr[3];
+                            lissajous((int)t, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                o[k] = clampf(o[k] - pr[k], -tr.clip_p, tr.clip_p);
+                                o[12 + k] = clampf(o[12 + k] - vr[k], -tr.clip_v, tr.clip_v);
+                            }
+                        }
                         if (C.any_noise) {
                             float nz[18];
                             obs_noise(C, (uint32_t)g, t, nz);
@@ -570,9 +604,26 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 motor_lag_off(C, u, s2);
                 rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
                 const float rw = reward(Cr, s2, a);
-                const bool term = terminated(C, s2);
+                const bool term = !TRACK && terminated(C, s2);
                 const uint32_t ep_after = ep_step + 1;
-                const bool trunc = !term && (int)ep_after >= C.episode_len;
+                const bool trunc = !TRACK && !term && (int)ep_after >= C.episode_len;
+                if constexpr (TRACK) {
+                    // error against the target at the new time; a non-finite state or an error
+                    // outside the termination box ends the flight (the lane then holds its
+                    // last state while its tile finishes the steps)
+                    float pr[3], vr[3];
+                    lissajous((int)t + 1, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+                    const float ex = s2[0] - pr[0], ey = s2[1] - pr[1], ez = s2[2] - pr[2];
+                    const bool crash = !finite_state(s2) || fabsf(ex) > C.term_pos ||
+                                       fabsf(ey) > C.term_pos || fabsf(ez) > C.term_pos;
+                    if (alive && crash) alive = false;
+                    if (alive) {
+                        const double exy2 = (double)ex * ex + (double)ey * ey;
+                        exy += exy2;
+                        e3 += exy2 + (double)ez * ez;
+                        n_ok += 1;
+                    }
+                }
                 // ---------------- transition record (field-major, streaming stores)
                 if (capacity > 0) {
                     if (active) {
@@ -638,8 +689,10 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     ep_step = 0;
                     ep_ret = 0.0f;
                 } else {
+                    if (!TRACK || alive) {
 #pragma unroll
-                    for (int i = 0; i < NS; ++i) s[i] = s2[i];
+                        for (int i = 0; i < NS; ++i) s[i] = s2[i];
+                    }
                     ep_step = ep_after;
                 }
             }
@@ -647,6 +700,14 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
             const bool bad = !(amax < HALF_MAX);  // also catches a NaN that reached an operand
             if (__any_sync(0xffffffffu, bad) && lane == 0 && active && p.status) atomicCAS(p.status, DEV_OK, DEV_RANGE);
 
+            if constexpr (TRACK) {
+                if (active) {
+                    tr.sq_err[g] = e3;
+                    tr.sq_err[ld + g] = exy;
+                    tr.steps_ok[g] = n_ok;
+                }
+                ep_index = alive ? 1u : 0u;
+            }
             // ---- write back (state, parameters, counters, history newest first)
             if (active) {
 #pragma unroll
@@ -714,7 +775,7 @@ qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, u
                                     float sigma, int w0, int w1, cudaStream_t st, int chunk, int* sched) {
     static bool configured = false;
     if (!configured) {
-        QCHECK_CUDA(cudaFuncSetAttribute(k_rollout_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+        QCHECK_CUDA(cudaFuncSetAttribute(k_rollout_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
         configured = true;
     }
     const int groups = (w1 - w0 + NCW - 1) / NCW;
@@ -723,13 +784,97 @@ qsim_status launch_rollout_tc_range(qsim_handle* h, const float* actor, int T, u
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
         QCHECK_CUDA(cudaMemsetAsync(sched, 0, sizeof(int) * (size_t)(1 + groups), st));
         const int grid = std::min(sms, groups);
-        k_rollout_tc<<<grid, NT, SMEM, st>>>(h->dc, h->p, actor, T, t0, head, h->capacity, sigma, w0, w1,
-                                             groups, std::min(chunk, T), sched);
+        k_rollout_tc<false><<<grid, NT, SMEM, st>>>(h->dc, h->p, actor, T, t0, head, h->capacity, sigma, w0, w1,
+                                                    groups, std::min(chunk, T), sched, TrackArgs{});
     } else {
-        k_rollout_tc<<<groups, NT, SMEM, st>>>(h->dc, h->p, actor, T, t0, head, h->capacity, sigma, w0, w1,
-                                               groups, T, nullptr);
+        k_rollout_tc<false><<<groups, NT, SMEM, st>>>(h->dc, h->p, actor, T, t0, head, h->capacity, sigma, w0, w1,
+                                                      groups, T, nullptr, TrackArgs{});
     }
     QCHECK_LAUNCH("k_rollout_tc");
+    return QSIM_OK;
+}
+
+// Start of every flight of a tracking call: on the target with its velocity, level, not
+// rotating, motors at the env's hover speed, empty action history, running sums zero;
+// ep_index = 1 marks a flight with a valid cycle time.
+__global__ void k_track_init(EnvCfg C, EnvPtrs p, TrackArgs tr) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ld = C.ld;
+    if (g >= ld) return;
+    float Tp = tr.period[g];
+    const bool ok = Tp > 0.0f && isfinite(Tp);
+    if (!ok) Tp = 1.0f;
+    float pr[3], vr[3];
+    lissajous(0, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+    const float m = p.prm[g], kf = p.prm[4 * ld + g];
+    const float hover = clampf(sqrtf(m * C.veh.g / (4.0f * kf)), C.veh.rpm_min, C.veh.rpm_max);
+    float s[NS];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        s[i] = pr[i];
+        s[7 + i] = vr[i];
+        s[10 + i] = 0.0f;
+    }
+    s[3] = 1.0f; s[4] = 0.0f; s[5] = 0.0f; s[6] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s[13 + i] = hover;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) p.state[i * ld + g] = s[i];
+    for (int i = 0; i < 4 * HMAX; ++i) p.hist[i * ld + g] = 0.0f;
+    p.ep_index[g] = ok ? 1u : 0u;
+    p.ep_step[g] = 0u; p.n_done[g] = 0u; p.len_sum[g] = 0u;
+    p.ep_ret[g] = 0.0f; p.ret_sum[g] = 0.0f;
+    tr.sq_err[g] = 0.0;
+    tr.sq_err[ld + g] = 0.0;
+    tr.steps_ok[g] = 0;
+}
+
+// Tracking flight of every env on the tensor-core kernel (hidden 64): the flights' states,
+// rings and flags live in scratch allocated on the stream for this call (the env set is
+// only read: its parameters and disturbances are copied), no observation noise, no
+// exploration, no warm-up; persistent schedule in chunks of `chunk` steps.
+qsim_status launch_track_tc(qsim_handle* h, const float* actor, int T, const TrackArgs& tr, int chunk,
+                            cudaStream_t st) {
+    static bool configured = false;
+    if (!configured) {
+        QCHECK_CUDA(cudaFuncSetAttribute(k_rollout_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+        configured = true;
+    }
+    const int ld = h->ld, warps = ld / 32;
+    const int groups = (warps + NCW - 1) / NCW;
+    const size_t n = (size_t)ld;
+    float* scr = nullptr;
+    QCHECK_CUDA(cudaMallocAsync((void**)&scr, sizeof(float) * (n * (NS + 8 + 6 + 4 * HMAX + 6) + 1 + groups), st));
+    EnvPtrs p = h->p;
+    p.state = scr;
+    p.prm = p.state + NS * n;
+    p.dist = p.prm + 8 * n;
+    p.hist = p.dist + 6 * n;
+    p.ep_index = reinterpret_cast<uint32_t*>(p.hist + 4 * HMAX * n);
+    p.ep_step = p.ep_index + n;
+    p.n_done = p.ep_step + n;
+    p.len_sum = p.n_done + n;
+    p.ep_ret = reinterpret_cast<float*>(p.len_sum + n);
+    p.ret_sum = p.ep_ret + n;
+    int* sched = reinterpret_cast<int*>(p.ret_sum + n);  // this call's unit counters
+    p.rec = nullptr;
+    p.side = nullptr;
+    QCHECK_CUDA(cudaMemcpyAsync(p.prm, h->p.prm, sizeof(float) * 8 * n, cudaMemcpyDeviceToDevice, st));
+    QCHECK_CUDA(cudaMemcpyAsync(p.dist, h->p.dist, sizeof(float) * 6 * n, cudaMemcpyDeviceToDevice, st));
+    EnvCfg C = h->dc;
+    C.learning_starts = 0;
+    C.any_noise = 0;
+    k_track_init<<<(ld + 127) / 128, 128, 0, st>>>(C, p, tr);
+    QCHECK_LAUNCH("k_track_init");
+    if (T > 0) {
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        QCHECK_CUDA(cudaMemsetAsync(sched, 0, sizeof(int) * (size_t)(1 + groups), st));
+        k_rollout_tc<true><<<std::min(sms, groups), NT, SMEM, st>>>(C, p, actor, T, 0u, 0, 0, 0.0f, 0, warps,
+                                                                     groups, std::min(chunk, T), sched, tr);
+        QCHECK_LAUNCH("k_rollout_tc<track>");
+    }
+    QCHECK_CUDA(cudaFreeAsync(scr, st));
     return QSIM_OK;
 }
 

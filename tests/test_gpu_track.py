@@ -29,12 +29,15 @@ def hover_actor(d, hidden, seed=3, gain=0.05):
 
 
 def fly(q, n, hidden, steps, periods=PERIODS, sample=None, clip_p=0.2, clip_v=1.0, amp=1.0,
-        z0=0.0, **over):
+        z0=0.0, engine=None, **over):
+    """engine None: the library's choice (tensor cores at hidden 64); 1: the SIMT kernel."""
     kw = dict(dist_f=0.004, dist_tau=2e-6)
     kw.update(over)
     d, cfg, veh = lib_config(q, "c2", n_envs=n, **kw)
     h = q.qsim_create(cfg, veh)
     try:
+        if engine is not None:
+            assert q.qsim_rollout_engine(h, engine) == engine
         info = q.qsim_info_get(h)
         ld = info["ld"]
         per = np.array([periods[i % len(periods)] for i in range(ld)], np.float32)
@@ -82,31 +85,37 @@ def compare(d, sq, ok, ref, periods, steps, what, amp=1.0, z0=0.0):
     assert not bad.any(), (what, np.argwhere(bad)[:3], sq[same][bad][:3], ref["sq_err"][same][bad][:3])
 
 
-@pytest.mark.parametrize("hidden,n", [(64, 300), (32, 97), (128, 130)])
-def test_track_parity(gpu, hidden, n):
-    """Ragged env counts (partial warps and blocks), every actor width, four cycle times
-    (agile 3.5 s to a slowly moving 1000 s target), disturbances on."""
+@pytest.mark.parametrize("hidden,n,engine", [(64, 300, None), (64, 300, 1), (64, 1000, None),
+                                             (32, 97, None), (128, 130, None)])
+def test_track_parity(gpu, hidden, n, engine):
+    """Ragged env counts (partial warps, blocks and 128-env tiles), every actor width, both
+    engines at hidden 64 (tensor cores by default, the SIMT kernel when pinned), four cycle
+    times (agile 3.5 s to a slowly moving 1000 s target), disturbances on."""
     steps = 300
-    d, sq, ok, ref, per = fly(gpu, n, hidden, steps)
+    d, sq, ok, ref, per = fly(gpu, n, hidden, steps, engine=engine)
     compare(d, sq, ok, ref, per, steps, f"track h{hidden} n{n}")
     assert ok.max() >= 100  # some flights last long enough to exercise the history ring
     assert (ok < steps).any()  # and some end
 
 
-def test_track_parity_without_history_and_with_binding_clips(gpu):
+@pytest.mark.parametrize("engine", [None, 1])
+def test_track_parity_without_history_and_with_binding_clips(gpu, engine):
     """18-input actor; tight clips that bind on most steps."""
     steps = 200
-    d, sq, ok, ref, per = fly(gpu, 130, 64, steps, n_hist=0, clip_p=0.02, clip_v=0.05)
+    d, sq, ok, ref, per = fly(gpu, 130, 64, steps, n_hist=0, clip_p=0.02, clip_v=0.05,
+                              engine=engine)
     compare(d, sq, ok, ref, per, steps, "track nh0 clips")
 
 
-def test_track_invalid_periods_and_empty_flight(gpu):
+@pytest.mark.parametrize("engine", [None, 1])
+def test_track_invalid_periods_and_empty_flight(gpu, engine):
     """Periods <= 0, infinite or NaN fly no step; n_steps = 0 writes zeros."""
-    d, sq, ok, ref, _ = fly(gpu, 40, 64, 50, periods=(0.0, -2.0, float("inf"), float("nan"), 5.5))
+    d, sq, ok, ref, _ = fly(gpu, 40, 64, 50, periods=(0.0, -2.0, float("inf"), float("nan"), 5.5),
+                            engine=engine)
     assert np.array_equal(ok, ref["steps_ok"])
     dead = np.arange(40) % 5 != 4
     assert np.all(ok[dead] == 0) and np.all(sq[dead] == 0.0)
-    d, sq, ok, ref, _ = fly(gpu, 40, 64, 0)
+    d, sq, ok, ref, _ = fly(gpu, 40, 64, 0, engine=engine)
     assert np.all(ok == 0) and np.all(sq == 0.0)
 
 
