@@ -39,6 +39,9 @@
 // Every hand-over wait is bounded; on expiry the waiting warp records DEV_TIMEOUT in the
 // status word and raises the CTA's abort flag, every warp leaves its step loop at its next
 // wait, and TMEM is freed on every path.
+// The kernel is a template on TRACK: the training step (false), or the trajectory-tracking
+// flight of qsim_track (true; Sec. V): offset, clipped observation, tracking error instead
+// of reward, no records or resets, the flights' state in per-call scratch.
 #include <cuda_fp16.h>
 
 #include <algorithm>
