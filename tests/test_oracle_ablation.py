@@ -102,3 +102,41 @@ def test_symmetric_critic_is_the_history_critic_without_motor_speeds(noise):
         # the updated critics agree too, column for column
         assert np.allclose(_strip_rpm_columns(Lh["c1"], dch, da, H), Ls["c1"], rtol=1e-10,
                            atol=1e-13)
+
+
+def test_ablation_presets_remove_one_component_each():
+    """The ten variants of the study: each differs from the full method in exactly the
+    component it names (the last in two)."""
+    full, fcur, frec = W.ablation("all_components")
+    assert set(W.ABLATIONS) == {"all_components", "observation_noise", "reward_recalculation",
+                                "exploration_noise_decay", "disturbances",
+                                "asymmetric_actor_critic", "action_history", "curriculum",
+                                "rotor_delay", "aac_and_curriculum"}
+    assert frec == 1 and full["critic_layout"] == 0 and full["n_hist"] == 16
+    assert full["motor_lag_off"] == 0 and full["dist_f"] > 0 and full["sig_p"] > 0
+    assert fcur["factor"][4] > 1.0 and fcur["sigma_factor"] < 1.0
+
+    def diff(name):
+        c, cur, rec = W.ablation(name)
+        keys = {k for k in full if c.get(k) != full[k]}
+        if rec != frec:
+            keys.add("recalc_rewards")
+        if cur["factor"] != fcur["factor"] or cur["target"] != fcur["target"]:
+            keys.add("curriculum")
+        if cur["sigma_factor"] != fcur["sigma_factor"]:
+            keys.add("sigma_factor")
+        return keys
+
+    assert diff("all_components") == set()
+    assert diff("observation_noise") == {"sig_p", "sig_R", "sig_v", "sig_w"}
+    assert diff("reward_recalculation") == {"recalc_rewards"}
+    assert diff("exploration_noise_decay") == {"sigma_factor"}
+    assert diff("disturbances") == {"dist_f", "dist_tau"}
+    assert diff("asymmetric_actor_critic") == {"critic_layout"}
+    assert diff("action_history") == {"n_hist"}
+    assert diff("curriculum") == {"curriculum"}
+    assert diff("rotor_delay") == {"motor_lag_off"}
+    assert diff("aac_and_curriculum") == {"critic_layout", "curriculum"}
+    # without the curriculum the reward constants stay at their start values
+    _, cur, _ = W.ablation("curriculum")
+    assert cur["factor"] == [1.0] * 7 and cur["target"] == list(W.REWARD)
