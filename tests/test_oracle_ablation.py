@@ -2,9 +2,10 @@
 off ("rotor delay" removed) and the symmetric critic (asymmetric actor-critic removed).
 
 The other ablations of the study are configuration values whose effect the existing pins
-already cover (no action history: n_hist 0; no curriculum: interval 0; no reward
-recalculation: recalc off; no disturbances / observation noise: zero scales; no
-exploration-noise decay: factor 1).
+already cover (no action history: n_hist 0; no curriculum: reward factors 1 with the
+exploration decay kept; no reward recalculation: recalc off; no disturbances /
+observation noise: zero scales; no exploration-noise decay: sigma factor 1); the last test
+pins that each preset changes only its component.
 """
 import copy
 
