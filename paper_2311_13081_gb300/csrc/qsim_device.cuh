@@ -203,23 +203,32 @@ struct TrackArgs {
 };
 
 // Figure-eight target of Sec. V at step k: p* = (A cos th, (A/2) sin 2 th, z0) with
-// th = 2 pi k dt / T, and its time derivative v*.  The cycle fraction k dt / T is formed in
-// double precision and reduced to [0, 1) before the single-precision sin / cos, so the
-// phase stays exact over long flights.
-__device__ __forceinline__ void lissajous(int k, float dt, float T, float A, float z0, float* pr,
+// th = 2 pi k dt / T, and its time derivative v*.  Per env the cycles per step dt / T
+// (double) and the velocity scale A 2 pi / T are formed once; per step the cycle fraction
+// k dt / T is one double product reduced to [0, 1) before the single-precision sin / cos,
+// so the phase stays exact over long flights.
+struct Target {
+    double cyc;  // dt / T
+    float aw;    // A 2 pi / T
+};
+
+__device__ __forceinline__ Target make_target(float dt, float T, float A) {
+    return Target{(double)dt / (double)T, A * (6.283185307179586f / T)};
+}
+
+__device__ __forceinline__ void lissajous(int k, const Target& tg, float A, float z0, float* pr,
                                           float* vr) {
-    const double x = (double)k * (double)dt / (double)T;
+    const double x = (double)k * tg.cyc;
     const float f1 = (float)(x - floor(x));
     const float f2 = (float)(2.0 * x - floor(2.0 * x));
     float s1, c1, s2, c2;
     sincospif(2.0f * f1, &s1, &c1);
     sincospif(2.0f * f2, &s2, &c2);
-    const float aw = A * (6.283185307179586f / T);  // A * 2 pi / T
     pr[0] = A * c1;
     pr[1] = 0.5f * A * s2;
     pr[2] = z0;
-    vr[0] = -aw * s1;
-    vr[1] = aw * c2;
+    vr[0] = -tg.aw * s1;
+    vr[1] = tg.aw * c2;
     vr[2] = 0.0f;
 }
 

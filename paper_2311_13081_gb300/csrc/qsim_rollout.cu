@@ -122,15 +122,16 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
                      p.prm[4 * ld + g], p.prm[5 * ld + g], p.prm[6 * ld + g]);
     // tracking: start on the target with its velocity, level, not rotating, motors at this
     // env's hover speed, empty action history
-    float Tp = 1.0f;
+    Target tg{1.0, 0.0f};
     double e3 = 0.0, exy = 0.0;
     int n_ok = 0;
     bool alive = true;
     if constexpr (TRACK) {
-        Tp = tr.period[g];
+        const float Tp = tr.period[g];
         alive = Tp > 0.0f && isfinite(Tp);
+        tg = make_target(C.dt, alive ? Tp : 1.0f, tr.amp);
         float pr[3], vr[3];
-        lissajous(0, C.dt, alive ? Tp : 1.0f, tr.amp, tr.z0, pr, vr);
+        lissajous(0, tg, tr.amp, tr.z0, pr, vr);
         const float hover = clampf(sqrtf(P.m * C.veh.g / (4.0f * P.kf)), C.veh.rpm_min, C.veh.rpm_max);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
@@ -141,7 +142,6 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
         s[3] = 1.0f; s[4] = 0.0f; s[5] = 0.0f; s[6] = 0.0f;
 #pragma unroll
         for (int i = 0; i < 4; ++i) s[13 + i] = hover;
-        if (!alive) Tp = 1.0f;
     }
     uint32_t ep_index = p.ep_index[g], ep_step = p.ep_step[g];
     uint32_t n_done = p.n_done[g], len_sum = p.len_sum[g];
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
             obs_state(s, o);
             if constexpr (TRACK) {
                 float pr[3], vr[3];
-                lissajous(tt, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+                lissajous(tt, tg, tr.amp, tr.z0, pr, vr);
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     o[k] = clampf(o[k] - pr[k], -tr.clip_p, tr.clip_p);
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
             // outside the training termination box ends the flight (the lane then holds its
             // last state while its warp finishes the steps)
             float pr[3], vr[3];
-            lissajous(tt + 1, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+            lissajous(tt + 1, tg, tr.amp, tr.z0, pr, vr);
             const float ex = s2[0] - pr[0], ey = s2[1] - pr[1], ez = s2[2] - pr[2];
             const bool crash = !finite_state(s2) || fabsf(ex) > C.term_pos ||
                                fabsf(ey) > C.term_pos || fabsf(ez) > C.term_pos;

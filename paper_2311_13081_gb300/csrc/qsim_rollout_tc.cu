@@ -457,6 +457,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     alive = false;
                 }
             }
+            const Target tg = make_target(C.dt, Tp, tr.amp);
             // action ring: slot (t0 - i) mod 16 holds a_{t0-i} (global history is newest first);
             // slot k = ring columns 2k, 2k + 1 (packed halves), after the 16 observation columns
 #pragma unroll 1
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                         obs_state(s, o);
                         if constexpr (TRACK) {
                             float pr[3], vr[3];
-                            lissajous((int)t, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+                            lissajous((int)t, tg, tr.amp, tr.z0, pr, vr);
 #pragma unroll
                             for (int k = 0; k < 3; ++k) {
                                 o[k] = clampf(o[k] - pr[k], -tr.clip_p, tr.clip_p);
@@ -615,7 +616,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     // outside the termination box ends the flight (the lane then holds its
                     // last state while its tile finishes the steps)
                     float pr[3], vr[3];
-                    lissajous((int)t + 1, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+                    lissajous((int)t + 1, tg, tr.amp, tr.z0, pr, vr);
                     const float ex = s2[0] - pr[0], ey = s2[1] - pr[1], ez = s2[2] - pr[2];
                     const bool crash = !finite_state(s2) || fabsf(ex) > C.term_pos ||
                                        fabsf(ey) > C.term_pos || fabsf(ez) > C.term_pos;
@@ -808,7 +809,7 @@ __global__ void k_track_init(EnvCfg C, EnvPtrs p, TrackArgs tr) {
     const bool ok = Tp > 0.0f && isfinite(Tp);
     if (!ok) Tp = 1.0f;
     float pr[3], vr[3];
-    lissajous(0, C.dt, Tp, tr.amp, tr.z0, pr, vr);
+    lissajous(0, make_target(C.dt, Tp, tr.amp), tr.amp, tr.z0, pr, vr);
     const float m = p.prm[g], kf = p.prm[4 * ld + g];
     const float hover = clampf(sqrtf(m * C.veh.g / (4.0f * kf)), C.veh.rpm_min, C.veh.rpm_max);
     float s[NS];
