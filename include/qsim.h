@@ -372,8 +372,10 @@ qsim_status ac_update_static(ac_handle* a, qsim_handle* env, int32_t n_updates, 
  * env step of each run's envs (actor, exploration, dynamics, reward, reset, transition
  * write) followed by updates_per_step updates once the buffer allows sampling, plus the
  * curriculum with reward recalculation when configured.  persistent = 1: one
- * persistent launch per chunk of steps for all runs, captured in a CUDA graph;
- * persistent = 0: the same kernel launched per run and per step (the plain form). */
+ * persistent launch of all the steps for all runs (clusters walk the runs longest first;
+ * ac_plan_* below captures such a launch in a CUDA graph for repeated use);
+ * persistent = 0: the same kernel launched per run and per step (the plain form).  Both
+ * forms give bit-identical results. */
 qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
                      int64_t steps_per_run, int32_t persistent, void* stream);
 
