@@ -316,9 +316,9 @@ typedef struct ac_config {
     float gamma, tau, lr, beta1, beta2, eps;
     float sigma_target;      /* target-policy smoothing std-dev */
     float noise_clip;        /* smoothing noise clip */
-    int32_t cluster;         /* CTAs that cooperate on one update (1..16; 0 = auto: 16 for a
-                                few runs with >= 16 samples per CTA, 1 for 64 runs or more;
-                                ac_train_autotune replaces it by the timed best) */
+    int32_t cluster;         /* CTAs that cooperate on one update (1..16; 0 = auto: 16 for up
+                                to 8 runs, 2 for up to 63, 1 beyond, halved while a CTA would
+                                get < 16 samples; ac_train_autotune sets the timed best) */
     int32_t reserved0;
 } ac_config;
 
