@@ -75,7 +75,7 @@ class Envs(C.Structure):
 
 class RollOut(C.Structure):
     _fields_ = [("rec_s", _P), ("rec_a", _P), ("rec_r", _P), ("rec_flags", _P),
-                ("rec_priv", _P), ("side", _P), ("mu", _P)]
+                ("rec_priv", _P), ("side", _P), ("mu", _P), ("obs", _P)]
 
 
 class Net(C.Structure):
@@ -101,7 +101,8 @@ class Buffer(C.Structure):
 
 
 class TD3Diag(C.Structure):
-    _fields_ = [("idx", _P), ("y", _P), ("q1", _P), ("q2", _P), ("a2", _P), ("g_c1", _P),
+    _fields_ = [("idx", _P), ("y", _P), ("q1", _P), ("q2", _P), ("a2", _P), ("oa", _P),
+                ("oa2", _P), ("oc", _P), ("oc2", _P), ("g_c1", _P),
                 ("g_c2", _P), ("g_a", _P), ("critic_loss", C.c_double),
                 ("actor_loss", C.c_double), ("actor_updated", C.c_int32), ("pad_", C.c_int32)]
 
@@ -350,20 +351,22 @@ def _envs_struct(e):
 
 
 def rollout(cfg, Cvals, e: dict, T: int, t0: int, actor=None, hidden=64, sigma_e=0.0,
-            ext_actions=None, n_threads=1) -> dict:
+            ext_actions=None, n_threads=1, obs=False) -> dict:
     """Advance env set ``e`` (modified in place) by T steps starting at global step t0.
 
     ``ext_actions`` ([T][n][4], normalised) replaces the actor, warm-up and exploration.
-    Returns the transition records ([T][n][...]) and the side slots.
+    Returns the transition records ([T][n][...]) and the side slots; with ``obs`` also the
+    actor observation of every step ([T][n][18 + 4 n_hist], noise included).
     """
     c = make_cfg(cfg)
     st = _envs_struct(e)
     n = st.n
     out = dict(rec_s=np.zeros((T, n, NS)), rec_a=np.zeros((T, n, 4)), rec_r=np.zeros((T, n)),
                rec_flags=np.zeros((T, n), np.uint32), rec_priv=np.zeros((T, n, NPRIV)),
-               side=np.full((T, n, NS), np.nan), mu=np.zeros((T, n, 4)))
+               side=np.full((T, n, NS), np.nan), mu=np.zeros((T, n, 4)),
+               obs=np.zeros((T, n, 18 + 4 * c.n_hist)) if obs else None)
     ro = RollOut(*[_p(out[k]) for k in ("rec_s", "rec_a", "rec_r", "rec_flags", "rec_priv",
-                                        "side", "mu")])
+                                        "side", "mu", "obs")])
     act = None if actor is None else _f64(actor)
     ext = None if ext_actions is None else _f64(ext_actions, (T, n, 4))
     rc = reward_c(Cvals)
@@ -398,9 +401,13 @@ def td3_update(cfg, hyper: dict, L: dict, buf: dict, diag: bool = True) -> dict:
                 int(buf["size"]), int(buf["t_now"]))
     PA = L["actor"].size
     PC = L["c1"].size
+    DA, DC = lib().or_actor_in(C.byref(c)), lib().or_critic_in(C.byref(c))
     dg = dict(idx=np.zeros(B, np.uint32), y=np.zeros(B), q1=np.zeros(B), q2=np.zeros(B),
-              a2=np.zeros((B, 4)), g_c1=np.zeros(PC), g_c2=np.zeros(PC), g_a=np.zeros(PA))
-    ds = TD3Diag(*[_p(dg[k]) for k in ("idx", "y", "q1", "q2", "a2", "g_c1", "g_c2", "g_a")],
+              a2=np.zeros((B, 4)), oa=np.zeros((B, DA)), oa2=np.zeros((B, DA)),
+              oc=np.zeros((B, DC)), oc2=np.zeros((B, DC)), g_c1=np.zeros(PC),
+              g_c2=np.zeros(PC), g_a=np.zeros(PA))
+    ds = TD3Diag(*[_p(dg[k]) for k in ("idx", "y", "q1", "q2", "a2", "oa", "oa2", "oc", "oc2",
+                                       "g_c1", "g_c2", "g_a")],
                  0.0, 0.0, 0, 0)
     rc = lib().or_td3_update(C.byref(c), C.byref(td), C.byref(bs), C.byref(ds))
     if rc != 0:

@@ -462,11 +462,22 @@ static void roll_env(const roll_job* J, int k) {
         uint64_t t = J->t0 + (uint64_t)tt;
         double a[4], mu[4] = {0, 0, 0, 0};
         if (J->ext) {
+            if (J->out->obs) {
+                double noise[18];
+                or_obs_noise(c, env, t, noise);
+                or_obs_actor(c, s, hist, noise, J->out->obs + (size_t)((size_t)tt * n + k) * da);
+            }
             for (int i = 0; i < 4; ++i)
                 a[i] = clampd(J->ext[((size_t)tt * n + k) * 4 + i], -1.0, 1.0);
         } else {
             if ((int64_t)t < (int64_t)c->learning_starts) {
                 /* warm-up: uniform random actions (reading of the TD3 start phase) */
+                if (J->out->obs) {
+                    /* the observation of this step, for callers that record it */
+                    double noise[18];
+                    or_obs_noise(c, env, t, noise);
+                    or_obs_actor(c, s, hist, noise, J->out->obs + (size_t)((size_t)tt * n + k) * da);
+                }
                 uint32_t r[4];
                 draw(c, env, (uint32_t)t, TAG_WARM, 0, r);
                 for (int i = 0; i < 4; ++i) a[i] = 2.0 * or_uniform(r[i]) - 1.0;
@@ -474,6 +485,8 @@ static void roll_env(const roll_job* J, int k) {
                 double noise[18], o[18 + 4 * OR_HMAX];
                 or_obs_noise(c, env, t, noise);
                 or_obs_actor(c, s, hist, noise, o);
+                if (J->out->obs) memcpy(J->out->obs + (size_t)((size_t)tt * n + k) * da, o,
+                                        sizeof(double) * (size_t)da);
                 or_mlp_forward(&actor, J->actor, o, h1, h2, mu, 1);
                 double z[4];
                 for (int sub = 0; sub < 2; ++sub) {
@@ -776,6 +789,12 @@ int or_td3_update(const or_cfg* c, or_td3* L, const or_buffer* b, or_td3_diag* d
             oc2[(size_t)j * DC + DC - 4 + i] = a2;
             if (d && d->a2) d->a2[4 * j + i] = a2;
         }
+    }
+    if (d) {
+        if (d->oa) memcpy(d->oa, oa, sizeof(double) * (size_t)B * DA);
+        if (d->oa2) memcpy(d->oa2, oa2, sizeof(double) * (size_t)B * DA);
+        if (d->oc) memcpy(d->oc, oc, sizeof(double) * (size_t)B * DC);
+        if (d->oc2) memcpy(d->oc2, oc2, sizeof(double) * (size_t)B * DC);
     }
     /* a11: twin target critics, clipped double-Q target; no bootstrap on termination */
     for (int j = 0; j < B; ++j) {

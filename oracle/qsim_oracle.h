@@ -78,6 +78,8 @@ typedef struct or_roll_out {
     double* rec_priv;   /* [T][n][6] */
     double* side;       /* [T][n][17], written where the episode ended */
     double* mu;         /* [T][n][4] deterministic actor output (may be NULL) */
+    double* obs;        /* [T][n][18 + 4 n_hist] actor observation at each step, noise
+                           included, also during warm-up (may be NULL) */
 } or_roll_out;
 
 typedef struct or_net {
@@ -107,6 +109,9 @@ typedef struct or_td3_diag {
     uint32_t* idx;      /* [B] sampled flat index */
     double *y, *q1, *q2;/* [B] */
     double* a2;         /* [B][4] smoothed target action */
+    double *oa, *oa2;   /* [B][18 + 4 n_hist] rebuilt actor observations at s and s' */
+    double *oc, *oc2;   /* [B][critic input] rebuilt critic inputs: o_c with the stored
+                           action, o_c' with the smoothed target action */
     double *g_c1, *g_c2, *g_a; /* gradients of the losses */
     double critic_loss, actor_loss;
     int32_t actor_updated, pad_;
