@@ -185,8 +185,25 @@ qsim_status qsim_destroy(qsim_handle* h);
 qsim_status qsim_info_get(const qsim_handle* h, qsim_info* out);
 /* Overwrite host-side counters (used when teacher-forcing a buffer): t_now, head, size. */
 qsim_status qsim_set_counters(qsim_handle* h, int64_t t_now, int64_t head, int64_t size);
-/* Device status word: QSIM_OK or the first device-side error since the last call. */
+/* Device status word: QSIM_OK or the first device-side error since the last call
+ * (synchronous; clears the word): QSIM_ETIMEOUT when a bounded wait of the tensor-core
+ * rollout ran out, QSIM_ESTATE when it met a value outside the half-precision range or
+ * not finite. */
 qsim_status qsim_sync(qsim_handle* h);
+
+/* Polls a bounded device-side wait of this env set's kernels makes before it gives up:
+ * the tensor-core rollout's hand-over waits between its compute and MMA warps and its
+ * waits for the previous chunk of an env group (1..2^30; 0 restores the default 2^22).
+ * A wait that runs out records QSIM_ETIMEOUT for qsim_sync; every warp of the block then
+ * leaves its step loop, the MMAs already committed are allowed to finish (a separate wait
+ * of the default length), tensor memory is released and the kernel returns, so later
+ * calls run normally.  The env set's contents are then those of a partly completed call
+ * (unspecified, finite if the inputs were), with the counters advanced as for a full
+ * call.  A limit far below the
+ * MMA latency (a few thousand cycles) makes the waits run out on purpose, which is how
+ * the failure path is tested.  Returns the previous limit, or a negative qsim_status.
+ * (No counterpart in the paper.) */
+int32_t qsim_set_wait_limit(qsim_handle* h, int32_t polls);
 
 /* Actor and critic observations of the current states (Sec. IV: o_a = {p, R, v, omega,
  * H} with noise of the current step; o_c privileged and noise-free, except in the
@@ -261,13 +278,13 @@ int32_t qsim_rollout_packed(qsim_handle* h, int32_t packed);  /* engines 0/1 of 
  * results as 0), 2 the tensor-core kernel (hidden = 64 only: the two hidden layers as
  * tcgen05 fp16 MMAs on hi/lo halves of every operand, three products per layer that keep
  * FP32 accuracy, accumulators in tensor memory, 384 envs per block; results agree with 0
- * to FP32 rounding, not bitwise; an actor input or hidden activation of magnitude >= 65504
- * is reported by qsim_sync as QSIM_ESTATE),
+ * to FP32 rounding, not bitwise; an actor weight of W1 or W2, actor input or hidden
+ * activation of magnitude >= 65504 or not finite is reported by qsim_sync as QSIM_ESTATE),
  * -1 automatic (the autotuner's choice once it has run; before that the tensor-core engine
  * at hidden 64 and the paired-FMA SIMT kernel otherwise).  Any other value
  * leaves the setting unchanged.  Returns the setting in effect.  The paper's environment
  * step has no counterpart of this switch: it selects among kernels computing the same step
- * (Sec. III, Eq. 1-4 dynamics, Sec. IV actor). */
+ * (Sec. IV: the quadrotor dynamics and the actor). */
 int32_t qsim_rollout_engine(qsim_handle* h, int32_t engine);
 
 /* Autotuner: times every (warps-per-block, schedule) variant of the rollout kernel that fits
@@ -344,8 +361,27 @@ qsim_status ac_set_counters(ac_handle* a, int64_t t_actor, int64_t t_critic, int
 /* n_updates TD3 updates (the AC UPDATE of the hot path): minibatch sample + gather from
  * `env`'s replay ring, target actor + smoothing, twin target critics, critic regression,
  * Adam on the critics, and every policy_delay-th update the actor gradient through
- * critic 1, Adam on the actor and Polyak averaging of all targets. */
+ * critic 1, Adam on the actor and Polyak averaging of all targets (Sec. IV; TD3).
+ * One launch on a cluster of the learner's single-run size (ac_config.cluster).
+ * Asynchronous: the learner keeps a device workspace (its run descriptor and the
+ * cluster's scratch) between calls, allocated with cudaMalloc on the first call and
+ * whenever a later call needs a larger one, and the host advances its copy of the
+ * counters without reading the device.  Calls on one learner (ac_update, ac_train,
+ * ac_update_static) must be ordered on the GPU: one stream, or streams ordered by events.
+ * The learner and the env set must belong to the current device (else QSIM_EINVAL). */
 qsim_status ac_update(ac_handle* a, qsim_handle* env, int32_t n_updates, void* stream);
+
+/* Debug output of the replay sampler: while idx is non-null (device, batch uint32,
+ * 4-byte aligned), every update writes the flat index k * n_envs + env of each minibatch
+ * sample j (k = time slot counted from the oldest sampled slot) to idx[j], so the latest
+ * update's indices can be compared with the reference sampler bit for bit.  NULL turns
+ * the log off.  Affects launches issued after the call. */
+qsim_status ac_set_index_log(ac_handle* a, uint32_t* idx);
+
+/* Set the learner's cluster size (CTAs per update: 0 = automatic, else a power of two
+ * <= 16), as ac_config.cluster.  Returns the previous setting, or a negative
+ * qsim_status. */
+int32_t ac_set_cluster(ac_handle* a, int32_t cluster);
 
 /* Allocation-free variant of ac_update, for callers that cannot allocate device memory
  * while they run updates -- for example an embedded trainer that reserves all memory up
@@ -361,11 +397,13 @@ qsim_status ac_update(ac_handle* a, qsim_handle* env, int32_t n_updates, void* s
  *  - The call makes no cudaMalloc / cudaFree and calls no allocating library routine.
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call before any
- *    stream capture.
+ *    stream capture.  The address is kept for the life of the process: like every
+ *    handle of this library, it does not survive a cudaDeviceReset.
  *  - Every call shares the one array: calls whose work overlaps on the GPU (other streams,
  *    other threads) race and must be serialised by the caller.  The array keeps the last
  *    call's contents; nothing in it needs to start at zero.
- *  - Synchronises `stream` (the updated counters are read back). */
+ *  - The run descriptor is copied from host stack memory into the array on every call
+ *    (cudaMemcpyAsync from pageable memory). */
 #define QSIM_STATIC_SCRATCH_BYTES (8u << 20)
 #define QSIM_STATIC_DESC_BYTES (4u << 10)
 qsim_status ac_update_static(ac_handle* a, qsim_handle* env, int32_t n_updates, void* stream);
@@ -373,11 +411,19 @@ qsim_status ac_update_static(ac_handle* a, qsim_handle* env, int32_t n_updates, 
 /* Train n_runs independent runs for steps_per_run env steps each: per step, the fused
  * env step of each run's envs (actor, exploration, dynamics, reward, reset, transition
  * write) followed by updates_per_step updates once the buffer allows sampling, plus the
- * curriculum with reward recalculation when configured.  persistent = 1: one
- * persistent launch of all the steps for all runs (clusters walk the runs longest first;
- * ac_plan_* below captures such a launch in a CUDA graph for repeated use);
- * persistent = 0: the same kernel launched per run and per step (the plain form).  Both
- * forms give bit-identical results. */
+ * curriculum with reward recalculation when configured (Sec. IV, Sec. VI).
+ *   persistent = 1: one persistent launch of all the steps for all runs (clusters of the
+ *     size every run shares walk the runs longest first; ac_plan_* below captures such a
+ *     launch in a CUDA graph for repeated use);
+ *   persistent = 0: the plain form: the same kernel launched per run and per step;
+ *   persistent = 2: one launch per run for all of its steps, runs one after another.
+ * Forms 0 and 2 give each run its own single-run cluster size (as ac_update); a single
+ * run with persistent = 1 runs as form 2.  Results are bit-identical between the forms
+ * whenever the cluster sizes agree (e.g. ac_config.cluster set); otherwise they differ in
+ * the order of the cross-CTA gradient sums (FP32 rounding).  Asynchronous for a single
+ * run and in forms 0 and 2 (the learners' workspaces, as ac_update); the multi-run
+ * persistent form allocates its descriptors and scratch on `stream` (cudaMallocAsync,
+ * freed in stream order), without synchronising. */
 qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
                      int64_t steps_per_run, int32_t persistent, void* stream);
 

@@ -363,10 +363,11 @@ def rollout(cfg, Cvals, e: dict, T: int, t0: int, actor=None, hidden=64, sigma_e
     n = st.n
     out = dict(rec_s=np.zeros((T, n, NS)), rec_a=np.zeros((T, n, 4)), rec_r=np.zeros((T, n)),
                rec_flags=np.zeros((T, n), np.uint32), rec_priv=np.zeros((T, n, NPRIV)),
-               side=np.full((T, n, NS), np.nan), mu=np.zeros((T, n, 4)),
-               obs=np.zeros((T, n, 18 + 4 * c.n_hist)) if obs else None)
-    ro = RollOut(*[_p(out[k]) for k in ("rec_s", "rec_a", "rec_r", "rec_flags", "rec_priv",
-                                        "side", "mu", "obs")])
+               side=np.full((T, n, NS), np.nan), mu=np.zeros((T, n, 4)))
+    if obs:
+        out["obs"] = np.zeros((T, n, 18 + 4 * c.n_hist))
+    ro = RollOut(*[_p(out.get(k)) for k in ("rec_s", "rec_a", "rec_r", "rec_flags", "rec_priv",
+                                            "side", "mu", "obs")])
     act = None if actor is None else _f64(actor)
     ext = None if ext_actions is None else _f64(ext_actions, (T, n, 4))
     rc = reward_c(Cvals)

@@ -113,6 +113,7 @@ _SIGS = {
     "qsim_info_get": (C.c_int, [P, C.POINTER(QsimInfo)]),
     "qsim_set_counters": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64]),
     "qsim_sync": (C.c_int, [P]),
+    "qsim_set_wait_limit": (C.c_int32, [P, C.c_int32]),
     "qsim_observe": (C.c_int, [P, P, P, P]),
     "qsim_step": (C.c_int, [P, P, P, P, P, P, P, P]),
     "qsim_rollout": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_float, P]),
@@ -132,6 +133,8 @@ _SIGS = {
     "ac_destroy": (C.c_int, [P]),
     "ac_info_get": (C.c_int, [P, C.POINTER(AcInfo)]),
     "ac_set_counters": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64]),
+    "ac_set_cluster": (C.c_int32, [P, C.c_int32]),
+    "ac_set_index_log": (C.c_int, [P, P]),
     "ac_update": (C.c_int, [P, P, C.c_int32, P]),
     "ac_update_static": (C.c_int, [P, P, C.c_int32, P]),
     "ac_train": (C.c_int, [P, P, C.c_int32, C.c_int64, C.c_int32, P]),
@@ -333,6 +336,15 @@ def qsim_sync(h):
     _chk(_lib.qsim_sync(h))
 
 
+def qsim_set_wait_limit(h, polls) -> int:
+    """Polls of a bounded device-side wait before it gives up (0 = default); returns the
+    previous limit."""
+    r = _lib.qsim_set_wait_limit(h, int(polls))
+    if r < 0:
+        _chk(r)
+    return r
+
+
 def qsim_observe(h, obs_a=None, obs_c=None, stream=None):
     _chk(_lib.qsim_observe(h, _ptr(obs_a), _ptr(obs_c), _stream(stream)))
 
@@ -440,12 +452,30 @@ def ac_update(a, env, n_updates, stream=None):
     _chk(_lib.ac_update(a, env, n_updates, _stream(stream)))
 
 
+def ac_set_cluster(a, cluster) -> int:
+    """Set the learner's cluster size (0 = automatic); returns the previous setting."""
+    r = _lib.ac_set_cluster(a, int(cluster))
+    if r < 0:
+        _chk(r)
+    return r
+
+
+def ac_set_index_log(a, idx):
+    """Log the replay indices of every update into ``idx`` (uint32/int32 cuda tensor of
+    batch elements), or stop logging with ``None``."""
+    if idx is not None:
+        assert idx.is_cuda and idx.dtype in (torch.int32, torch.uint32) and idx.is_contiguous()
+    _chk(_lib.ac_set_index_log(a, None if idx is None else idx.data_ptr()))
+
+
 def ac_update_static(a, env, n_updates, stream=None):
     """ac_update without any device allocation (library-owned static scratch)."""
     _chk(_lib.ac_update_static(a, env, n_updates, _stream(stream)))
 
 
 def ac_train(runs, envs, steps_per_run, persistent=1, stream=None):
+    """persistent 1: all runs in one launch; 0: one launch per run and step (plain form);
+    2: one launch per run for all of its steps, runs one after another."""
     n = len(runs)
     ra = (P * n)(*[r.value if isinstance(r, P) else r for r in runs])
     ea = (P * n)(*[e.value if isinstance(e, P) else e for e in envs])

@@ -40,8 +40,11 @@ struct EnvCfg {
     int no_lag;  // motor model ablated: rotors at the set-point at once
     int obs_dim, cobs_dim, n_priv, F;  // F: floats per transition record
     uint32_t key0, key1, run_id;
+    int wait_limit;  // polls of a bounded device-side wait before it gives up
     int n, ld;
 };
+
+constexpr int DEFAULT_WAIT_LIMIT = 1 << 22;
 
 // Per-env parameters with the reciprocals the derivative needs.
 struct Prm {

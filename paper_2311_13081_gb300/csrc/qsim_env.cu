@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "qsim_internal.h"
+#include "qsim_recalc.cuh"
 
 namespace qsim {
 
@@ -56,6 +57,7 @@ EnvCfg make_env_cfg(const qsim_config& c, const qsim_params& v, int n, int ld) {
     EnvCfg C;
     memset(&C, 0, sizeof(C));
     C.veh = make_vehicle(v);
+    C.wait_limit = DEFAULT_WAIT_LIMIT;
     C.dt = c.dt;
     C.renorm = c.renorm_q;
     C.m0 = v.mass; C.Jx0 = v.J[0]; C.Jy0 = v.J[1]; C.Jz0 = v.J[2];
@@ -302,41 +304,14 @@ __global__ void k_step(EnvCfg C, EnvPtrs p, const float* __restrict__ actions, u
 }
 
 // Reward recalculation over every stored record (HBM streaming: reads s', a, flags,
-// writes r).  One thread per (record, env); s' is the side slot for finished episodes,
-// the next record's s otherwise, and the live state for the newest record.
-__global__ void k_recalc(EnvCfg C, EnvPtrs p, int64_t head, int64_t size, int64_t capacity) {
-    const int ld = C.ld, F = C.F;
-    const int64_t total = size * (int64_t)ld;
+// writes r), four envs of one slot per thread (recalc_range).
+__global__ void __launch_bounds__(256) k_recalc(EnvCfg C, EnvPtrs p, int64_t head, int64_t size,
+                                                int64_t capacity) {
     float Cr[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i) Cr[i] = p.rewardC[i];
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = idx / ld;
-        const int e = (int)(idx - k * ld);
-        if (e >= C.n) continue;
-        int64_t slot = (head - size + k) % capacity;
-        if (slot < 0) slot += capacity;
-        const float* rec = p.rec + (size_t)slot * F * ld;
-        const uint32_t fl = __float_as_uint(rec[22 * ld + e]);
-        float s2[NS], a[4];
-        if (fl & 3u) {
-            const float* sd = p.side + (size_t)slot * NS * ld;
-#pragma unroll
-            for (int i = 0; i < NS; ++i) s2[i] = sd[i * ld + e];
-        } else if (k == size - 1) {
-#pragma unroll
-            for (int i = 0; i < NS; ++i) s2[i] = p.state[i * ld + e];
-        } else {
-            const int64_t nx = (slot + 1) % capacity;
-            const float* rn = p.rec + (size_t)nx * F * ld;
-#pragma unroll
-            for (int i = 0; i < NS; ++i) s2[i] = rn[i * ld + e];
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = rec[(17 + i) * ld + e];
-        const_cast<float*>(rec)[21 * ld + e] = reward(Cr, s2, a);
-    }
+    recalc_range(C, p, Cr, head, size, capacity, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                 (uint64_t)gridDim.x * blockDim.x);
 }
 
 __global__ void k_set_reward(float* rewardC, float c0, float c1, float c2, float c3, float c4,
@@ -589,6 +564,14 @@ extern "C" qsim_status qsim_set_counters(qsim_handle* h, int64_t t_now, int64_t 
     return QSIM_OK;
 }
 
+extern "C" int32_t qsim_set_wait_limit(qsim_handle* h, int32_t polls) {
+    if (!h) return fail(QSIM_EINVAL, "qsim_set_wait_limit: null handle");
+    if (polls < 0 || polls > (1 << 30)) return fail(QSIM_EINVAL, "qsim_set_wait_limit: %d polls", polls);
+    const int32_t prev = h->dc.wait_limit;
+    h->dc.wait_limit = polls == 0 ? DEFAULT_WAIT_LIMIT : polls;
+    return prev;
+}
+
 extern "C" qsim_status qsim_sync(qsim_handle* h) {
     if (!h) return fail(QSIM_EINVAL, "qsim_sync: null handle");
     int st = 0;
@@ -597,8 +580,8 @@ extern "C" qsim_status qsim_sync(qsim_handle* h) {
         cudaMemset(h->p.status, 0, 4);
         if (st == DEV_TIMEOUT) return fail(QSIM_ETIMEOUT, "device-side wait ran out");
         if (st == DEV_RANGE)
-            return fail(QSIM_ESTATE, "tensor-core rollout: an actor input or hidden activation "
-                                     "exceeded the half-precision range (|x| >= 65504)");
+            return fail(QSIM_ESTATE, "tensor-core rollout: an actor weight, input or hidden activation "
+                                     "was outside the half-precision range (|x| >= 65504) or not finite");
         return fail(QSIM_ESTATE, "device reported status %d", st);
     }
     return QSIM_OK;
@@ -633,7 +616,8 @@ extern "C" qsim_status qsim_step(qsim_handle* h, const float* actions, float* ob
 extern "C" qsim_status qsim_recalc_rewards(qsim_handle* h, void* stream) {
     if (!h) return fail(QSIM_EINVAL, "qsim_recalc_rewards: null handle");
     if (h->capacity == 0 || h->size == 0) return QSIM_OK;
-    const int64_t total = h->size * (int64_t)h->ld;
+    const int64_t total = h->size * (int64_t)((h->n + 3) / 4);  // quads of four envs
+    if (total >= (int64_t)1 << 32) return fail(QSIM_EINVAL, "qsim_recalc_rewards: ring too large");
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device);
     const int64_t want = (total + 255) / 256;

@@ -70,8 +70,7 @@ struct ac_handle {
     float *actor, *actor_t, *c1, *c1_t, *c2, *c2_t;
     float *m_a, *v_a, *m_c1, *v_c1, *m_c2, *v_c2;
     float* stats;     // [4]
-    float* scratch;   // per-CTA learner scratch
-    size_t scratch_floats_per_cta;
-    int scratch_ctas;
+    void* cache;      // device workspace + host copy of its descriptor for single-run launches
+    uint32_t* idx_log;  // optional [batch] device log of the latest update's replay indices
     int* status;
 };

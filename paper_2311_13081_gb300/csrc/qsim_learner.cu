@@ -26,6 +26,7 @@
 #include "qsim_gemm.cuh"
 #include "qsim_smlp.cuh"
 #include "qsim_internal.h"
+#include "qsim_recalc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -58,7 +59,7 @@ struct RunDesc {
     int64_t t_a, t_c, u;
     int64_t start_updates;
     LearnHyper hp;
-    float* scratch_extra;  // unused, keeps the struct 16-byte multiple
+    uint32_t* idx_log;  // [B] flat replay indices of the latest update, or null
 };
 
 // Forward of in -> H (ReLU) -> H (ReLU) -> out (tanh or linear) for M rows of X [M][ldx].
@@ -410,11 +411,6 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
 }
 
 // ------------------------------------------------------------------------- TD3 update
-__device__ __forceinline__ int64_t pmod64(int64_t a, int64_t m) {
-    const int64_t r = a % m;
-    return r < 0 ? r + m : r;
-}
-
 // Ring index a mod m for a in [-m, 2m).
 __device__ __forceinline__ int64_t ring(int64_t a, int64_t m) {
     return a < 0 ? a + m : (a >= m ? a - m : a);
@@ -446,6 +442,7 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
         const uint4 rr = draw(C, (uint32_t)j >> 2, u, TAG_REPLAY, 0);
         const uint32_t x = (j & 3) == 0 ? rr.x : ((j & 3) == 1 ? rr.y : ((j & 3) == 2 ? rr.z : rr.w));
         const uint32_t idx = (uint32_t)(((uint64_t)x * (uint64_t)nvalid) >> 32);
+        if (w == 0 && R.idx_log) R.idx_log[j] = idx;
         const int64_t k = idx / (uint32_t)NE;
         const int env = (int)(idx % (uint32_t)NE);
         const int64_t slot = ring(head - size + lost + k, CAP);
@@ -898,29 +895,10 @@ __device__ __noinline__ void curriculum_step(RunDesc& R, int64_t head, int64_t s
     }
     cluster_sync_all(nS);
     if (!R.recalc || R.capacity == 0) return;
-    const EnvCfg& C = R.C;
-    const int ld = C.ld, F = C.F;
     float Cr[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i) Cr[i] = ldcg(R.E.rewardC + i);
-    const int64_t total = size * (int64_t)R.n_env;
-    for (int64_t idx = (int64_t)rk * LT + threadIdx.x; idx < total; idx += (int64_t)nS * LT) {
-        const int64_t k = idx / R.n_env;
-        const int e = (int)(idx - k * R.n_env);
-        const int64_t slot = pmod64(head - size + k, R.capacity);
-        float* rec = R.E.rec + (size_t)slot * F * ld + e;
-        const uint32_t fl = __float_as_uint(ldcg(rec + 22 * ld));
-        const float* src;
-        if (fl & 3u) src = R.E.side + (size_t)slot * NS * ld + e;
-        else if (k == size - 1) src = R.E.state + e;
-        else src = R.E.rec + (size_t)pmod64(slot + 1, R.capacity) * F * ld + e;
-        float s2[NS], a[4];
-#pragma unroll
-        for (int i = 0; i < NS; ++i) s2[i] = ldcg(src + i * ld);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = ldcg(rec + (17 + i) * ld);
-        rec[21 * ld] = reward(Cr, s2, a);
-    }
+    recalc_range(R.C, R.E, Cr, head, size, R.capacity, (uint64_t)rk * LT + threadIdx.x, (uint64_t)nS * LT);
     cluster_sync_all(nS);
 }
 
@@ -1020,6 +998,7 @@ using namespace qsim;
 // ---------------------------------------------------------------------------- ABI
 static qsim_status fill_desc(ac_handle* a, qsim_handle* e, RunDesc& R) {
     memset(&R, 0, sizeof(R));
+    if (!a || !e) return fail(QSIM_EINVAL, "null handle");
     R.C = e->dc;
     R.E = e->p;
     R.capacity = e->capacity; R.head = e->head; R.size = e->size; R.t_now = e->t_now;
@@ -1039,12 +1018,36 @@ static qsim_status fill_desc(ac_handle* a, qsim_handle* e, RunDesc& R) {
     const ac_config& c = a->cfg;
     R.hp = LearnHyper{c.gamma, c.tau, c.lr, c.beta1, c.beta2, c.eps, c.sigma_target, c.noise_clip,
                       c.policy_delay, c.updates_per_step};
+    R.idx_log = a->idx_log;
     return QSIM_OK;
 }
 
 static void read_back(ac_handle* a, qsim_handle* e, const RunDesc& R) {
     e->head = R.head; e->size = R.size; e->t_now = R.t_now; e->next_curriculum = R.next_curr;
     a->t_actor = R.t_a; a->t_critic = R.t_c; a->updates = R.u;
+}
+
+// Advances the counters of a run descriptor exactly as k_train does over n_iters
+// iterations, so that the host knows them without reading the descriptor back.
+static void advance_desc(RunDesc& R, int64_t n_iters, int do_env) {
+    for (int64_t it = 0; it < n_iters; ++it) {
+        int n_upd = 1;
+        if (do_env) {
+            R.t_now += 1;
+            if (R.capacity > 0) {
+                R.head = R.head + 1 == R.capacity ? 0 : R.head + 1;
+                if (R.size < R.capacity) R.size += 1;
+            }
+            if (R.curr_interval > 0 && R.t_now * (int64_t)R.n_env >= R.next_curr) R.next_curr += R.curr_interval;
+            n_upd = R.t_now >= R.start_updates ? R.hp.updates_per_step : 0;
+        }
+        for (int k = 0; k < n_upd; ++k) {
+            R.t_c += 1;
+            if ((int64_t)((uint32_t)R.u % (uint32_t)R.hp.policy_delay) == (int64_t)(R.hp.policy_delay - 1))
+                R.t_a += 1;
+            R.u += 1;
+        }
+    }
 }
 
 static int pick_cluster(const ac_handle* a, int n_runs) {
@@ -1058,17 +1061,13 @@ static int pick_cluster(const ac_handle* a, int n_runs) {
     return s;
 }
 
-struct TrainPlan {
-    RunDesc* d_runs = nullptr;
-    int* d_order = nullptr;
-    int* d_off = nullptr;
-    float* scratch = nullptr;
-    size_t stride = 0;
-    int n_clusters = 0, nS = 1, grid = 0;
-};
-
 static qsim_status validate_pair(const ac_handle* a, const qsim_handle* e) {
     if (!a || !e) return fail(QSIM_EINVAL, "null handle");
+    int dev = -1;
+    QCHECK_CUDA(cudaGetDevice(&dev));
+    if (dev != a->device || dev != e->device)
+        return fail(QSIM_EINVAL, "the current device (%d) is not the one the learner (%d) and env set (%d) "
+                    "were created on", dev, a->device, e->device);
     if (e->capacity < 2) return fail(QSIM_ESTATE, "env set has no replay buffer");
     if (e->capacity < e->cfg.n_hist + 2)
         return fail(QSIM_EINVAL, "replay capacity %lld must exceed the history length + 1",
@@ -1078,19 +1077,142 @@ static qsim_status validate_pair(const ac_handle* a, const qsim_handle* e) {
     return QSIM_OK;
 }
 
+// Launch geometry of one run by itself: cluster size and per-CTA scratch (floats).
+struct SingleRun {
+    int nS = 1;
+    size_t stride = 0;
+};
+
+// Checks shared by every single-run launch (ac_update, ac_update_static and the plain
+// forms of ac_train).  do_env = 0: n_iters updates from the buffer as it is, which must
+// already allow sampling.
+static qsim_status prepare_single(const ac_handle* a, const qsim_handle* env, int do_env,
+                                  int64_t n_iters, const char* who, SingleRun* out) {
+    qsim_status s = validate_pair(a, env);
+    if (s != QSIM_OK) return s;
+    if (n_iters < 0) return fail(QSIM_EINVAL, "%s: negative count", who);
+    if ((uint64_t)env->capacity * (uint64_t)env->n >= (1ull << 32))
+        return fail(QSIM_EINVAL, "%s: replay buffer exceeds 2^32 transitions", who);
+    if (do_env) {
+        if (((env->t_now + n_iters) >> 32) != 0) return fail(QSIM_ESTATE, "%s: step counter exhausted", who);
+    } else {
+        const int64_t lost = env->size == env->capacity ? env->cfg.n_hist : 0;
+        if (env->size - 1 - lost < 1)
+            return fail(QSIM_ESTATE, "%s: replay buffer too small to sample (size=%lld)", who,
+                        (long long)env->size);
+        if (((a->updates + n_iters) >> 32) != 0) return fail(QSIM_ESTATE, "%s: update counter exhausted", who);
+    }
+    out->nS = pick_cluster(a, 1);
+    if (a->batch % out->nS)
+        return fail(QSIM_EINVAL, "%s: batch %d not divisible by cluster %d", who, a->batch, out->nS);
+    out->stride = scratch_floats(a->batch / out->nS, a->hidden, a->obs_dim, a->critic_in, a->n_actor,
+                                 a->n_critic, env->n);
+    return QSIM_OK;
+}
+
+// Device image of one run's launch: the descriptor and a one-run schedule.
+struct PackedRun {
+    RunDesc run;
+    int order[1];
+    int off[2];
+};
+static_assert(sizeof(PackedRun) <= QSIM_STATIC_DESC_BYTES, "run descriptor exceeds its static area");
+constexpr size_t kPackedBytes = (sizeof(PackedRun) + 255) & ~(size_t)255;
+
+static qsim_status launch_k_train(int grid, int nS, cudaStream_t st, RunDesc* d_runs, const int* d_order,
+                                  const int* d_off, int64_t n_iters, int do_env, float* scratch,
+                                  size_t stride) {
+    if (n_iters > INT32_MAX) return fail(QSIM_EINVAL, "too many steps for one launch");
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(LT);
+    lc.dynamicSmemBytes = learner_smem();
+    lc.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = nS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (nS > 8) QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    QCHECK_CUDA(cudaLaunchKernelEx(&lc, k_train, d_runs, d_order, d_off, (int)n_iters, do_env, scratch,
+                                   stride, nS));
+    return QSIM_OK;
+}
+
+// One run, one launch of n_iters iterations.  desc_dev holds a PackedRun; when `mirror`
+// is given it is the host copy of what desc_dev holds once the stream's earlier work has
+// run, and the descriptor is uploaded only if the handles' state differs from it.
+static qsim_status run_single(ac_handle* a, qsim_handle* env, int64_t n_iters, int do_env,
+                              const SingleRun& L, unsigned char* desc_dev, float* scratch,
+                              RunDesc* mirror, cudaStream_t st) {
+    PackedRun pk;
+    memset(&pk, 0, sizeof(pk));
+    qsim_status s = fill_desc(a, env, pk.run);
+    if (s != QSIM_OK) return s;
+    pk.off[1] = 1;
+    PackedRun* d_pk = reinterpret_cast<PackedRun*>(desc_dev);
+    if (!mirror || memcmp(&pk.run, mirror, sizeof(RunDesc)) != 0) {
+        // pageable source: the copy is staged before the call returns
+        QCHECK_CUDA(cudaMemcpyAsync(d_pk, &pk, sizeof(pk), cudaMemcpyHostToDevice, st));
+    }
+    s = launch_k_train(L.nS, L.nS, st, &d_pk->run, d_pk->order, d_pk->off, n_iters, do_env, scratch, L.stride);
+    if (s != QSIM_OK) {
+        if (mirror) memset(mirror, 0xff, sizeof(RunDesc));  // unknown device state: upload next time
+        return s;
+    }
+    advance_desc(pk.run, n_iters, do_env);
+    read_back(a, env, pk.run);
+    if (mirror) *mirror = pk.run;
+    return QSIM_OK;
+}
+
+// The learner's own workspace for single-run launches: [PackedRun | scratch of the
+// cluster], kept between calls, grown when a launch needs more.
+struct LearnerCache {
+    unsigned char* dev = nullptr;
+    size_t bytes = 0;
+    RunDesc mirror;
+    LearnerCache() { memset(&mirror, 0xff, sizeof(mirror)); }
+};
+
+static qsim_status learner_run(ac_handle* a, qsim_handle* env, int64_t n_iters, int do_env,
+                               const SingleRun& L, cudaStream_t st) {
+    LearnerCache* c = static_cast<LearnerCache*>(a->cache);
+    const size_t need = kPackedBytes + sizeof(float) * L.stride * (size_t)L.nS;
+    if (c->bytes < need) {
+        if (c->dev) {
+            QCHECK_CUDA(cudaStreamSynchronize(st));
+            cudaFree(c->dev);
+            c->dev = nullptr;
+            c->bytes = 0;
+        }
+        if (cudaMalloc((void**)&c->dev, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(QSIM_ENOMEM, "learner workspace of %zu bytes", need);
+        }
+        c->bytes = need;
+        memset(&c->mirror, 0xff, sizeof(RunDesc));
+    }
+    return run_single(a, env, n_iters, do_env, L, c->dev, reinterpret_cast<float*>(c->dev + kPackedBytes),
+                      &c->mirror, st);
+}
+
+// All runs in one persistent launch (clusters walk a longest-processing-time-first list).
 static qsim_status launch_train(std::vector<ac_handle*>& A, std::vector<qsim_handle*>& E,
-                                int n_iters, int do_env, int nS, cudaStream_t st,
-                                std::vector<int>* order_in, int n_clusters_in) {
+                                int64_t n_iters, int do_env, int nS, cudaStream_t st,
+                                int n_clusters_in) {
     const int n = (int)A.size();
     std::vector<RunDesc> D(n);
     size_t stride = 0;
     for (int i = 0; i < n; ++i) {
-        fill_desc(A[i], E[i], D[i]);
+        qsim_status s = fill_desc(A[i], E[i], D[i]);
+        if (s != QSIM_OK) return s;
         if (A[i]->batch % nS) return fail(QSIM_EINVAL, "batch %d not divisible by cluster %d", A[i]->batch, nS);
         stride = std::max(stride, scratch_floats(A[i]->batch / nS, A[i]->hidden, A[i]->obs_dim,
                                                  A[i]->critic_in, A[i]->n_actor, A[i]->n_critic, E[i]->n));
     }
-    // longest-processing-time-first assignment of runs to clusters
     const int n_clusters = std::max(1, std::min(n, n_clusters_in));
     std::vector<int> order(n), off(n_clusters + 1, 0);
     {
@@ -1118,8 +1240,7 @@ static qsim_status launch_train(std::vector<ac_handle*>& A, std::vector<qsim_han
         }
         off[n_clusters] = k;
     }
-    if (order_in) *order_in = order;
-    // device copies (stream-ordered; freed after the launch completes)
+    // device copies (stream-ordered; freed in stream order after the launch)
     RunDesc* d_runs;
     int *d_order, *d_off;
     float* scratch;
@@ -1131,31 +1252,17 @@ static qsim_status launch_train(std::vector<ac_handle*>& A, std::vector<qsim_han
     QCHECK_CUDA(cudaMemcpyAsync(d_runs, D.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, st));
     QCHECK_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
     QCHECK_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (n_clusters + 1), cudaMemcpyHostToDevice, st));
-    QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)learner_smem()));
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(n_clusters * nS);
-    lc.blockDim = dim3(LT);
-    lc.dynamicSmemBytes = learner_smem();
-    lc.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = nS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    lc.attrs = attr;
-    lc.numAttrs = 1;
-    if (nS > 8) QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    QCHECK_CUDA(cudaLaunchKernelEx(&lc, k_train, d_runs, (const int*)d_order, (const int*)d_off,
-                                   n_iters, do_env, scratch, stride, nS));
-    // fetch the advanced counters
-    QCHECK_CUDA(cudaMemcpyAsync(D.data(), d_runs, sizeof(RunDesc) * n, cudaMemcpyDeviceToHost, st));
-    QCHECK_CUDA(cudaFreeAsync(scratch, st));
-    QCHECK_CUDA(cudaFreeAsync(d_off, st));
-    QCHECK_CUDA(cudaFreeAsync(d_order, st));
-    QCHECK_CUDA(cudaFreeAsync(d_runs, st));
-    QCHECK_CUDA(cudaStreamSynchronize(st));
-    for (int i = 0; i < n; ++i) read_back(A[i], E[i], D[i]);
+    qsim_status s = launch_k_train(n_clusters * nS, nS, st, d_runs, d_order, d_off, n_iters, do_env,
+                                   scratch, stride);
+    cudaFreeAsync(scratch, st);
+    cudaFreeAsync(d_off, st);
+    cudaFreeAsync(d_order, st);
+    cudaFreeAsync(d_runs, st);
+    if (s != QSIM_OK) return s;
+    for (int i = 0; i < n; ++i) {
+        advance_desc(D[i], n_iters, do_env);
+        read_back(A[i], E[i], D[i]);
+    }
     return QSIM_OK;
 }
 
@@ -1168,6 +1275,10 @@ extern "C" qsim_status ac_create(const ac_config* cfg, const qsim_handle* env, a
     if (cfg->policy_delay < 1) return fail(QSIM_EINVAL, "ac_create: policy_delay < 1");
     if (cfg->cluster < 0 || cfg->cluster > 16 || (cfg->cluster & (cfg->cluster - 1)))
         return fail(QSIM_EINVAL, "ac_create: cluster must be 0 or a power of two <= 16");
+    int dev = -1;
+    QCHECK_CUDA(cudaGetDevice(&dev));
+    if (dev != env->device)
+        return fail(QSIM_EINVAL, "ac_create: the current device (%d) is not the env set's (%d)", dev, env->device);
     // the learner kernel needs more than the default 48 KB of dynamic shared memory (set on
     // the current device, where every launch for this learner happens)
     QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1175,7 +1286,9 @@ extern "C" qsim_status ac_create(const ac_config* cfg, const qsim_handle* env, a
     ac_handle* a = new ac_handle();
     a->cfg = *cfg;
     if (a->cfg.updates_per_step < 1) a->cfg.updates_per_step = 1;
-    cudaGetDevice(&a->device);
+    a->device = dev;
+    a->cache = new LearnerCache();
+    a->idx_log = nullptr;
     a->obs_dim = env->dc.obs_dim;
     a->critic_in = env->dc.cobs_dim + 4;
     a->hidden = cfg->hidden;
@@ -1217,6 +1330,14 @@ extern "C" qsim_status ac_create(const ac_config* cfg, const qsim_handle* env, a
 
 extern "C" qsim_status ac_destroy(ac_handle* a) {
     if (!a) return QSIM_OK;
+    LearnerCache* c = static_cast<LearnerCache*>(a->cache);
+    if (c) {
+        if (c->dev) {
+            cudaDeviceSynchronize();
+            cudaFree(c->dev);
+        }
+        delete c;
+    }
     if (a->base) cudaFree(a->base);
     if (a->status) cudaFree(a->status);
     delete a;
@@ -1242,20 +1363,27 @@ extern "C" qsim_status ac_set_counters(ac_handle* a, int64_t t_actor, int64_t t_
     return QSIM_OK;
 }
 
+extern "C" int32_t ac_set_cluster(ac_handle* a, int32_t cluster) {
+    if (!a) return fail(QSIM_EINVAL, "ac_set_cluster: null handle");
+    if (cluster < 0 || cluster > 16 || (cluster & (cluster - 1)))
+        return fail(QSIM_EINVAL, "ac_set_cluster: cluster must be 0 or a power of two <= 16");
+    const int32_t prev = a->cfg.cluster;
+    a->cfg.cluster = cluster;
+    return prev;
+}
+
+extern "C" qsim_status ac_set_index_log(ac_handle* a, uint32_t* idx) {
+    if (!a) return fail(QSIM_EINVAL, "ac_set_index_log: null handle");
+    if (reinterpret_cast<uintptr_t>(idx) & 3u) return fail(QSIM_EINVAL, "ac_set_index_log: misaligned pointer");
+    a->idx_log = idx;
+    return QSIM_OK;
+}
+
 extern "C" qsim_status ac_update(ac_handle* a, qsim_handle* env, int32_t n_updates, void* stream) {
-    qsim_status s = validate_pair(a, env);
-    if (s != QSIM_OK) return s;
-    if (n_updates < 0) return fail(QSIM_EINVAL, "ac_update: n_updates < 0");
-    if (n_updates == 0) return QSIM_OK;
-    const int64_t lost = env->size == env->capacity ? env->cfg.n_hist : 0;
-    if (env->size - 1 - lost < 1)
-        return fail(QSIM_ESTATE, "ac_update: replay buffer too small to sample (size=%lld)", (long long)env->size);
-    if ((uint64_t)(env->size - 1 - lost) * (uint64_t)env->n >= (1ull << 32))
-        return fail(QSIM_EINVAL, "ac_update: replay buffer exceeds 2^32 transitions");
-    std::vector<ac_handle*> A{a};
-    std::vector<qsim_handle*> E{env};
-    const int nS = pick_cluster(a, 1);
-    return launch_train(A, E, n_updates, 0, nS, (cudaStream_t)stream, nullptr, 1);
+    SingleRun L;
+    qsim_status s = prepare_single(a, env, 0, n_updates, "ac_update", &L);
+    if (s != QSIM_OK || n_updates == 0) return s;
+    return learner_run(a, env, n_updates, 0, L, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------- allocation-free learner update
@@ -1299,97 +1427,55 @@ qsim_status static_slot(int device, StaticSlot** out) {
 
 extern "C" qsim_status ac_update_static(ac_handle* a, qsim_handle* env, int32_t n_updates,
                                         void* stream) {
-    qsim_status st = validate_pair(a, env);
-    if (st != QSIM_OK) return st;
-    if (n_updates < 0) return fail(QSIM_EINVAL, "ac_update_static: n_updates < 0");
-    if (n_updates == 0) return QSIM_OK;
-    const int64_t lost = env->size == env->capacity ? env->cfg.n_hist : 0;
-    if (env->size - 1 - lost < 1)
-        return fail(QSIM_ESTATE, "ac_update_static: replay buffer too small to sample (size=%lld)",
-                    (long long)env->size);
-    if ((uint64_t)(env->size - 1 - lost) * (uint64_t)env->n >= (1ull << 32))
-        return fail(QSIM_EINVAL, "ac_update_static: replay buffer exceeds 2^32 transitions");
-    const int nS = pick_cluster(a, 1);
-    if (a->batch % nS) return fail(QSIM_EINVAL, "ac_update_static: batch %d not divisible by cluster %d", a->batch, nS);
-    const size_t stride = scratch_floats(a->batch / nS, a->hidden, a->obs_dim, a->critic_in,
-                                         a->n_actor, a->n_critic, env->n);
-    const size_t need = stride * sizeof(float) * (size_t)nS;
+    SingleRun L;
+    qsim_status st = prepare_single(a, env, 0, n_updates, "ac_update_static", &L);
+    if (st != QSIM_OK || n_updates == 0) return st;
+    const size_t need = L.stride * sizeof(float) * (size_t)L.nS;
     if (need > QSIM_STATIC_SCRATCH_BYTES)
         return fail(QSIM_EINVAL,
                     "ac_update_static: needs %zu bytes of scratch (batch %d, hidden %d, cluster %d), "
                     "more than the static maximum of %d bytes; use ac_update",
-                    need, a->batch, a->hidden, nS, (int)QSIM_STATIC_SCRATCH_BYTES);
-    int device = 0;
-    QCHECK_CUDA(cudaGetDevice(&device));
+                    need, a->batch, a->hidden, L.nS, (int)QSIM_STATIC_SCRATCH_BYTES);
     StaticSlot* slot = nullptr;
-    st = static_slot(device, &slot);
+    st = static_slot(a->device, &slot);
     if (st != QSIM_OK) return st;
-    struct Packed {
-        RunDesc run;
-        int order[1];
-        int off[2];
-    };
-    static_assert(sizeof(Packed) <= QSIM_STATIC_DESC_BYTES, "run descriptor exceeds its static area");
-    Packed pk;
-    memset(&pk, 0, sizeof(pk));
-    fill_desc(a, env, pk.run);
-    pk.order[0] = 0;
-    pk.off[0] = 0;
-    pk.off[1] = 1;
-    cudaStream_t cs = (cudaStream_t)stream;
-    Packed* d_pk = reinterpret_cast<Packed*>(slot->desc);
-    QCHECK_CUDA(cudaMemcpyAsync(d_pk, &pk, sizeof(pk), cudaMemcpyHostToDevice, cs));
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3(nS);
-    lc.blockDim = dim3(LT);
-    lc.dynamicSmemBytes = learner_smem();
-    lc.stream = cs;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = nS;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    lc.attrs = attr;
-    lc.numAttrs = 1;
-    if (nS > 8) QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    QCHECK_CUDA(cudaLaunchKernelEx(&lc, k_train, &d_pk->run, (const int*)d_pk->order,
-                                   (const int*)d_pk->off, (int)n_updates, 0, slot->scratch,
-                                   stride, nS));
-    QCHECK_CUDA(cudaMemcpyAsync(&pk, d_pk, sizeof(pk), cudaMemcpyDeviceToHost, cs));
-    QCHECK_CUDA(cudaStreamSynchronize(cs));
-    read_back(a, env, pk.run);
-    return QSIM_OK;
+    // the shared descriptor area is rewritten on every call (no mirror)
+    return run_single(a, env, n_updates, 0, L, slot->desc, slot->scratch, nullptr, (cudaStream_t)stream);
 }
 
 extern "C" qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs, int32_t n_runs,
                                 int64_t steps_per_run, int32_t persistent, void* stream) {
-    if (!runs || !envs || n_runs < 1 || steps_per_run < 0)
+    if (!runs || !envs || n_runs < 1 || steps_per_run < 0 || persistent < 0 || persistent > 2)
         return fail(QSIM_EINVAL, "ac_train: bad argument");
     std::vector<ac_handle*> A(runs, runs + n_runs);
     std::vector<qsim_handle*> E(envs, envs + n_runs);
+    std::vector<SingleRun> L(n_runs);
     for (int i = 0; i < n_runs; ++i) {
-        qsim_status s = validate_pair(A[i], E[i]);
+        qsim_status s = prepare_single(A[i], E[i], 1, steps_per_run, "ac_train", &L[i]);
         if (s != QSIM_OK) return s;
-        if ((uint64_t)E[i]->capacity * (uint64_t)E[i]->n >= (1ull << 32))
-            return fail(QSIM_EINVAL, "ac_train: replay buffer exceeds 2^32 transitions");
-        if (((E[i]->t_now + steps_per_run) >> 32) != 0)
-            return fail(QSIM_ESTATE, "ac_train: step counter exhausted");
     }
     if (steps_per_run == 0) return QSIM_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const int nS = pick_cluster(A[0], n_runs);
-    for (int i = 1; i < n_runs; ++i)
-        if (pick_cluster(A[i], n_runs) != nS) return fail(QSIM_EINVAL, "ac_train: runs need one cluster size");
-    if (!persistent) {
+    if (persistent == 0) {
+        // plain form: one launch per run and env step, each run on its own cluster size
         for (int64_t t = 0; t < steps_per_run; ++t)
             for (int i = 0; i < n_runs; ++i) {
-                std::vector<ac_handle*> a1{A[i]};
-                std::vector<qsim_handle*> e1{E[i]};
-                qsim_status s = launch_train(a1, e1, 1, 1, nS, st, nullptr, 1);
+                qsim_status s = learner_run(A[i], E[i], 1, 1, L[i], st);
                 if (s != QSIM_OK) return s;
             }
         return QSIM_OK;
     }
+    if (persistent == 2 || n_runs == 1) {
+        // one launch per run for all its steps, runs one after another
+        for (int i = 0; i < n_runs; ++i) {
+            qsim_status s = learner_run(A[i], E[i], steps_per_run, 1, L[i], st);
+            if (s != QSIM_OK) return s;
+        }
+        return QSIM_OK;
+    }
+    const int nS = pick_cluster(A[0], n_runs);
+    for (int i = 1; i < n_runs; ++i)
+        if (pick_cluster(A[i], n_runs) != nS) return fail(QSIM_EINVAL, "ac_train: runs need one cluster size");
     int max_clusters = 1;
     {
         cudaLaunchConfig_t lc = {};
@@ -1411,7 +1497,7 @@ extern "C" qsim_status ac_train(ac_handle* const* runs, qsim_handle* const* envs
             max_clusters = std::max(1, sms / nS);
         }
     }
-    return launch_train(A, E, (int)steps_per_run, 1, nS, st, nullptr, max_clusters);
+    return launch_train(A, E, steps_per_run, 1, nS, st, max_clusters);
 }
 
 // Autotuner of the batched launch: the cluster size S (CTAs per run) is timed on the runs
@@ -1542,7 +1628,8 @@ extern "C" qsim_status ac_plan_create(ac_handle* const* runs, qsim_handle* const
     p->n_clusters = std::max(1, std::min(n, max_clusters));
     std::vector<RunDesc> D(n);
     for (int i = 0; i < n; ++i) {
-        fill_desc(p->A[i], p->E[i], D[i]);
+        qsim_status s = fill_desc(p->A[i], p->E[i], D[i]);
+        if (s != QSIM_OK) { ac_plan_destroy(p); return s; }
         p->stride = std::max(p->stride, scratch_floats(p->A[i]->batch / nS, p->A[i]->hidden,
                                                        p->A[i]->obs_dim, p->A[i]->critic_in,
                                                        p->A[i]->n_actor, p->A[i]->n_critic, p->E[i]->n));

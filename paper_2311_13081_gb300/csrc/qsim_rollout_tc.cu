@@ -87,7 +87,9 @@ constexpr int SMEM = OFF_DESC + 8 * (N_DESC1 + N_DESC2);
 static_assert(SMEM <= 227 * 1024, "tensor-core rollout: shared memory");
 static_assert(SZ_W1 % 128 == 0 && OFF_A2 % 128 == 0 && SZ_A2 % 128 == 0, "alignment");
 
-constexpr int WAIT_LIMIT = 1 << 22;  // polls of a hand-over barrier before giving up
+// polls of the wait that lets committed MMAs finish before an aborting CTA frees tensor
+// memory (the hand-over and inter-CTA waits use the env set's run-time limit)
+constexpr int WAIT_LIMIT = 1 << 22;
 constexpr float HALF_MAX = 65504.0f;
 
 // instruction descriptor: D f32, A and B f16, both K-major, N = 64, M = 128
@@ -128,8 +130,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 
 // The whole warp waits (try_wait suspends it in hardware between polls), kept uniform by a
 // vote; false (warp-uniform) when the wait gave up.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
-    for (int i = 0; i < WAIT_LIMIT; ++i) {
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          int limit) {
+    for (int i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
@@ -179,12 +182,19 @@ __device__ __forceinline__ __half2 u2h(uint32_t u) { return *reinterpret_cast<__
 
 // Split a pair (x0, x1) into packed hi and lo halves; amax tracks the largest magnitude
 // (checked against the half-precision range once per launch).
+// max that propagates NaN (fmaxf would drop it), so a non-finite operand reaches the range check
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+    float d;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo, float& amax) {
     const __half2 h = __floats2half2_rn(x0, x1);
     const float2 f = __half22float2(h);
     hi = h2u(h);
     lo = h2u(__floats2half2_rn(x0 - f.x, x1 - f.y));
-    amax = fmaxf(amax, fmaxf(fabsf(x0), fabsf(x1)));
+    amax = fmax_nan(amax, fmax_nan(fabsf(x0), fabsf(x1)));
 }
 
 // Value of a packed hi/lo pair.
@@ -235,6 +245,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
         const float* gb2 = gW2 + H * H;
         const float* gW3 = gb2 + H;
         const float* gb3 = gW3 + 4 * H;
+        bool wbad = false;  // a weight outside the half-precision range (or not finite)
         for (int i = tid; i < 2 * H * KW; i += NT) {
             const int copy = i / (H * KW), j = i - copy * H * KW;  // copy 0: E, 1: O (shifted by 4)
             const int n = j / KW, kk = j - n * KW;
@@ -251,6 +262,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     if (lag <= nh) w = gW1[n * DA + 18 + 4 * (lag - 1) + c];
                 }
             }
+            wbad |= !(fabsf(w) < HALF_MAX);
             const __half hi = __float2half_rn(w);
             __half* base = W1s + (size_t)(2 * copy) * (H * KW);
             base[cano16(n, kk, KC1)] = hi;
@@ -259,6 +271,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
         for (int i = tid; i < H * H; i += NT) {
             const int n = i / H, k = i - n * H;
             const float w = gW2[i];
+            wbad |= !(fabsf(w) < HALF_MAX);
             const __half hi = __float2half_rn(w);
             W2s[cano16(n, k, KC2)] = hi;
             W2s[H * H + cano16(n, k, KC2)] = __float2half_rn(w - __half2float(hi));
@@ -271,6 +284,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     reinterpret_cast<float2*>(smb + OFF_W3)[4 * i + o] = make_float2(gW3[o * H + 2 * i], gW3[o * H + 2 * i + 1]);
         }
         if (tid < 4) sB3[tid] = gb3[tid];
+        if (wbad && p.status) atomicCAS(p.status, DEV_OK, DEV_RANGE);
         if (tid == 0) {
             for (int k = 0; k < TILES; ++k) {
                 const uint32_t b0 = smem_addr(smb + OFF_BAR + 32 * k);
@@ -341,7 +355,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 const int* done = sched + 1 + u % n_groups;
                 const int need = u / n_groups;
                 bool ok = false;
-                for (int i = 0; i < WAIT_LIMIT; ++i) {
+                for (int i = 0; i < C.wait_limit; ++i) {
                     int v;
                     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(done) : "memory");
                     if (v >= need) { ok = true; break; }
@@ -371,7 +385,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
             for (int tt = 0; tt < Tu; ++tt) {
                 const uint32_t t = t0u + (uint32_t)tt;
                 if ((int64_t)t < (int64_t)C.learning_starts) continue;
-                if (!warp_wait(bar_a1, ph, abort_flag, p.status)) break;
+                if (!warp_wait(bar_a1, ph, abort_flag, p.status, C.wait_limit)) break;
                 fence_after();
                 if (lane == 0) {
 #pragma unroll
@@ -388,7 +402,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 }
                 __syncwarp();
                 issued = 1;
-                if (!warp_wait(bar_a2, ph, abort_flag, p.status)) break;
+                if (!warp_wait(bar_a2, ph, abort_flag, p.status, C.wait_limit)) break;
                 fence_after();
                 if (lane == 0) {
 #pragma unroll
@@ -534,7 +548,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                         z[0] = gauss(r0.x, r0.y); z[1] = gauss(r0.z, r0.w);
                         z[2] = gauss(r1.x, r1.y); z[3] = gauss(r1.z, r1.w);
                     }
-                    if (!warp_wait(bar_d1, ph, abort_flag, p.status)) break;
+                    if (!warp_wait(bar_d1, ph, abort_flag, p.status, C.wait_limit)) break;
                     fence_after();
                     // ---------------- epilogue 1: bias, ReLU, split -> A2 (shared memory); hand over
 #pragma unroll 1
@@ -559,7 +573,7 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar_a2);
-                    if (!warp_wait(bar_d2, ph, abort_flag, p.status)) break;
+                    if (!warp_wait(bar_d2, ph, abort_flag, p.status, C.wait_limit)) break;
                     fence_after();
                     ph ^= 1u;
                     // ---------------- epilogue 2 + output layer (64 -> 4), tanh

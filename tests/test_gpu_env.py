@@ -65,6 +65,82 @@ def test_dynamics_step_parity(gpu, n, steps):
     assert_close(f64(out)[:, :n].T, ref, STATE_SCALE, what="state")
 
 
+def _bench_start(d, n):
+    """Initial states of the dynamics benchmark kernel, formed in FP32 as it forms them: a
+    per-env offset off = 1e-3 (e mod 1024) / 1024 on position, roll/yaw rate and the
+    motor speeds around the hover set-point, level attitude, zero velocity."""
+    f32 = np.float32
+    off = (f32(1e-3) * (np.arange(n) % 1024).astype(f32)) / f32(1024)
+    uh = np.sqrt(f32(d["mass"]) * f32(d["g"]) / (f32(4) * f32(d["kf"])))
+    s = np.zeros((n, 17), f32)
+    s[:, 0], s[:, 1], s[:, 2] = off, -off, f32(0.5) * off
+    s[:, 3] = 1
+    s[:, 10], s[:, 12] = off, -off
+    s[:, 13:17] = (uh * (f32(1) + off))[:, None]
+    u = np.full((n, 4), uh, f32)
+    prm = np.zeros((n, 8), f32)
+    prm[:, :7] = [d["mass"], d["Jx"], d["Jy"], d["Jz"], d["kf"], d["km"], d["tm"]]
+    return s.astype(np.float64), u.astype(np.float64), prm.astype(np.float64)
+
+
+def _fp32_config(d):
+    """The vehicle constants as the GPU holds them (FP32), promoted to FP64."""
+    dd = {k: (float(np.float32(v)) if isinstance(v, float) else v) for k, v in d.items()}
+    dd["rotor_pos"] = [float(np.float32(x)) for x in d["rotor_pos"]]
+    dd["rotor_dir"] = [float(np.float32(x)) for x in d["rotor_dir"]]
+    return dd
+
+
+@pytest.mark.parametrize("n,steps", [(8192, 1), (1000, 10), (3000, 100)])
+def test_dynamics_bench_parity(gpu, n, steps):
+    """The kernel timed as the simulator benchmark (Sec. V: forward dynamics only, hover
+    set-point) against the oracle's batch dynamics from the same initial states, element by
+    element at the per-call tolerance.  Up to 100 steps the FP32 rounding accumulated in
+    the hover balance (thrust / mass - g) stays below a fifth of it."""
+    q = gpu
+    d = W.config("c1")
+    veh = q.make_params(d)
+    ld = q.padded(n)
+    out = torch.full((17, ld), float("nan"), device="cuda")
+    q.qsim_dynamics_bench(veh, n, ld, steps, 0.01, out)
+    torch.cuda.synchronize()
+    s, u, prm = _bench_start(d, n)
+    ref = O.dynamics_batch(_fp32_config(d), s, u, prm, None, dt=np.float64(np.float32(0.01)),
+                           renorm=1, n_steps=steps)
+    assert_close(f64(out)[:, :n].T, ref, STATE_SCALE, what=f"bench {steps} steps")
+
+
+def test_dynamics_bench_long_run_invariants(gpu):
+    """1,000 steps (10 s) of the open-loop hover, beyond per-call range: the hover is
+    unstable, so an FP32 rounding of the torque balance (one ulp of a rotor moment,
+    ~1e-10 N m, e.g. from a fused multiply-add that breaks the exact cancellation of the
+    symmetric rotors) grows like g (dtau / J) t^4 / 24 into ~3 cm of horizontal drift over
+    10 s, and the thrust balance (thrust / m - g) accumulates ~5e-4 m in height.  Checked
+    by invariants: finite, unit quaternion, motor speeds settled on the set-point (the lag
+    factor 0.9355 per step leaves < 1e-28 of the initial offset; an FP32 increment below
+    half an ulp rounds away, which can leave the speed up to 7 ulps = 5e-7 relative off the
+    set-point); against the oracle within those drift bounds (height 1e-2 m, horizontal
+    0.1 m, velocity 0.1 m/s)."""
+    q = gpu
+    d = W.config("c1")
+    veh = q.make_params(d)
+    n, steps = 2048, 1000
+    ld = q.padded(n)
+    out = torch.full((17, ld), float("nan"), device="cuda")
+    q.qsim_dynamics_bench(veh, n, ld, steps, 0.01, out)
+    torch.cuda.synchronize()
+    g = f64(out)[:, :n].T
+    s, u, prm = _bench_start(d, n)
+    ref = O.dynamics_batch(_fp32_config(d), s, u, prm, None, dt=np.float64(np.float32(0.01)),
+                           renorm=1, n_steps=steps)
+    assert np.isfinite(g).all()
+    assert np.allclose(np.linalg.norm(g[:, 3:7], axis=1), 1.0, atol=1e-6)
+    assert np.allclose(g[:, 13:17], u, rtol=1e-6, atol=0)
+    assert np.max(np.abs(g[:, 2] - ref[:, 2])) < 1e-2
+    assert np.max(np.abs(g[:, 0:2] - ref[:, 0:2])) < 0.1
+    assert np.max(np.abs(g[:, 7:10] - ref[:, 7:10])) < 0.1
+
+
 def test_dynamics_rejects_bad_arguments(gpu):
     q = gpu
     veh = q.make_params(W.config("c1"))

@@ -85,8 +85,12 @@ def make_run(q, n_env=3, cap=64, hidden=32, batch=64, cluster=1, layout=0, steps
 @pytest.mark.parametrize("cluster,layout,hidden,batch", [(1, 0, 32, 64), (2, 0, 64, 64),
                                                          (4, 1, 32, 128), (1, 2, 16, 32),
                                                          (8, 0, 128, 256), (1, 0, 128, 128),
-                                                         (2, 3, 64, 64)])
+                                                         (2, 3, 64, 64), (16, 0, 64, 256),
+                                                         (1, 0, 128, 512), (0, 1, 64, 256)])
 def test_ac_update_parity(gpu, cluster, layout, hidden, batch):
+    """Cluster 16 at hidden 64 / batch 256 is the single run's automatic choice; hidden 128
+    with batch 512 on one CTA is the largest shape of the batched workload; cluster 0 is
+    the automatic choice with the privileged critic."""
     q = gpu
     d, h, a, hp = make_run(q, hidden=hidden, batch=batch, cluster=cluster, layout=layout)
     try:
@@ -144,15 +148,15 @@ def test_train_iteration_parity(gpu, lag_off, layout):
         q.qsim_destroy(h)
 
 
-def _train_pair(q, persistent, n_runs=3, steps=25):
+def _train_pair(q, persistent, n_runs=3, steps=25, cluster=1):
     runs, envs = [], []
     for r in range(n_runs):
         d, cfg, veh = lib_config(q, "c1", n_envs=2 + r, capacity=40, learning_starts=6,
                                  episode_len=15, seed=r, run_id=r)
         h = q.qsim_create(cfg, veh)
         hp = dict(W.TD3)
-        hp.update(hidden=[32, 64, 16][r % 3], batch=32)
-        a = q.ac_create(q.make_ac_config(hp, cluster=1), h)
+        hp.update(hidden=[32, 64, 16][r % 3], batch=[32, 64, 32][r % 3])
+        a = q.ac_create(q.make_ac_config(hp, cluster=cluster), h)
         runs.append(a)
         envs.append(h)
     q.ac_train(runs, envs, steps, persistent=persistent)
@@ -168,12 +172,80 @@ def _train_pair(q, persistent, n_runs=3, steps=25):
 
 
 def test_plain_and_persistent_training_are_bitwise_equal(gpu):
+    """Same cluster size: the batched launch, one launch per run and step, and one launch
+    per run give the same bits."""
     q = gpu
     s1 = _train_pair(q, persistent=1)
-    s0 = _train_pair(q, persistent=0)
-    for a, b in zip(s1, s0):
+    for form in (0, 2):
+        s0 = _train_pair(q, persistent=form)
+        for a, b in zip(s1, s0):
+            for k in a:
+                assert np.array_equal(a[k].view(np.uint8), b[k].view(np.uint8)), (form, k)
+
+
+def test_plain_forms_use_each_runs_own_cluster(gpu):
+    """Automatic cluster sizes: the two one-run-at-a-time forms give each run its
+    single-run size (2 CTAs for batch 32, 4 for batch 64) and agree bit for bit; split
+    into several calls they continue where they stopped (the learners keep their
+    workspaces and host-side counters between calls)."""
+    q = gpu
+    s0 = _train_pair(q, persistent=0, cluster=0)
+    s2 = _train_pair(q, persistent=2, cluster=0)
+    for a, b in zip(s0, s2):
         for k in a:
             assert np.array_equal(a[k].view(np.uint8), b[k].view(np.uint8)), k
+    # 25 steps as 10 + 1 + 14 in the per-run form
+    runs, envs = [], []
+    for r in range(3):
+        d, cfg, veh = lib_config(q, "c1", n_envs=2 + r, capacity=40, learning_starts=6,
+                                 episode_len=15, seed=r, run_id=r)
+        h = q.qsim_create(cfg, veh)
+        hp = dict(W.TD3)
+        hp.update(hidden=[32, 64, 16][r % 3], batch=[32, 64, 32][r % 3])
+        runs.append(q.ac_create(q.make_ac_config(hp, cluster=0), h))
+        envs.append(h)
+    for steps in (10, 1, 14):
+        q.ac_train(runs, envs, steps, persistent=2)
+    torch.cuda.synchronize()
+    for r, (a, h) in enumerate(zip(runs, envs)):
+        ai, info = q.ac_info_get(a), q.qsim_info_get(h)
+        # updates start once t_now >= max(learning_starts, n_hist + 2) = 18
+        assert ai["updates"] == 25 - 18 + 1 and info["t_now"] == 25
+        for k in NETS:
+            assert np.array_equal(cpu(ai[k]).view(np.uint8), s2[r][k].view(np.uint8)), k
+        for k in ("state", "records"):
+            assert np.array_equal(cpu(info[k]).view(np.uint8), s2[r][k].view(np.uint8)), k
+        q.ac_destroy(a)
+        q.qsim_destroy(h)
+
+
+@pytest.mark.parametrize("cluster,cap,steps", [(4, 64, 40), (2, 24, 60), (1, 200, 30)])
+def test_replay_indices_bit_exact(gpu, cluster, cap, steps):
+    """The sampled flat replay indices of every update equal the oracle sampler's bit for
+    bit (Philox tag 4 words scaled by the number of valid transitions), before and after
+    the ring wraps, on several CTAs of a cluster."""
+    q = gpu
+    d, h, a, hp = make_run(q, hidden=32, batch=128, cluster=cluster, cap=cap, steps=steps)
+    try:
+        idx = torch.zeros(128, dtype=torch.int32, device="cuda")
+        q.ac_set_index_log(a, idx)
+        for call in range(3):
+            info = q.qsim_info_get(h)
+            buf = oracle_buffer(info, info["n_envs"])
+            L = oracle_learner(q.ac_info_get(a))
+            q.ac_update(a, h, 1)
+            torch.cuda.synchronize()
+            dg = O.td3_update(d, hp, L, buf)
+            got = cpu(idx).view(np.uint32)
+            assert np.array_equal(got, dg["idx"]), (call, got[:8], dg["idx"][:8])
+            # one more env step between updates moves the window
+            acts = torch.tensor(W.random_actions(70 + call, (4, info["ld"])),
+                                dtype=torch.float32, device="cuda")
+            q.qsim_step(h, acts)
+        q.ac_set_index_log(a, None)
+    finally:
+        q.ac_destroy(a)
+        q.qsim_destroy(h)
 
 
 def test_curriculum_inside_training(gpu):

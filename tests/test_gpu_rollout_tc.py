@@ -228,3 +228,92 @@ def test_tc_engine_other_widths_run_on_simt(gpu):
         assert q.qsim_rollout_engine(h, 5) == TC
     finally:
         q.qsim_destroy(h)
+
+
+def test_tc_persistent_1000_steps_every_step_teacher_forced(gpu):
+    """The benchmark's call: 65,536 envs x 1,000 steps in one persistent launch of 50-step
+    units (each unit reloads its envs' state and action ring from HBM), observation noise
+    on.  Every step of 256 sampled envs is replayed on the oracle from the GPU's own ring:
+    state s_t from record t, action history from the records of the same episode, the
+    episode's domain-randomised parameters from the oracle's reset of (env, episode); the
+    action, reward, flags and successor state (record t+1, the side slot at episode ends,
+    the final state after the last step) are compared per step.  Termination decisions may
+    differ only where the oracle's successor sits within 1e-5 m of the box edge."""
+    q = gpu
+    n, T = 65536, 1000
+    d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=T, learning_starts=0, sig_p=0.005,
+                             sig_R=0.01, sig_v=0.02, sig_w=0.02)
+    h = q.qsim_create(cfg, veh)
+    try:
+        q.qsim_rollout_engine(h, TC)
+        q.qsim_rollout_schedule(h, 1, 50)
+        actor = _actor(d)
+        A = torch.tensor(actor, device="cuda")
+        ids = np.unique([O.replay_index(int(O.philox([i, 0, 4 << 24, 0], [0, 0])[0]), n)
+                         for i in range(256)])
+        k = ids.size
+        q.qsim_rollout(h, A, 64, T, 0.1)
+        q.qsim_sync(h)
+        info = q.qsim_info_get(h)
+        assert info["t_now"] == T and info["size"] == T
+        idt = torch.tensor(ids, device="cuda")
+        R = info["records"][:, :, idt]
+        rec = f64(R)                                   # [T][F][k]
+        flags = cpu(R).view(np.uint32)[:, 22]          # [T][k]
+        side = f64(info["side"][:, :, idt])            # [T][17][k]
+        final = f64(info["state"][:, idt]).T           # [k][17]
+        del R
+        rs, ra, rr = rec[:, 0:17].transpose(0, 2, 1), rec[:, 17:21].transpose(0, 2, 1), rec[:, 21]
+        resets = {}
+
+        def episode_params(env, ep):
+            if (env, ep) not in resets:
+                resets[(env, ep)] = O.reset_env(d, env, ep)[1:]
+            return resets[(env, ep)]
+
+        ep_index = np.zeros(k, np.uint32)
+        actor64 = actor.astype(np.float64)
+        edge = 0
+        worst = 0.0
+        for t in range(T):
+            ep_step = flags[t] >> 8
+            hist = np.zeros((k, 64))
+            for i in range(1, 17):
+                has = ep_step >= i
+                if t - i >= 0:
+                    hist[has, 4 * (i - 1):4 * i] = ra[t - i][has]
+                else:
+                    assert not has.any()
+            prm = np.array([episode_params(int(e), int(p))[0] for e, p in zip(ids, ep_index)])
+            dist = np.array([episode_params(int(e), int(p))[1] for e, p in zip(ids, ep_index)])
+            e = dict(env_id=ids.astype(np.uint32), s=rs[t].copy(), prm=prm, dist=dist, hist=hist,
+                     ep_index=ep_index.copy(), ep_step=ep_step.astype(np.uint32),
+                     ep_ret=np.zeros(k), n_done=np.zeros(k, np.uint32),
+                     len_sum=np.zeros(k, np.uint32), ret_sum=np.zeros(k))
+            ref = O.rollout(d, W.REWARD, e, 1, t, actor=actor64, hidden=64, sigma_e=0.1)
+            of, gf = ref["rec_flags"][0], flags[t]
+            odone = (of & 3) != 0
+            # successor the oracle computed: side slot if done, else its new state
+            s_ref = np.where(odone[:, None], np.nan_to_num(ref["side"][0]), e["s"])
+            mism = gf != of
+            if mism.any():
+                pos = np.abs(s_ref[mism, 0:3])
+                assert np.all(np.min(np.abs(pos - d["term_pos"]), axis=1) < 1e-5), \
+                    f"step {t}: flags differ away from the box edge: {gf[mism]} vs {of[mism]}"
+                edge += int(mism.sum())
+            ok = ~mism
+            assert_close(ra[t][ok], ref["rec_a"][0][ok], 1.0, what=f"step {t} a")
+            assert_close(rr[t][ok], ref["rec_r"][0][ok], 1.0, what=f"step {t} r")
+            gdone = (gf & 3) != 0
+            if t + 1 < T:
+                s_gpu = np.where(gdone[:, None], side[t].T, rs[t + 1])
+            else:
+                s_gpu = np.where(gdone[:, None], side[t].T, final)
+            sel = ok & ~np.isnan(s_ref).any(axis=1)
+            assert_close(s_gpu[sel], s_ref[sel], STATE_SCALE, what=f"step {t} s'")
+            worst = max(worst, float(np.max(np.abs(ra[t][ok] - ref["rec_a"][0][ok]))))
+            ep_index = ep_index + gdone.astype(np.uint32)
+        assert edge <= 3, edge
+        assert worst < 1e-3
+    finally:
+        q.qsim_destroy(h)
