@@ -311,6 +311,11 @@ qsim_status qsim_mma_probe(int32_t n_mma, int32_t n_cols, int32_t n_warps, int64
 /* Recompute every stored reward from (s', a) with the current reward constants (Sec. VI
  * reward recalculation). */
 qsim_status qsim_recalc_rewards(qsim_handle* h, void* stream);
+/* The same for n env sets (1..65535, all on the current device) in one launch, each with
+ * its own constants; results equal qsim_recalc_rewards on each set.  The launch's set
+ * descriptors are staged in memory allocated on `stream` (cudaMallocAsync, freed in
+ * stream order). */
+qsim_status qsim_recalc_rewards_batch(qsim_handle* const* hs, int32_t n, void* stream);
 /* Set the current reward constants (7 floats) and exploration std-dev (host values). */
 qsim_status qsim_set_reward(qsim_handle* h, const float c[7], float sigma_e, void* stream);
 
@@ -481,7 +486,12 @@ qsim_status ac_load(ac_handle* a, qsim_handle* env, const char* path);
  * workspace (device, 16-byte aligned, qsim_vjp_workspace() bytes, caller-owned) grows with
  * H/ckpt + ckpt, not H.  s0 [17][ld], params [8][ld] (m Jx Jy Jz kf km T_m -). */
 typedef struct qsim_vjp_desc {
-    int32_t n, ld, H, ckpt, mode, n_hist, hidden, reserved0;
+    int32_t n, ld, H, ckpt, mode, n_hist, hidden;
+    int32_t lanes_per_env;  /* closed loop at hidden 32 / 64 with <= 96 actor inputs: lanes
+                               that share one env (32, 16 or 8; 0 = automatic, 8); each
+                               group integrates its env redundantly and splits the actor's
+                               layers over its lanes.  Results agree between settings to FP32
+                               rounding (the order of the group sums differs). */
     float w_p, w_q, w_v, w_a;
     float dt;
     int32_t renorm;

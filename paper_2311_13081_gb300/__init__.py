@@ -91,7 +91,7 @@ class AcInfo(C.Structure):
 class QsimVjpDesc(C.Structure):
     _fields_ = [("n", C.c_int32), ("ld", C.c_int32), ("H", C.c_int32), ("ckpt", C.c_int32),
                 ("mode", C.c_int32), ("n_hist", C.c_int32), ("hidden", C.c_int32),
-                ("reserved0", C.c_int32), ("w_p", C.c_float), ("w_q", C.c_float),
+                ("lanes_per_env", C.c_int32), ("w_p", C.c_float), ("w_q", C.c_float),
                 ("w_v", C.c_float), ("w_a", C.c_float), ("dt", C.c_float),
                 ("renorm", C.c_int32)]
 
@@ -127,6 +127,7 @@ _SIGS = {
     "qsim_ffma_probe": (C.c_int, [C.c_int32, C.c_int32, P, P]),
     "qsim_mma_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P]),
     "qsim_recalc_rewards": (C.c_int, [P, P]),
+    "qsim_recalc_rewards_batch": (C.c_int, [P, C.c_int32, P]),
     "qsim_set_reward": (C.c_int, [P, P, C.c_float, P]),
     "qsim_stats_get": (C.c_int, [P, C.POINTER(QsimStats), P]),
     "ac_create": (C.c_int, [C.POINTER(AcConfig), P, C.POINTER(P)]),
@@ -404,6 +405,13 @@ def qsim_ffma_probe(n_blocks, iters, out, stream=None):
 
 def qsim_recalc_rewards(h, stream=None):
     _chk(_lib.qsim_recalc_rewards(h, _stream(stream)))
+
+
+def qsim_recalc_rewards_batch(hs, stream=None):
+    """Reward recalculation of several env sets in one launch."""
+    n = len(hs)
+    ha = (P * n)(*[h.value if isinstance(h, P) else h for h in hs])
+    _chk(_lib.qsim_recalc_rewards_batch(C.cast(ha, P), n, _stream(stream)))
 
 
 def qsim_set_reward(h, c7, sigma_e, stream=None):

@@ -428,18 +428,21 @@ __global__ void __launch_bounds__(VT) k_vjp_backward(VjpArgs a, int g) {
         for (int i = 0; i < 4; ++i) a.g_params[i * ld + e] = gp[i];
 }
 
-// ------------------------------------------------------------- closed loop, warp per env
+// ------------------------------------------------------- closed loop, lane group per env
 // The thread-per-env kernels above leave the GPU nearly idle at a few thousand envs (one
 // warp per SM) and re-read every activation from memory for each output.  For hidden 32 or
-// 64 (and at most 96 actor inputs) the closed loop runs one env per warp instead: every
-// lane keeps the full state and runs RK4 and its vector-Jacobian product redundantly (no
-// communication), while the actor's layers are split across lanes (lane l owns hidden units
-// l, l+32; inputs l, l+32, l+64), with broadcasts by warp shuffles and the weights in shared
-// memory (odd row strides: conflict-free for lane-varying rows and columns alike).
-// The action history and the history-input adjoints live in per-warp rings of 16 x 4
-// floats in shared memory.  Activation records for the weight gradient are written
-// env-major ([step][env][field]: one contiguous row per env).
-constexpr int WV = 4;  // warps (envs) per CTA of the warp-per-env kernels
+// 64 (and at most 96 actor inputs) the closed loop runs one env per group of LPE lanes
+// instead (LPE = 32, 16 or 8; 32 / LPE envs per warp): every lane of a group keeps the full
+// state and runs RK4 and its vector-Jacobian product redundantly (no communication), while
+// the actor's layers are split across the group's lanes (lane l of the group owns hidden
+// units l + LPE j and inputs l + LPE m), with broadcasts by group-wide shuffles and the
+// weights in shared memory (odd row strides: conflict-free for lane-varying rows and
+// columns alike; the groups of a warp read the same weights, a broadcast).  Narrower groups
+// spend fewer instructions per env on the redundant integration.  The action history and
+// the history-input adjoints live in per-env rings of 16 x 4 floats in shared memory.
+// Activation records for the weight gradient are written env-major ([step][env][field]:
+// one contiguous row per env).
+constexpr int WV = 4;  // warps per CTA of the lane-group kernels
 
 // Weights in shared memory, one copy each with odd row strides so that both orientations
 // are conflict-free: W1 [H][DA+1], W2 [H][H+1] (lane-varying rows in the forward pass,
@@ -483,24 +486,48 @@ __host__ __device__ inline int warp_actor_floats(int DA, int H) {
     return H * (DA + 1) + H * (H + 1) + 2 * H + 4 * H + 4;
 }
 
-// This lane's actor inputs x[m] = input lane + 32 m: the observation of state s (lanes < 18)
-// then the action history a_{t-i} (zero before the rollout starts or beyond n_hist), read
-// through `hist(step, component)`.
-template <class Hist>
-__device__ __forceinline__ void warp_actor_input(const float* s, int t, int DA, int nh, Hist hist, float* x) {
-    const int lane = threadIdx.x & 31;
+// Per-lane shape of the lane-group kernels.
+template <int H, int LPE>
+struct Grp {
+    static constexpr int HPL = H / LPE;               // hidden units per lane
+    static constexpr int NX = (96 + LPE - 1) / LPE;   // actor inputs per lane (at most 96 inputs)
+    static constexpr int G = 32 / LPE;                // envs per warp
+    static_assert(H % LPE == 0 && 32 % LPE == 0, "lane-group shape");
+};
+
+// Value of v[i] for a run-time index i (select chain; v stays in registers).
+template <int N>
+__device__ __forceinline__ float pick(const float* v, int i) {
+    float r = v[0];
+#pragma unroll
+    for (int k = 1; k < N; ++k) r = i == k ? v[k] : r;
+    return r;
+}
+
+template <int LPE>
+__device__ __forceinline__ float grp_sum(float v) {
+#pragma unroll
+    for (int o = LPE / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// This lane's actor inputs x[m] = input (group lane + LPE m): the observation of state s
+// (inputs < 18) then the action history a_{t-i} (zero before the rollout starts or beyond
+// n_hist), read through `hist(step, component)`.
+template <int LPE, int NX, class Hist>
+__device__ __forceinline__ void grp_actor_input(const float* s, int t, int DA, int nh, Hist hist, float* x) {
+    const int gl = threadIdx.x & (LPE - 1);
     float o[18];
     obs_state(s, o);
-    float own = o[0];
 #pragma unroll
-    for (int i = 1; i < 18; ++i) own = lane == i ? o[i] : own;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        const int k = lane + 32 * m;
+    for (int m = 0; m < NX; ++m) {
+        const int k = gl + LPE * m;
         float v = 0.0f;
-        if (k < 18) {
-            v = own;
-        } else if (k < DA) {
+        if (LPE * m < 18) {
+            const float ok = pick<18>(o, k);
+            if (k < 18) v = ok;
+        }
+        if (k >= 18 && k < DA) {
             const int i = ((k - 18) >> 2) + 1, c = (k - 18) & 3;
             if (i <= nh && t - i >= 0) v = hist(t - i, c);
         }
@@ -508,62 +535,73 @@ __device__ __forceinline__ void warp_actor_input(const float* s, int t, int DA, 
     }
 }
 
-__device__ __forceinline__ float warp_sum_all(float v) {
+// Actor forward for this group's env: h1, h2 for the lane's hidden units, mu on every lane.
+template <int H, int LPE>
+__device__ __forceinline__ void grp_actor_fwd(const WarpActor& w, int DA, const float* x, float* h1,
+                                              float* h2, float* mu) {
+    using S = Grp<H, LPE>;
+    const int gl = threadIdx.x & (LPE - 1);
+    float acc[S::HPL];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Actor forward for this warp's env: h1, h2 for the lane's hidden units, mu on every lane.
-template <int HPL>
-__device__ __forceinline__ void warp_actor_fwd(const WarpActor& w, int DA, const float* x, float* h1,
-                                               float* h2, float* mu) {
-    constexpr int H = 32 * HPL;
-    const int lane = threadIdx.x & 31;
-    float acc[HPL];
+    for (int j = 0; j < S::HPL; ++j) acc[j] = w.b1[gl + LPE * j];
 #pragma unroll
-    for (int j = 0; j < HPL; ++j) acc[j] = w.b1[lane + 32 * j];
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        const int kend = min(32, DA - 32 * m);
+    for (int m = 0; m < S::NX; ++m) {
+        const int kend = min(LPE, DA - LPE * m);
         for (int kk = 0; kk < kend; ++kk) {
-            const float xk = __shfl_sync(0xffffffffu, x[m], kk);
-            const float* wr = w.W1 + lane * w.l1 + 32 * m + kk;
+            const float xk = __shfl_sync(0xffffffffu, x[m], kk, LPE);
+            const float* wr = w.W1 + gl * w.l1 + LPE * m + kk;
 #pragma unroll
-            for (int j = 0; j < HPL; ++j) acc[j] = fmaf(wr[32 * j * w.l1], xk, acc[j]);
+            for (int j = 0; j < S::HPL; ++j) acc[j] = fmaf(wr[LPE * j * w.l1], xk, acc[j]);
         }
     }
 #pragma unroll
-    for (int j = 0; j < HPL; ++j) { h1[j] = fmaxf(acc[j], 0.0f); acc[j] = w.b2[lane + 32 * j]; }
+    for (int j = 0; j < S::HPL; ++j) { h1[j] = fmaxf(acc[j], 0.0f); acc[j] = w.b2[gl + LPE * j]; }
 #pragma unroll
-    for (int m = 0; m < HPL; ++m)
-        for (int kk = 0; kk < 32; ++kk) {
-            const float hk = __shfl_sync(0xffffffffu, h1[m], kk);
-            const float* wr = w.W2 + lane * w.l2 + 32 * m + kk;
+    for (int m = 0; m < S::HPL; ++m)
+        for (int kk = 0; kk < LPE; ++kk) {
+            const float hk = __shfl_sync(0xffffffffu, h1[m], kk, LPE);
+            const float* wr = w.W2 + gl * w.l2 + LPE * m + kk;
 #pragma unroll
-            for (int j = 0; j < HPL; ++j) acc[j] = fmaf(wr[32 * j * w.l2], hk, acc[j]);
+            for (int j = 0; j < S::HPL; ++j) acc[j] = fmaf(wr[LPE * j * w.l2], hk, acc[j]);
         }
 #pragma unroll
-    for (int j = 0; j < HPL; ++j) h2[j] = fmaxf(acc[j], 0.0f);
+    for (int j = 0; j < S::HPL; ++j) h2[j] = fmaxf(acc[j], 0.0f);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         float pc = 0.0f;
 #pragma unroll
-        for (int j = 0; j < HPL; ++j) pc = fmaf(w.W3[c * H + lane + 32 * j], h2[j], pc);
-        mu[c] = tanhf(warp_sum_all(pc) + w.b3[c]);
+        for (int j = 0; j < S::HPL; ++j) pc = fmaf(w.W3[c * H + gl + LPE * j], h2[j], pc);
+        mu[c] = tanhf(grp_sum<LPE>(pc) + w.b3[c]);
     }
 }
 
-template <int HPL>
+// Env handled by this lane's group, whether it exists, and whether any group of the warp
+// has an env (warp-uniform).  A group past the last env runs on a valid index (the last
+// env) so that the warp's shuffles stay complete, and stores nothing.
+template <int LPE>
+__device__ __forceinline__ void grp_env(int n, int& e, bool& live, bool& warp_live) {
+    constexpr int G = 32 / LPE;
+    const int warp = threadIdx.x >> 5, sub = (threadIdx.x & 31) / LPE;
+    const int e0 = (blockIdx.x * WV + warp) * G;
+    e = e0 + sub;
+    live = e < n;
+    warp_live = e0 < n;
+    if (!live) e = n - 1;
+}
+
+template <int H, int LPE>
 __global__ void __launch_bounds__(32 * WV) k_vjp_forward_w(VjpArgs a) {
+    using S = Grp<H, LPE>;
     extern __shared__ __align__(16) float sm[];
-    constexpr int H = 32 * HPL;
     const int DA = a.DA, ld = a.ld;
     const WarpActor w = stage_warp_actor(a.actor, DA, H, sm);
-    float* ring = sm + warp_actor_floats(DA, H) + 64 * (threadIdx.x >> 5);  // actions a_tau at (tau & 15)
+    const int gl = threadIdx.x & (LPE - 1);
+    float* ring = sm + warp_actor_floats(DA, H) + 64 * (threadIdx.x / LPE);  // a_tau at (tau & 15)
     __syncthreads();
-    const int e = blockIdx.x * WV + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (e >= a.n) return;  // warp-uniform
+    int e;
+    bool live, warp_live;
+    grp_env<LPE>(a.n, e, live, warp_live);
+    if (!warp_live) return;  // warp-uniform
     float s[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) s[i] = a.s0[i * ld + e];
@@ -573,21 +611,25 @@ __global__ void __launch_bounds__(32 * WV) k_vjp_forward_w(VjpArgs a) {
     const float half = 0.5f * (a.V.rpm_max - a.V.rpm_min);
     float loss = 0.0f;
     for (int t = 0; t < a.H; ++t) {
-        if (t % a.ckpt == 0 && lane < NS) {
-            float v = s[0];
+        if (t % a.ckpt == 0) {
 #pragma unroll
-            for (int i = 1; i < NS; ++i) v = lane == i ? s[i] : v;
-            a.ck[(size_t)(t / a.ckpt) * NS * ld + (size_t)lane * ld + e] = v;
+            for (int r = 0; r < (NS + LPE - 1) / LPE; ++r) {
+                const int i = gl + LPE * r;
+                const float v = pick<NS>(s, i);
+                if (live && i < NS) a.ck[(size_t)(t / a.ckpt) * NS * ld + (size_t)i * ld + e] = v;
+            }
         }
-        float x[3], h1[HPL], h2[HPL], act[4];
-        warp_actor_input(s, t, DA, a.nh, [&](int tau, int c) { return ring[(tau & 15) * 4 + c]; }, x);
-        warp_actor_fwd<HPL>(w, DA, x, h1, h2, act);
+        float x[S::NX], h1[S::HPL], h2[S::HPL], act[4];
+        grp_actor_input<LPE, S::NX>(s, t, DA, a.nh, [&](int tau, int c) { return ring[(tau & 15) * 4 + c]; }, x);
+        grp_actor_fwd<H, LPE>(w, DA, x, h1, h2, act);
         __syncwarp();
-        if (lane < 4) {
-            const float v = lane == 0 ? act[0] : (lane == 1 ? act[1] : (lane == 2 ? act[2] : act[3]));
-            ring[(t & 15) * 4 + lane] = v;
-            a.A[((size_t)t * 4 + lane) * ld + e] = v;
-            if (a.actions_out) a.actions_out[((size_t)t * 4 + lane) * ld + e] = v;
+        if (gl < 4) {
+            const float v = pick<4>(act, gl);
+            ring[(t & 15) * 4 + gl] = v;
+            if (live) {
+                a.A[((size_t)t * 4 + gl) * ld + e] = v;
+                if (a.actions_out) a.actions_out[((size_t)t * 4 + gl) * ld + e] = v;
+            }
         }
         __syncwarp();
         float u[4];
@@ -596,28 +638,28 @@ __global__ void __launch_bounds__(32 * WV) k_vjp_forward_w(VjpArgs a) {
         rk4(a.V, a.dt, a.renorm, s, u, P, d0);
         loss += state_loss(a, s) + a.w_a * (act[0] * act[0] + act[1] * act[1] + act[2] * act[2] + act[3] * act[3]);
     }
-    if (a.loss && lane == 0) a.loss[e] = loss;
+    if (a.loss && gl == 0 && live) a.loss[e] = loss;
 }
 
-// Reverse sweep over segment g, one env per warp.
-template <int HPL>
+// Reverse sweep over segment g, one env per lane group.
+template <int H, int LPE>
 __global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g) {
+    using S = Grp<H, LPE>;
+    constexpr int HPL = S::HPL, NX = S::NX;
     extern __shared__ __align__(16) float sm[];
-    constexpr int H = 32 * HPL;
     const int DA = a.DA, ld = a.ld, nh = a.nh;
     const WarpActor w = stage_warp_actor(a.actor, DA, H, sm);
-    float* adj = sm + warp_actor_floats(DA, H) + 64 * (threadIdx.x >> 5);  // dL/da_tau at (tau & 15)
-    const int e = blockIdx.x * WV + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    const bool live = e < a.n;
+    float* adj = sm + warp_actor_floats(DA, H) + 64 * (threadIdx.x / LPE);  // dL/da_tau at (tau & 15)
+    const int gl = threadIdx.x & (LPE - 1);
+    int e;
+    bool live, warp_live;
+    grp_env<LPE>(a.n, e, live, warp_live);
     const int t0 = g * a.ckpt, t1 = min(a.H, t0 + a.ckpt);
     const bool last = (t1 == a.H);
-    if (live) {
-        // history adjoints carried over from the later segments (zero for the last one)
-        adj[lane] = a.la[(size_t)lane * ld + e];
-        adj[lane + 32] = a.la[(size_t)(lane + 32) * ld + e];
-    }
+    // history adjoints carried over from the later segments (zero for the last one)
+    for (int i = gl; i < 64; i += LPE) adj[i] = live ? a.la[(size_t)i * ld + e] : 0.0f;
     __syncthreads();
-    if (!live) return;  // warp-uniform
+    if (!warp_live) return;  // warp-uniform
     const float seed = a.seed ? a.seed[e] : 1.0f;
     Prm P;
     load_vehicle_prm(a, e, P);
@@ -628,11 +670,11 @@ __global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g)
     for (int i = 0; i < NS; ++i) s[i] = a.ck[(size_t)g * NS * ld + (size_t)i * ld + e];
     for (int t = t0; t < t1; ++t) {
         float* ss = a.segs + (size_t)(t - t0) * NS * ld + e;
-        if (lane < NS) {
-            float v = s[0];
 #pragma unroll
-            for (int i = 1; i < NS; ++i) v = lane == i ? s[i] : v;
-            ss[(size_t)lane * ld] = v;
+        for (int r = 0; r < (NS + LPE - 1) / LPE; ++r) {
+            const int i = gl + LPE * r;
+            const float v = pick<NS>(s, i);
+            if (live && i < NS) ss[(size_t)i * ld] = v;
         }
         float u[4];
 #pragma unroll
@@ -673,11 +715,11 @@ __global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g)
 #pragma unroll
         for (int c = 0; c < 4; ++c) ga[c] = gu[c] * half + seed * 2.0f * a.w_a * act[c] + adj[(t & 15) * 4 + c];
         __syncwarp();
-        if (lane < 4) adj[(t & 15) * 4 + lane] = 0.0f;  // slot now belongs to step t - 16
+        if (gl < 4) adj[(t & 15) * 4 + gl] = 0.0f;  // slot now belongs to step t - 16
         // actor forward at step t (its inputs: the state and the previous actions)
-        float x[3], h1[HPL], h2[HPL], mu[4];
-        warp_actor_input(st, t, DA, nh, [&](int tau, int c) { return a.A[((size_t)tau * 4 + c) * ld + e]; }, x);
-        warp_actor_fwd<HPL>(w, DA, x, h1, h2, mu);
+        float x[NX], h1[HPL], h2[HPL], mu[4];
+        grp_actor_input<LPE, NX>(st, t, DA, nh, [&](int tau, int c) { return a.A[((size_t)tau * 4 + c) * ld + e]; }, x);
+        grp_actor_fwd<H, LPE>(w, DA, x, h1, h2, mu);
         // reverse: output layer, layer 2, layer 1, inputs
         float dz3[4];
 #pragma unroll
@@ -687,7 +729,7 @@ __global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g)
         for (int j = 0; j < HPL; ++j) {
             float acc = 0.0f;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc = fmaf(w.W3[c * H + lane + 32 * j], dz3[c], acc);
+            for (int c = 0; c < 4; ++c) acc = fmaf(w.W3[c * H + gl + LPE * j], dz3[c], acc);
             dz2[j] = h2[j] > 0.0f ? acc : 0.0f;
         }
         {
@@ -696,52 +738,56 @@ __global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g)
             for (int i = 0; i < HPL; ++i) acc[i] = 0.0f;
 #pragma unroll
             for (int m = 0; m < HPL; ++m)
-                for (int jj = 0; jj < 32; ++jj) {
-                    const float dj = __shfl_sync(0xffffffffu, dz2[m], jj);
-                    const float* wr = w.W2 + (32 * m + jj) * w.l2 + lane;
+                for (int jj = 0; jj < LPE; ++jj) {
+                    const float dj = __shfl_sync(0xffffffffu, dz2[m], jj, LPE);
+                    const float* wr = w.W2 + (LPE * m + jj) * w.l2 + gl;
 #pragma unroll
-                    for (int i = 0; i < HPL; ++i) acc[i] = fmaf(wr[32 * i], dj, acc[i]);
+                    for (int i = 0; i < HPL; ++i) acc[i] = fmaf(wr[LPE * i], dj, acc[i]);
                 }
 #pragma unroll
             for (int i = 0; i < HPL; ++i) dz1[i] = h1[i] > 0.0f ? acc[i] : 0.0f;
         }
-        float dx[3] = {0.0f, 0.0f, 0.0f};
+        float dx[NX];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) dx[q] = 0.0f;
 #pragma unroll
         for (int m = 0; m < HPL; ++m)
-            for (int jj = 0; jj < 32; ++jj) {
-                const float dj = __shfl_sync(0xffffffffu, dz1[m], jj);
-                const float* wr = w.W1 + (32 * m + jj) * w.l1 + lane;
+            for (int jj = 0; jj < LPE; ++jj) {
+                const float dj = __shfl_sync(0xffffffffu, dz1[m], jj, LPE);
+                const float* wr = w.W1 + (LPE * m + jj) * w.l1 + gl;
 #pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    if (lane + 32 * q < DA) dx[q] = fmaf(wr[32 * q], dj, dx[q]);
+                for (int q = 0; q < NX; ++q)
+                    if (gl + LPE * q < DA) dx[q] = fmaf(wr[LPE * q], dj, dx[q]);
             }
         // observation part -> state adjoint (every lane), history part -> earlier actions
         float go[18];
 #pragma unroll
-        for (int k = 0; k < 18; ++k) go[k] = __shfl_sync(0xffffffffu, dx[0], k);
+        for (int k = 0; k < 18; ++k) go[k] = __shfl_sync(0xffffffffu, dx[k / LPE], k % LPE, LPE);
         obs_vjp(st, go, gs);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const int k = lane + 32 * q;
+        for (int q = 0; q < NX; ++q) {
+            const int k = gl + LPE * q;
             if (k >= 18 && k < DA) {
                 const int i = ((k - 18) >> 2) + 1, c = (k - 18) & 3;
                 if (t - i >= 0) adj[((t - i) & 15) * 4 + c] += dx[q];
             }
         }
-        // activation record of (step t, env e): x | h1 | h2 | dZ1 | dZ2 | dZ3
-        float* R = a.rec + (size_t)(t - t0) * NR * ld + (size_t)e * NR;
+        // activation record of (step t, env e): x | h1 | h2 | dZ1 | dZ2 | dZ3, env-major over
+        // the segment ([env][step][field]): a chunk of envs is one contiguous run of rows
+        if (live) {
+            float* R = a.rec + ((size_t)e * (t1 - t0) + (t - t0)) * NR;
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
-            if (lane + 32 * q < DA) R[lane + 32 * q] = x[q];
+            for (int q = 0; q < NX; ++q)
+                if (gl + LPE * q < DA) R[gl + LPE * q] = x[q];
 #pragma unroll
-        for (int j = 0; j < HPL; ++j) {
-            R[DA + lane + 32 * j] = h1[j];
-            R[DA + H + lane + 32 * j] = h2[j];
-            R[DA + 2 * H + lane + 32 * j] = dz1[j];
-            R[DA + 3 * H + lane + 32 * j] = dz2[j];
+            for (int j = 0; j < HPL; ++j) {
+                R[DA + gl + LPE * j] = h1[j];
+                R[DA + H + gl + LPE * j] = h2[j];
+                R[DA + 2 * H + gl + LPE * j] = dz1[j];
+                R[DA + 3 * H + gl + LPE * j] = dz2[j];
+            }
+            if (gl < 4) R[DA + 4 * H + gl] = pick<4>(dz3, gl);
         }
-        if (lane < 4)
-            R[DA + 4 * H + lane] = lane == 0 ? dz3[0] : (lane == 1 ? dz3[1] : (lane == 2 ? dz3[2] : dz3[3]));
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < NS; ++i) lam[i] = gs[i];
@@ -754,22 +800,24 @@ __global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g)
             for (int i = 0; i < NS; ++i) lam[i] = fmaf(seed, lg[i], lam[i]);
         }
     }
-    if (lane == 0) {
+    if (live) {
+        if (gl == 0) {
 #pragma unroll
-        for (int i = 0; i < NS; ++i) a.lam[i * ld + e] = lam[i];
+            for (int i = 0; i < NS; ++i) a.lam[i * ld + e] = lam[i];
 #pragma unroll
-        for (int i = 0; i < 7; ++i) a.gp[i * ld + e] = gp[i];
-        if (g == 0 && a.g_params)
+            for (int i = 0; i < 7; ++i) a.gp[i * ld + e] = gp[i];
+            if (g == 0 && a.g_params)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a.g_params[i * ld + e] = gp[i];
+                for (int i = 0; i < 4; ++i) a.g_params[i * ld + e] = gp[i];
+        }
+        for (int i = gl; i < 64; i += LPE) a.la[(size_t)i * ld + e] = adj[i];
     }
-    a.la[(size_t)lane * ld + e] = adj[lane];
-    a.la[(size_t)(lane + 32) * ld + e] = adj[lane + 32];
 }
 
 // Partial actor-weight gradient of segment g over env chunk blockIdx.x (closed loop).
-// Records are field-major (fs = ld, es = 1: the thread-per-env kernels) or env-major
-// (fs = 1, es = NR: the warp-per-env kernels).
+// Records are field-major per step (fs = ld, es = 1: the thread-per-env kernels; one GEMM
+// pass per step) or env-major over the whole segment (fs = 1, es = NR: the lane-group
+// kernels; the chunk's env x step rows are contiguous, one GEMM pass over all of them).
 __global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g, int fs, int es) {
     extern __shared__ __align__(16) float sm[];
     const int ld = a.ld, DA = a.DA, H = a.hid;
@@ -787,8 +835,12 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g, int fs, int 
     float* gb2 = gW2 + H * H;
     float* gW3 = gb2 + H;
     float* gb3 = gW3 + 4 * H;
-    for (int t = t0; t < t1; ++t) {
-        const float* R = a.rec + (size_t)(t - t0) * NR * ld + (size_t)e0 * es;
+    const bool seg_rows = fs == 1;  // env-major over the segment
+    const int steps = seg_rows ? 1 : t1 - t0;
+    const int nk = seg_rows ? ne * (t1 - t0) : ne;  // reduction rows per pass
+    for (int t = t0; t < t0 + steps; ++t) {
+        const float* R = seg_rows ? a.rec + (size_t)e0 * (t1 - t0) * NR
+                                  : a.rec + (size_t)(t - t0) * NR * ld + (size_t)e0 * es;
         const float* O = R;
         const float* H1 = R + (size_t)DA * fs;
         const float* H2 = H1 + (size_t)H * fs;
@@ -796,15 +848,15 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g, int fs, int 
         const float* dZ2 = dZ1 + (size_t)H * fs;
         const float* dZ3 = dZ2 + (size_t)H * fs;
         const bool first = (t == t0);
-        cta_gemm(H, DA, ne, Mat{dZ1, fs, es}, Mat{O, es, fs}, sm, [&](int m, int n, float v) {
+        cta_gemm(H, DA, nk, Mat{dZ1, fs, es}, Mat{O, es, fs}, sm, [&](int m, int n, float v) {
             float* p = gW1 + m * DA + n;
             *p = first ? v : *p + v;
         });
-        cta_gemm(H, H, ne, Mat{dZ2, fs, es}, Mat{H1, es, fs}, sm, [&](int m, int n, float v) {
+        cta_gemm(H, H, nk, Mat{dZ2, fs, es}, Mat{H1, es, fs}, sm, [&](int m, int n, float v) {
             float* p = gW2 + m * H + n;
             *p = first ? v : *p + v;
         });
-        cta_gemm(4, H, ne, Mat{dZ3, fs, es}, Mat{H2, es, fs}, sm, [&](int m, int n, float v) {
+        cta_gemm(4, H, nk, Mat{dZ3, fs, es}, Mat{H2, es, fs}, sm, [&](int m, int n, float v) {
             float* p = gW3 + m * H + n;
             *p = first ? v : *p + v;
         });
@@ -813,7 +865,7 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g, int fs, int 
                                                                          : dZ3 + (size_t)(j - 2 * H) * fs);
             float* dst = j < H ? gb1 + j : (j < 2 * H ? gb2 + (j - H) : gb3 + (j - 2 * H));
             float s = 0.0f;
-            for (int q = 0; q < ne; ++q) s += ldcg(src + (size_t)q * es);
+            for (int q = 0; q < nk; ++q) s += ldcg(src + (size_t)q * es);
             *dst = first ? s : *dst + s;
         }
         __syncthreads();
@@ -857,6 +909,24 @@ static WsLayout ws_layout(const qsim_vjp_desc& d, int DA, int PA, int nchunk) {
 }
 
 static constexpr int kChunk = 32;  // envs per weight-gradient CTA
+static constexpr int kAutoLanesPerEnv = 8;  // lane-group width of the closed loop by default
+
+// The lane-group kernels of one (hidden, lanes per env) shape.
+struct GrpKernels {
+    void (*fw)(VjpArgs);
+    void (*bw)(VjpArgs, int);
+};
+
+static GrpKernels grp_kernels(int hidden64, int lanes_index) {
+    static const GrpKernels tab[2][3] = {
+        {{k_vjp_forward_w<32, 32>, k_vjp_backward_w<32, 32>},
+         {k_vjp_forward_w<32, 16>, k_vjp_backward_w<32, 16>},
+         {k_vjp_forward_w<32, 8>, k_vjp_backward_w<32, 8>}},
+        {{k_vjp_forward_w<64, 32>, k_vjp_backward_w<64, 32>},
+         {k_vjp_forward_w<64, 16>, k_vjp_backward_w<64, 16>},
+         {k_vjp_forward_w<64, 8>, k_vjp_backward_w<64, 8>}}};
+    return tab[hidden64][lanes_index];
+}
 
 }  // namespace qsim
 
@@ -871,6 +941,8 @@ static qsim_status check_desc(const qsim_vjp_desc* d) {
     if (d->mode == 1 && (d->n_hist < 0 || d->n_hist > HMAX || d->hidden < 4 || d->hidden > 128))
         return fail(QSIM_EINVAL, "qsim_rollout_vjp: bad actor shape (n_hist=%d hidden=%d)", d->n_hist,
                     d->hidden);
+    if (d->lanes_per_env != 0 && d->lanes_per_env != 8 && d->lanes_per_env != 16 && d->lanes_per_env != 32)
+        return fail(QSIM_EINVAL, "qsim_rollout_vjp: lanes per env %d not 0, 8, 16 or 32", d->lanes_per_env);
     return QSIM_OK;
 }
 
@@ -924,23 +996,24 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
         QCHECK_CUDA(cudaFuncSetAttribute(k_vjp_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     const int grid = (d->n + VT - 1) / VT;
-    // closed loop at hidden 32 / 64: one env per warp
+    // closed loop at hidden 32 / 64: one env per group of lpe lanes
     const bool warp_path = d->mode == 1 && (a.hid == 32 || a.hid == 64) && a.DA <= 96;
-    const int gridw = (d->n + WV - 1) / WV;
-    const size_t smem_fw = sizeof(float) * (size_t)(warp_actor_floats(a.DA, a.hid) + 64 * WV);
+    const int lpe = d->lanes_per_env == 0 ? kAutoLanesPerEnv : d->lanes_per_env;
+    const int envs_per_cta = WV * (32 / lpe);
+    const int gridw = (d->n + envs_per_cta - 1) / envs_per_cta;
+    const size_t smem_fw = sizeof(float) * (size_t)(warp_actor_floats(a.DA, a.hid) + 64 * envs_per_cta);
     const size_t smem_bw = smem_fw;
+    GrpKernels gk{};
     if (warp_path) {
-        static bool configured[2] = {false, false};
-        const int hi = a.hid == 64;
-        if (!configured[hi]) {
-            auto fw = hi ? k_vjp_forward_w<2> : k_vjp_forward_w<1>;
-            auto bw = hi ? k_vjp_backward_w<2> : k_vjp_backward_w<1>;
-            QCHECK_CUDA(cudaFuncSetAttribute(fw, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-            QCHECK_CUDA(cudaFuncSetAttribute(bw, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-            configured[hi] = true;
+        const int hi = a.hid == 64, li = lpe == 32 ? 0 : (lpe == 16 ? 1 : 2);
+        gk = grp_kernels(hi, li);
+        static bool configured[2][3] = {};
+        if (!configured[hi][li]) {
+            QCHECK_CUDA(cudaFuncSetAttribute(gk.fw, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            QCHECK_CUDA(cudaFuncSetAttribute(gk.bw, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+            configured[hi][li] = true;
         }
-        if (a.hid == 64) k_vjp_forward_w<2><<<gridw, 32 * WV, smem_fw, cs>>>(a);
-        else k_vjp_forward_w<1><<<gridw, 32 * WV, smem_fw, cs>>>(a);
+        gk.fw<<<gridw, 32 * WV, smem_fw, cs>>>(a);
     } else {
         k_vjp_forward<<<grid, VT, smem, cs>>>(a);
     }
@@ -962,8 +1035,7 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
     }
     for (int g = a.nseg - 1; g >= 0; --g) {
         if (warp_path) {
-            if (a.hid == 64) k_vjp_backward_w<2><<<gridw, 32 * WV, smem_bw, cs>>>(a, g);
-            else k_vjp_backward_w<1><<<gridw, 32 * WV, smem_bw, cs>>>(a, g);
+            gk.bw<<<gridw, 32 * WV, smem_bw, cs>>>(a, g);
         } else {
             k_vjp_backward<<<grid, VT, smem, cs>>>(a, g);
         }

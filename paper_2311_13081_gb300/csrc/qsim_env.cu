@@ -3,6 +3,7 @@
 //
 // Layouts are field-major [field][ld] (ld = env count padded to 32) so that one warp's
 // access of one field is a single 128-byte transaction.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -314,6 +315,22 @@ __global__ void __launch_bounds__(256) k_recalc(EnvCfg C, EnvPtrs p, int64_t hea
                  (uint64_t)gridDim.x * blockDim.x);
 }
 
+// The same over several env sets in one launch: blockIdx.y selects the set.
+struct RecalcJob {
+    EnvCfg C;
+    EnvPtrs p;
+    int64_t head, size, capacity;
+};
+
+__global__ void __launch_bounds__(256) k_recalc_batch(const RecalcJob* __restrict__ jobs) {
+    const RecalcJob& J = jobs[blockIdx.y];
+    float Cr[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Cr[i] = J.p.rewardC[i];
+    recalc_range(J.C, J.p, Cr, J.head, J.size, J.capacity, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                 (uint64_t)gridDim.x * blockDim.x);
+}
+
 __global__ void k_set_reward(float* rewardC, float c0, float c1, float c2, float c3, float c4,
                              float c5, float c6, float sigma) {
     rewardC[0] = c0; rewardC[1] = c1; rewardC[2] = c2; rewardC[3] = c3;
@@ -437,7 +454,13 @@ extern "C" qsim_status qsim_dynamics_bench(const qsim_params* veh, int32_t n, in
     P.im = 1.0f / P.m; P.iJx = 1.0f / P.Jx; P.iJy = 1.0f / P.Jy; P.iJz = 1.0f / P.Jz;
     P.itm = 1.0f / P.tm;
     const float u_h = sqrtf(veh->mass * veh->g / (4.0f * veh->kf));
-    k_dynamics_bench<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(
+    // blocks of 128 threads, halved (to 32) while they would not cover every SM: the paper's
+    // shape (8,192 envs) then runs on all SMs instead of 64
+    int sms = 152, bs = 128, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    while (bs > 32 && grid_for(n, bs) < sms) bs >>= 1;
+    k_dynamics_bench<<<grid_for(n, bs), bs, 0, (cudaStream_t)stream>>>(
         make_vehicle(*veh), P, u_h, dt, n, ld, n_steps, state_out);
     QCHECK_LAUNCH("k_dynamics_bench");
     return QSIM_OK;
@@ -624,6 +647,40 @@ extern "C" qsim_status qsim_recalc_rewards(qsim_handle* h, void* stream) {
     const int grid = (int)(want < (int64_t)dev_sms * 16 ? want : (int64_t)dev_sms * 16);
     k_recalc<<<grid, 256, 0, (cudaStream_t)stream>>>(h->dc, h->p, h->head, h->size, h->capacity);
     QCHECK_LAUNCH("k_recalc");
+    return QSIM_OK;
+}
+
+extern "C" qsim_status qsim_recalc_rewards_batch(qsim_handle* const* hs, int32_t n, void* stream) {
+    if (!hs || n < 1 || n > 65535) return fail(QSIM_EINVAL, "qsim_recalc_rewards_batch: bad argument");
+    int dev = -1;
+    QCHECK_CUDA(cudaGetDevice(&dev));
+    std::vector<RecalcJob> jobs;
+    int64_t most = 0, total = 0;
+    for (int i = 0; i < n; ++i) {
+        const qsim_handle* h = hs[i];
+        if (!h) return fail(QSIM_EINVAL, "qsim_recalc_rewards_batch: null handle %d", i);
+        if (h->device != dev) return fail(QSIM_EINVAL, "qsim_recalc_rewards_batch: handle %d is on another device", i);
+        if (h->capacity == 0 || h->size == 0) continue;
+        const int64_t quads = h->size * (int64_t)((h->n + 3) / 4);
+        if (quads >= (int64_t)1 << 32) return fail(QSIM_EINVAL, "qsim_recalc_rewards_batch: ring %d too large", i);
+        jobs.push_back(RecalcJob{h->dc, h->p, h->head, h->size, h->capacity});
+        most = std::max(most, quads);
+        total += quads;
+    }
+    if (jobs.empty()) return QSIM_OK;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // blocks per set: its share of 16 blocks per SM, at least one, at most one per 256 quads
+    const int64_t want = std::max<int64_t>(1, (int64_t)sms * 16 * most / std::max<int64_t>(total, 1));
+    const int gx = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (most + 255) / 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    RecalcJob* d_jobs = nullptr;
+    QCHECK_CUDA(cudaMallocAsync((void**)&d_jobs, sizeof(RecalcJob) * jobs.size(), st));
+    QCHECK_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(RecalcJob) * jobs.size(), cudaMemcpyHostToDevice, st));
+    k_recalc_batch<<<dim3(gx, (unsigned)jobs.size()), 256, 0, st>>>(d_jobs);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(d_jobs, st);
+    if (e != cudaSuccess) return cuda_fail(e, "k_recalc_batch");
     return QSIM_OK;
 }
 

@@ -27,6 +27,7 @@
 #include "qsim_smlp.cuh"
 #include "qsim_internal.h"
 #include "qsim_recalc.cuh"
+#include "qsim_tcgen05.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -35,6 +36,9 @@ namespace qsim {
 
 constexpr int SMEM_ENGINE = smlp::floats() > smlp::floats2() ? smlp::floats() : smlp::floats2();
 constexpr int SMEM_MAIN = GEMM_SMEM > SMEM_ENGINE ? GEMM_SMEM : SMEM_ENGINE;
+// the small-run env step keeps an actor of hidden <= 64 and <= 128 inputs in shared memory
+static_assert(SMEM_MAIN >= 64 * 128 + 64 + 64 * 64 + 64 + 4 * 64 + 4 + 4 + 8 * (132 + 2 * 68 + 4 + 32),
+              "learner shared memory too small for the small-run env step");
 
 struct LearnHyper {
     float gamma, tau, lr, beta1, beta2, eps, sigma_t, noise_clip;
@@ -410,6 +414,199 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
     __syncthreads();
 }
 
+// Env step of a run with at most 8 envs (one CTA; a single run's env step sits on the
+// critical path of every update): the actor's weights are copied into shared memory
+// asynchronously (cp.async, L2 -> shared) while each env's thread loads its state and
+// history and builds its observation in shared memory; the three layers then read
+// shared memory only; the env's data stay in registers from the observation to the
+// write-back, and the history shift reads the observation row already in shared memory.
+// Same arithmetic, in the same order per output, as env_step_cta's small-batch path.
+__device__ __noinline__ void env_step_small(RunDesc& R, uint32_t t, int64_t slot, float* sm) {
+    const EnvCfg& C = R.C;
+    const int ld = C.ld, n = R.n_env, DA = R.DA, H = R.H, PA = R.PA;
+    const bool warm = (int64_t)t < (int64_t)C.learning_starts;
+    constexpr int LX = 132, LH = 68;
+    float* Ws = sm;                                   // actor parameters, as stored
+    float* xs = sm + ((PA + 3) & ~3);                 // [8][LX] observations
+    float* h1 = xs + 8 * LX;                          // [8][LH]
+    float* h2 = h1 + 8 * LH;                          // [8][LH]
+    float* mus = h2 + 8 * LH;                         // [8][4]
+    float* park = mus + 8 * 4;                        // [8][32]: env data across the layers
+    if (!warm) {
+        const int nv = PA >> 2;
+        const uint32_t sW = (uint32_t)__cvta_generic_to_shared(Ws);
+        for (int v = threadIdx.x; v < nv; v += LT)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(sW + 16u * (uint32_t)v),
+                         "l"(R.actor + 4 * v) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int i = 4 * nv + threadIdx.x; i < PA; i += LT) Ws[i] = ldcg(R.actor + i);
+    }
+    const int e = threadIdx.x;
+    const bool mine = e < n;
+    if (mine) {
+        // the env's data wait in shared memory while the layers run (no long live ranges)
+        float* pk = park + 32 * e;
+        float s[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) s[i] = pk[i] = ldcg(R.E.state + i * ld + e);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) pk[NS + i] = ldcg(R.E.dist + i * ld + e);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) pk[NS + 6 + i] = ldcg(R.E.prm + i * ld + e);
+        pk[30] = __uint_as_float(ldcg(R.E.ep_step + e));
+        pk[31] = ldcg(R.E.ep_ret + e);
+        float* row = xs + e * LX;
+        const int nh4 = 4 * C.n_hist;
+        // history in two halves, each with all its loads in flight before its stores
+#pragma unroll 1
+        for (int h0 = 0; h0 < 4 * HMAX; h0 += 2 * HMAX) {
+            float hv[2 * HMAX];
+#pragma unroll
+            for (int k = 0; k < 2 * HMAX; ++k) hv[k] = h0 + k < nh4 ? ldcg(R.E.hist + (h0 + k) * ld + e) : 0.0f;
+#pragma unroll
+            for (int k = 0; k < 2 * HMAX; ++k) row[18 + h0 + k] = hv[k];
+        }
+        float o[18];
+        obs_state(s, o);
+        if (!warm && C.any_noise) {
+            float nz[18];
+            obs_noise(C, (uint32_t)e, t, nz);
+#pragma unroll
+            for (int k = 0; k < 18; ++k) o[k] += nz[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 18; ++k) row[k] = o[k];
+    }
+    if (!warm) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        // layer 1 and 2: one warp per output unit, lanes over the inputs, shuffle sums
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const float* b1 = Ws + H * DA;
+        const float* W2 = b1 + H;
+        const float* b2 = W2 + H * H;
+        const float* W3 = b2 + H;
+        const float* b3 = W3 + 4 * H;
+        for (int j = warp; j < H; j += LT / 32) {
+            for (int r = 0; r < n; ++r) {
+                float acc = 0.0f;
+                for (int k = lane; k < DA; k += 32) acc = fmaf(Ws[j * DA + k], xs[r * LX + k], acc);
+                acc = smlp::warp_sum(acc) + b1[j];
+                if (lane == 0) h1[r * LH + j] = fmaxf(acc, 0.0f);
+            }
+        }
+        __syncthreads();
+        for (int j = warp; j < H; j += LT / 32) {
+            for (int r = 0; r < n; ++r) {
+                float acc = 0.0f;
+                for (int k = lane; k < H; k += 32) acc = fmaf(W2[j * H + k], h1[r * LH + k], acc);
+                acc = smlp::warp_sum(acc) + b2[j];
+                if (lane == 0) h2[r * LH + j] = fmaxf(acc, 0.0f);
+            }
+        }
+        __syncthreads();
+        for (int item = warp; item < 4 * n; item += LT / 32) {
+            const int r = item >> 2, o = item & 3;
+            float acc = 0.0f;
+            for (int k = lane; k < H; k += 32) acc = fmaf(W3[o * H + k], h2[r * LH + k], acc);
+            acc = smlp::warp_sum(acc) + b3[o];
+            if (lane == 0) mus[r * 4 + o] = tanhf(acc);
+        }
+    }
+    __syncthreads();
+    if (!mine) return;
+    float s[NS], d[6];
+    const float* pk = park + 32 * e;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) s[i] = pk[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) d[i] = pk[NS + i];
+    const Prm P = make_prm(pk[23], pk[24], pk[25], pk[26], pk[27], pk[28], pk[29]);
+    const uint32_t ep_step = __float_as_uint(pk[30]);
+    const float ret0 = pk[31];
+    const float sigma = ldcg(R.E.rewardC + 7);
+    float Cr[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Cr[i] = ldcg(R.E.rewardC + i);
+    float a[4];
+    if (warm) {
+        const uint4 r = draw(C, (uint32_t)e, t, TAG_WARM, 0);
+        a[0] = 2.0f * u01(r.x) - 1.0f; a[1] = 2.0f * u01(r.y) - 1.0f;
+        a[2] = 2.0f * u01(r.z) - 1.0f; a[3] = 2.0f * u01(r.w) - 1.0f;
+    } else {
+        const float* mu = mus + e * 4;
+        if (sigma > 0.0f) {
+            const uint4 r0 = draw(C, (uint32_t)e, t, TAG_EXPL, 0);
+            const uint4 r1 = draw(C, (uint32_t)e, t, TAG_EXPL, 1);
+            a[0] = clampf(fmaf(sigma, gauss(r0.x, r0.y), mu[0]), -1.0f, 1.0f);
+            a[1] = clampf(fmaf(sigma, gauss(r0.z, r0.w), mu[1]), -1.0f, 1.0f);
+            a[2] = clampf(fmaf(sigma, gauss(r1.x, r1.y), mu[2]), -1.0f, 1.0f);
+            a[3] = clampf(fmaf(sigma, gauss(r1.z, r1.w), mu[3]), -1.0f, 1.0f);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[j] = clampf(mu[j], -1.0f, 1.0f);
+        }
+    }
+    float u[4], s2[NS];
+    action_to_rpm(C.veh, a, u);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) s2[i] = s[i];
+    motor_lag_off(C, u, s2);
+    rk4(C.veh, C.dt, C.renorm, s2, u, P, d);
+    const float r = reward(Cr, s2, a);
+    const bool term = terminated(C, s2);
+    const uint32_t ep_after = ep_step + 1;
+    const bool trunc = !term && (int)ep_after >= C.episode_len;
+    if (R.capacity > 0) {
+        float* rec = R.E.rec + (size_t)slot * C.F * ld + e;
+#pragma unroll
+        for (int i = 0; i < NS; ++i) rec[i * ld] = s[i];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rec[(17 + i) * ld] = a[i];
+        rec[21 * ld] = r;
+        rec[22 * ld] = __uint_as_float(pack_flags(term, trunc, ep_step));
+        if (C.n_priv) {
+            float pv[NPRIV];
+            priv_vals(C, P, d, pv);
+#pragma unroll
+            for (int k = 0; k < NPRIV; ++k) rec[(23 + k) * ld] = pv[k];
+        }
+        if (term || trunc) {
+            float* sd = R.E.side + (size_t)slot * NS * ld + e;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) sd[i * ld] = s2[i];
+        }
+    }
+    float ret = ret0 + r;
+    uint32_t eps = ep_after;
+    if (term || trunc) {
+        R.E.n_done[e] = ldcg(R.E.n_done + e) + 1;
+        R.E.len_sum[e] = ldcg(R.E.len_sum + e) + ep_after;
+        R.E.ret_sum[e] = ldcg(R.E.ret_sum + e) + ret;
+        const uint32_t epi = ldcg(R.E.ep_index + e) + 1;
+        R.E.ep_index[e] = epi;
+        float prm7[7];
+        reset_env(C, (uint32_t)e, epi, s2, prm7, d);
+        for (int i = 0; i < 7; ++i) R.E.prm[i * ld + e] = prm7[i];
+        for (int i = 0; i < 6; ++i) R.E.dist[i * ld + e] = d[i];
+        for (int i = 0; i < 4 * HMAX; ++i) R.E.hist[i * ld + e] = 0.0f;
+        ret = 0.0f;
+        eps = 0;
+    } else {
+        // history newest first: a_t, then the previous entries (from the observation row)
+        const int nh4 = 4 * C.n_hist;
+        const float* row = xs + e * LX + 18;
+        for (int k = nh4 - 1; k >= 4; --k) R.E.hist[k * ld + e] = row[k - 4];
+        if (C.n_hist > 0)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) R.E.hist[c * ld + e] = a[c];
+    }
+    R.E.ep_ret[e] = ret;
+    R.E.ep_step[e] = eps;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) R.E.state[i * ld + e] = s2[i];
+}
+
 // ------------------------------------------------------------------------- TD3 update
 // Ring index a mod m for a in [-m, 2m).
 __device__ __forceinline__ int64_t ring(int64_t a, int64_t m) {
@@ -740,6 +937,197 @@ __device__ __noinline__ void td3_update(RunDesc& R, int64_t head, int64_t size, 
     cluster_sync_all(nS);
 }
 
+// ------------------------------------------------ tensor-core forward pass (tcgen05)
+// Forward of a CTA's Bc rows (Bc a multiple of 128) through a network in -> H -> H -> out
+// (in <= 96, H in {32, 64, 128}): both hidden layers as tcgen05 MMAs (M 128 rows, N = H,
+// K = 16) on fp16 hi/lo operands in shared memory (three products per FP32-accurate
+// product), accumulators in tensor memory; bias, ReLU and the 4- or 1-wide output layer on
+// the CUDA cores.  One thread issues the MMAs and commits them to an mbarrier that every
+// thread waits on (bounded).  Shared memory is the learner's engine region, laid out here
+// per call: W1 hi/lo [H][96], W2 hi/lo [H][H], the tile operand hi/lo (X [128][96], then the
+// first hidden layer [128][H] in place), b1, b2, W3, b3, partial outputs, the mbarrier.
+namespace tcf {
+constexpr int KP = 96, KC1 = KP / 8;
+constexpr int TMEM_COLS = 256;  // D1 [128 x H] at column 0, D2 at column H (H <= 128)
+constexpr int WAIT_POLLS = 1 << 24;
+struct Lay {
+    int w1h, w1l, w2h, w2l, th, tl, b1, b2, w3, b3, part, bar, end;
+};
+__host__ __device__ constexpr Lay lay(int H) {
+    const int w1 = H * KP * 2, w2 = H * H * 2, t = 128 * (H > KP ? H : KP) * 2;
+    Lay L{};
+    L.w1h = 0; L.w1l = w1; L.w2h = 2 * w1; L.w2l = 2 * w1 + w2; L.th = 2 * w1 + 2 * w2; L.tl = L.th + t;
+    L.b1 = L.tl + t; L.b2 = L.b1 + 4 * H; L.w3 = L.b2 + 4 * H; L.b3 = L.w3 + 16 * H;
+    L.part = L.b3 + 16; L.bar = L.part + 2 * 128 * 4 * 4; L.end = L.bar + 16;
+    return L;
+}
+static_assert(lay(128).end <= 4 * SMEM_MAIN, "tensor-core forward: shared memory");
+
+__device__ __forceinline__ bool eligible(const RunDesc& R, int Bc) {
+    return Bc % 128 == 0 && (R.H == 32 || R.H == 64 || R.H == 128) && R.DA <= KP && R.DC <= KP;
+}
+
+// rows of 8 consecutive inputs -> packed hi / lo halves (zero beyond `in`)
+__device__ __forceinline__ void split8(const float* src, int k0, int in, uint4& hi, uint4& lo) {
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = k0 + e < in ? ldcg(src + k0 + e) : 0.0f;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) tc::split2(v[2 * e], v[2 * e + 1], h[e], l[e]);
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+}  // namespace tcf
+
+__device__ __noinline__ void tc_forward(const float* W, int in, int H, int out, const float* X, int ldx,
+                                        int Bc, float* Y, int ldy, bool tanh_out, float* sm, uint32_t tmem,
+                                        int* status) {
+    using namespace tcf;
+    unsigned char* smb = reinterpret_cast<unsigned char*>(sm);
+    const Lay L = lay(H);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int KC2 = H / 8;
+    const float* gb1 = W + H * in;
+    const float* gW2 = gb1 + H;
+    const float* gb2 = gW2 + H * H;
+    const float* gW3 = gb2 + H;
+    const float* gb3 = gW3 + out * H;
+    __half* w1h = reinterpret_cast<__half*>(smb + L.w1h);
+    __half* w1l = reinterpret_cast<__half*>(smb + L.w1l);
+    __half* w2h = reinterpret_cast<__half*>(smb + L.w2h);
+    __half* w2l = reinterpret_cast<__half*>(smb + L.w2l);
+    __half* th = reinterpret_cast<__half*>(smb + L.th);
+    __half* tl = reinterpret_cast<__half*>(smb + L.tl);
+    float* b1 = reinterpret_cast<float*>(smb + L.b1);
+    float* b2 = reinterpret_cast<float*>(smb + L.b2);
+    float* W3 = reinterpret_cast<float*>(smb + L.w3);
+    float* b3 = reinterpret_cast<float*>(smb + L.b3);
+    float* part = reinterpret_cast<float*>(smb + L.part);  // [2][128][4]
+    const uint32_t bar = tc::smem_u32(smb + L.bar);
+    // stage the weights as hi / lo halves in the canonical K-major layout
+    for (int i = tid; i < H * KC1; i += LT) {
+        const int n = i / KC1, kc = i - n * KC1;
+        uint4 hi, lo;
+        split8(W + (size_t)n * in, 8 * kc, in, hi, lo);
+        *reinterpret_cast<uint4*>(w1h + tc::cano16(n, 8 * kc, KC1)) = hi;
+        *reinterpret_cast<uint4*>(w1l + tc::cano16(n, 8 * kc, KC1)) = lo;
+    }
+    for (int i = tid; i < H * KC2; i += LT) {
+        const int n = i / KC2, kc = i - n * KC2;
+        uint4 hi, lo;
+        split8(gW2 + (size_t)n * H, 8 * kc, H, hi, lo);
+        *reinterpret_cast<uint4*>(w2h + tc::cano16(n, 8 * kc, KC2)) = hi;
+        *reinterpret_cast<uint4*>(w2l + tc::cano16(n, 8 * kc, KC2)) = lo;
+    }
+    for (int i = tid; i < H; i += LT) {
+        b1[i] = ldcg(gb1 + i);
+        b2[i] = ldcg(gb2 + i);
+    }
+    for (int i = tid; i < out * H; i += LT) W3[i] = ldcg(gW3 + i);
+    if (tid < out) b3[tid] = ldcg(gb3 + tid);
+    if (tid == 0) tc::bar_init(bar, 1);
+    uint32_t phase = 0;
+    const uint32_t idesc = tc::idesc_f16(H);
+    const uint32_t d1 = tmem, d2 = tmem + (uint32_t)H;
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    const int half = warp >> 2;                 // column half of the epilogues
+    const int r = 32 * (warp & 3) + lane;       // tile row of this thread in the epilogues
+    const int cbeg = half * (H / 2), cend = cbeg + H / 2;
+    for (int t0 = 0; t0 < Bc; t0 += 128) {
+        // input tile -> hi / lo halves
+        for (int i = tid; i < 128 * KC1; i += LT) {
+            const int rr = i / KC1, kc = i - rr * KC1;
+            uint4 hi, lo;
+            split8(X + (size_t)(t0 + rr) * ldx, 8 * kc, in, hi, lo);
+            *reinterpret_cast<uint4*>(th + tc::cano16(rr, 8 * kc, KC1)) = hi;
+            *reinterpret_cast<uint4*>(tl + tc::cano16(rr, 8 * kc, KC1)) = lo;
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < KP / 16; ++j) {
+                const uint32_t ko = (uint32_t)j * 256u;
+                const uint64_t ah = tc::sdesc(tc::smem_u32(th) + ko, KC1), al = tc::sdesc(tc::smem_u32(tl) + ko, KC1);
+                const uint64_t bh = tc::sdesc(tc::smem_u32(w1h) + ko, KC1), bl = tc::sdesc(tc::smem_u32(w1l) + ko, KC1);
+                tc::mma_ss(d1, ah, bh, idesc, j > 0);
+                tc::mma_ss(d1, ah, bl, idesc, 1);
+                tc::mma_ss(d1, al, bh, idesc, 1);
+            }
+            tc::commit(bar);
+        }
+        if (!tc::bar_wait(bar, phase, WAIT_POLLS) && lane == 0 && status) atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+        phase ^= 1u;
+        tc::fence_after();
+        // epilogue 1: bias, ReLU, split -> the tile buffer as the layer-2 operand
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
+            uint32_t v[16];
+            tc::ld16(d1 + lane_off + (uint32_t)c0, v);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                uint32_t h[4], l[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = c0 + 8 * q + 2 * e;
+                    const float x0 = fmaxf(__uint_as_float(v[8 * q + 2 * e]) + b1[c], 0.0f);
+                    const float x1 = fmaxf(__uint_as_float(v[8 * q + 2 * e + 1]) + b1[c + 1], 0.0f);
+                    tc::split2(x0, x1, h[e], l[e]);
+                }
+                const int off = tc::cano16(r, c0 + 8 * q, KC2);
+                *reinterpret_cast<uint4*>(th + off) = make_uint4(h[0], h[1], h[2], h[3]);
+                *reinterpret_cast<uint4*>(tl + off) = make_uint4(l[0], l[1], l[2], l[3]);
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid == 0) {
+            for (int j = 0; j < H / 16; ++j) {
+                const uint32_t ko = (uint32_t)j * 256u;
+                const uint64_t ah = tc::sdesc(tc::smem_u32(th) + ko, KC2), al = tc::sdesc(tc::smem_u32(tl) + ko, KC2);
+                const uint64_t bh = tc::sdesc(tc::smem_u32(w2h) + ko, KC2), bl = tc::sdesc(tc::smem_u32(w2l) + ko, KC2);
+                tc::mma_ss(d2, ah, bh, idesc, j > 0);
+                tc::mma_ss(d2, ah, bl, idesc, 1);
+                tc::mma_ss(d2, al, bh, idesc, 1);
+            }
+            tc::commit(bar);
+        }
+        if (!tc::bar_wait(bar, phase, WAIT_POLLS) && lane == 0 && status) atomicCAS(status, DEV_OK, DEV_TIMEOUT);
+        phase ^= 1u;
+        tc::fence_after();
+        // epilogue 2: bias, ReLU, the output layer's partial sums over this warp's columns
+        float po[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
+            uint32_t v[16];
+            tc::ld16(d2 + lane_off + (uint32_t)c0, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int c = c0 + e;
+                const float h2 = fmaxf(__uint_as_float(v[e]) + b2[c], 0.0f);
+#pragma unroll
+                for (int o = 0; o < 4; ++o)
+                    if (o < out) po[o] = fmaf(W3[o * H + c], h2, po[o]);
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) part[(half * 128 + r) * 4 + o] = po[o];
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if (tid < 128) {
+            for (int o = 0; o < out; ++o) {
+                const float y = part[tid * 4 + o] + part[(128 + tid) * 4 + o] + b3[o];
+                Y[(size_t)(t0 + tid) * ldy + o] = tanh_out ? tanhf(y) : y;
+            }
+        }
+        __syncthreads();  // the tile buffer and the partials are reused by the next tile
+    }
+}
+
 // One TD3 update with every network pass resident in shared memory (hidden <= 64, or the
 // 128-wide engine shape for HT = 128): same phases and cluster reduction as td3_update.  HT/DAT/DCT fix the hidden width and the
 // actor/critic input widths at compile time (0: taken from the run descriptor), so that the
@@ -748,7 +1136,7 @@ template <int HT, int DAT, int DCT>
 __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t size, int64_t t_now,
                                              uint32_t u, int64_t& t_a, int64_t& t_c, const Scr& S,
                                              float* scr_base, size_t scr_stride, int rk, int nS,
-                                             float* sm) {
+                                             float* sm, uint32_t tmem, bool tmem_ok) {
     using namespace smlp;
     const int B = R.B, Bc = B / nS, PA = R.PA, PC = R.PC;
     const int H = HT ? HT : R.H, DA = DAT ? DAT : R.DA, DC = DCT ? DCT : R.DC;
@@ -760,9 +1148,16 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
     // a9: gather
     gather_all(R, j0, Bc, u, head, size, t_now, S, sm);
     __syncthreads();
+    // the pure forward passes (target actor, target critics) on the tensor cores when the
+    // CTA holds whole 128-row tiles
+    const bool tcf_on = tmem_ok && tcf::eligible(R, Bc);
     // a10: target actor + smoothing
-    stage(R.actor_t, DA, H, 4, b);
-    for (int r0 = 0; r0 < Bc; r0 += MC) forward(DA, H, 4, S.oa2, DA, r0, min(MC, Bc - r0), b, S.mu, 4, true);
+    if (tcf_on) {
+        tc_forward(R.actor_t, DA, H, 4, S.oa2, DA, Bc, S.mu, 4, true, sm, tmem, R.E.status);
+    } else {
+        stage(R.actor_t, DA, H, 4, b);
+        for (int r0 = 0; r0 < Bc; r0 += MC) forward(DA, H, 4, S.oa2, DA, r0, min(MC, Bc - r0), b, S.mu, 4, true);
+    }
     for (int jl = threadIdx.x; jl < Bc; jl += LT) {
         const uint32_t j = (uint32_t)(j0 + jl);
         const uint4 r0 = draw(R.C, j, u, TAG_SMOOTH, 0), r1 = draw(R.C, j, u, TAG_SMOOTH, 1);
@@ -775,10 +1170,15 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
     }
     __syncthreads();
     // a11: twin target critics
-    stage(R.c1_t, DC, H, 1, b);
-    for (int r0 = 0; r0 < Bc; r0 += MC) forward(DC, H, 1, S.oc2, DC, r0, min(MC, Bc - r0), b, S.q1, 1, false);
-    stage(R.c2_t, DC, H, 1, b);
-    for (int r0 = 0; r0 < Bc; r0 += MC) forward(DC, H, 1, S.oc2, DC, r0, min(MC, Bc - r0), b, S.q2, 1, false);
+    if (tcf_on) {
+        tc_forward(R.c1_t, DC, H, 1, S.oc2, DC, Bc, S.q1, 1, false, sm, tmem, R.E.status);
+        tc_forward(R.c2_t, DC, H, 1, S.oc2, DC, Bc, S.q2, 1, false, sm, tmem, R.E.status);
+    } else {
+        stage(R.c1_t, DC, H, 1, b);
+        for (int r0 = 0; r0 < Bc; r0 += MC) forward(DC, H, 1, S.oc2, DC, r0, min(MC, Bc - r0), b, S.q1, 1, false);
+        stage(R.c2_t, DC, H, 1, b);
+        for (int r0 = 0; r0 < Bc; r0 += MC) forward(DC, H, 1, S.oc2, DC, r0, min(MC, Bc - r0), b, S.q2, 1, false);
+    }
     for (int jl = threadIdx.x; jl < Bc; jl += LT) {
         const float qmin = fminf(S.q1[jl], S.q2[jl]);
         S.y[jl] = S.r[jl] + (S.term[jl] != 0.0f ? 0.0f : hp.gamma * qmin);
@@ -905,8 +1305,21 @@ __device__ __noinline__ void curriculum_step(RunDesc& R, int64_t head, int64_t s
 // Persistent training kernel.  Cluster c walks runs order[off[c] .. off[c+1]).
 __global__ void __launch_bounds__(LT) k_train(RunDesc* runs, const int* order, const int* off,
                                               int n_iters, int do_env, float* scratch,
-                                              size_t scr_stride, int nS) {
+                                              size_t scr_stride, int nS, int use_tc) {
     extern __shared__ __align__(16) float sm[];
+    // tensor memory for the tensor-core forward passes, when some run of the launch has them
+    __shared__ uint32_t tmem_slot;
+    if (use_tc) {
+        if ((threadIdx.x >> 5) == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                         :: "r"(tc::smem_u32(&tmem_slot)), "r"(tcf::TMEM_COLS) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+    }
+    const uint32_t tmem = use_tc ? tmem_slot : 0u;
     const int rk = nS > 1 ? (int)cg::this_cluster().block_rank() : 0;
     const int cl = blockIdx.x / nS;
     float* my = scratch + (size_t)blockIdx.x * scr_stride;
@@ -919,7 +1332,12 @@ __global__ void __launch_bounds__(LT) k_train(RunDesc* runs, const int* order, c
         for (int it = 0; it < n_iters; ++it) {
             int n_upd = 1;
             if (do_env) {
-                if (rk == 0) env_step_cta(R, S, (uint32_t)t_now, head, sm);
+                if (rk == 0) {
+                    if (R.n_env <= 8 && R.H <= 64 && R.DA <= 128)
+                        env_step_small(R, (uint32_t)t_now, head, sm);
+                    else
+                        env_step_cta(R, S, (uint32_t)t_now, head, sm);
+                }
                 t_now += 1;
                 if (R.capacity > 0) {
                     head = head + 1 == R.capacity ? 0 : head + 1;
@@ -941,20 +1359,20 @@ __global__ void __launch_bounds__(LT) k_train(RunDesc* runs, const int* order, c
                     const int key = R.H * 1000000 + R.DA * 1000 + R.DC;
                     if (key == 64082090)
                         td3_update_smem<64, 82, 90>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S,
-                                                    my, scr_stride, rk, nS, sm);
+                                                    my, scr_stride, rk, nS, sm, tmem, use_tc != 0);
                     else if (key == 32082090)
                         td3_update_smem<32, 82, 90>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S,
-                                                    my, scr_stride, rk, nS, sm);
+                                                    my, scr_stride, rk, nS, sm, tmem, use_tc != 0);
                     else if (key == 64082096)
                         td3_update_smem<64, 82, 96>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S,
-                                                    my, scr_stride, rk, nS, sm);
+                                                    my, scr_stride, rk, nS, sm, tmem, use_tc != 0);
                     else
                         td3_update_smem<0, 0, 0>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S,
-                                                 my, scr_stride, rk, nS, sm);
+                                                 my, scr_stride, rk, nS, sm, tmem, use_tc != 0);
                 } else if (resident128) {
                     // hidden 128 with 16 actions of history: the 128-wide engine shape
                     td3_update_smem<128, 82, 90>(R, head, size, t_now, (uint32_t)u, t_a, t_c, S, my,
-                                                 scr_stride, rk, nS, sm);
+                                                 scr_stride, rk, nS, sm, tmem, use_tc != 0);
                 } else
                     td3_update(R, head, size, t_now, (uint32_t)u, t_a, t_c, S, my, scr_stride,
                                blockIdx.x - rk, rk, nS, sm);
@@ -967,6 +1385,13 @@ __global__ void __launch_bounds__(LT) k_train(RunDesc* runs, const int* order, c
             R.next_curr = next_curr;
         }
         cluster_sync_all(nS);
+    }
+    if (use_tc) {
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+        if ((threadIdx.x >> 5) == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(tcf::TMEM_COLS) : "memory");
     }
 }
 
@@ -1119,9 +1544,15 @@ struct PackedRun {
 static_assert(sizeof(PackedRun) <= QSIM_STATIC_DESC_BYTES, "run descriptor exceeds its static area");
 constexpr size_t kPackedBytes = (sizeof(PackedRun) + 255) & ~(size_t)255;
 
+// Whether the run's pure forward passes go to the tensor cores (tcf::eligible on the device).
+static bool tc_forward_wanted(const RunDesc& R, int nS) {
+    const int Bc = R.B / nS;
+    return Bc % 128 == 0 && (R.H == 32 || R.H == 64 || R.H == 128) && R.DA <= tcf::KP && R.DC <= tcf::KP;
+}
+
 static qsim_status launch_k_train(int grid, int nS, cudaStream_t st, RunDesc* d_runs, const int* d_order,
                                   const int* d_off, int64_t n_iters, int do_env, float* scratch,
-                                  size_t stride) {
+                                  size_t stride, int use_tc) {
     if (n_iters > INT32_MAX) return fail(QSIM_EINVAL, "too many steps for one launch");
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(grid);
@@ -1137,7 +1568,7 @@ static qsim_status launch_k_train(int grid, int nS, cudaStream_t st, RunDesc* d_
     lc.numAttrs = 1;
     if (nS > 8) QCHECK_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     QCHECK_CUDA(cudaLaunchKernelEx(&lc, k_train, d_runs, d_order, d_off, (int)n_iters, do_env, scratch,
-                                   stride, nS));
+                                   stride, nS, use_tc));
     return QSIM_OK;
 }
 
@@ -1157,7 +1588,8 @@ static qsim_status run_single(ac_handle* a, qsim_handle* env, int64_t n_iters, i
         // pageable source: the copy is staged before the call returns
         QCHECK_CUDA(cudaMemcpyAsync(d_pk, &pk, sizeof(pk), cudaMemcpyHostToDevice, st));
     }
-    s = launch_k_train(L.nS, L.nS, st, &d_pk->run, d_pk->order, d_pk->off, n_iters, do_env, scratch, L.stride);
+    s = launch_k_train(L.nS, L.nS, st, &d_pk->run, d_pk->order, d_pk->off, n_iters, do_env, scratch, L.stride,
+                       tc_forward_wanted(pk.run, L.nS) ? 1 : 0);
     if (s != QSIM_OK) {
         if (mirror) memset(mirror, 0xff, sizeof(RunDesc));  // unknown device state: upload next time
         return s;
@@ -1252,8 +1684,10 @@ static qsim_status launch_train(std::vector<ac_handle*>& A, std::vector<qsim_han
     QCHECK_CUDA(cudaMemcpyAsync(d_runs, D.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, st));
     QCHECK_CUDA(cudaMemcpyAsync(d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
     QCHECK_CUDA(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (n_clusters + 1), cudaMemcpyHostToDevice, st));
+    int use_tc = 0;
+    for (int i = 0; i < n; ++i) use_tc |= tc_forward_wanted(D[i], nS) ? 1 : 0;
     qsim_status s = launch_k_train(n_clusters * nS, nS, st, d_runs, d_order, d_off, n_iters, do_env,
-                                   scratch, stride);
+                                   scratch, stride, use_tc);
     cudaFreeAsync(scratch, st);
     cudaFreeAsync(d_off, st);
     cudaFreeAsync(d_order, st);
@@ -1634,6 +2068,8 @@ extern "C" qsim_status ac_plan_create(ac_handle* const* runs, qsim_handle* const
                                                        p->A[i]->obs_dim, p->A[i]->critic_in,
                                                        p->A[i]->n_actor, p->A[i]->n_critic, p->E[i]->n));
     }
+    int use_tc = 0;
+    for (int i = 0; i < n; ++i) use_tc |= tc_forward_wanted(D[i], nS) ? 1 : 0;
     // longest-processing-time-first assignment of runs to clusters
     std::vector<int> order(n), off(p->n_clusters + 1, 0);
     {
@@ -1691,7 +2127,7 @@ extern "C" qsim_status ac_plan_create(ac_handle* const* runs, qsim_handle* const
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess)
         e = cudaLaunchKernelEx(&lc, k_train, p->d_runs, (const int*)p->d_order, (const int*)p->d_off,
-                               steps_per_chunk, 1, p->scratch, p->stride, nS);
+                               steps_per_chunk, 1, p->scratch, p->stride, nS, use_tc);
     cudaError_t e2 = cudaStreamEndCapture(cs, &p->graph);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);

@@ -10,10 +10,12 @@ import torch
 from . import (QsimParams, QsimVjpDesc, _lib, load, qsim_rollout_vjp, qsim_vjp_workspace)
 
 
-def make_desc(n, ld, H, ckpt, mode, weights, dt=0.01, renorm=1, n_hist=16, hidden=64):
+def make_desc(n, ld, H, ckpt, mode, weights, dt=0.01, renorm=1, n_hist=16, hidden=64,
+              lanes_per_env=0):
     d = QsimVjpDesc()
     d.n, d.ld, d.H, d.ckpt, d.mode = int(n), int(ld), int(H), int(ckpt), int(mode)
     d.n_hist, d.hidden = int(n_hist), int(hidden)
+    d.lanes_per_env = int(lanes_per_env)
     d.w_p, d.w_q, d.w_v, d.w_a = (float(x) for x in weights)
     d.dt, d.renorm = float(dt), int(renorm)
     return d

@@ -26,7 +26,7 @@ def close(g, r, what):
     assert not bad.any(), f"{what}: {bad.sum()} elements off, e.g. {g[bad][:3]} vs {r[bad][:3]}"
 
 
-def setup(n, H, mode, seed=0, n_hist=16, hidden=64, ckpt=7):
+def setup(n, H, mode, seed=0, n_hist=16, hidden=64, ckpt=7, lanes=0):
     q = __import__("paper_2311_13081_gb300")
     from paper_2311_13081_gb300 import diff
     d = W.config("c1")
@@ -38,7 +38,8 @@ def setup(n, H, mode, seed=0, n_hist=16, hidden=64, ckpt=7):
     prm[:, :n] = W.random_params(seed + 1, n).T
     prm[:, n:] = prm[:, :1]
     wts = (1.0, 0.5, 0.2, 0.05)
-    desc = diff.make_desc(n, ld, H, ckpt, mode, wts, n_hist=n_hist, hidden=hidden)
+    desc = diff.make_desc(n, ld, H, ckpt, mode, wts, n_hist=n_hist, hidden=hidden,
+                          lanes_per_env=lanes)
     S0, PR = torch.tensor(s0, device="cuda"), torch.tensor(prm, device="cuda")
     return q, diff, d, veh, ld, S0, PR, desc, wts
 
@@ -81,6 +82,36 @@ def test_closed_loop_vjp_matches_oracle(gpu):
     close(f64(aout)[:, :, :n].transpose(2, 0, 1), ref["act_out"], "actions")
     close(f64(gw), ref["g_actor"], "g_actor")
     close(f64(gp)[:, :n].T, ref["g_prm"][:, :4], "g_params")
+
+
+@pytest.mark.parametrize("hid,lanes", [(64, 32), (64, 16), (64, 8), (32, 16), (32, 8)])
+def test_closed_loop_lane_groups_match_oracle(gpu, hid, lanes):
+    """The lane-group kernels (hidden 32 / 64, 16 actions of history): one env per 32, 16 or
+    8 lanes.  45 envs leave the last warp's groups partly without an env (they run on a
+    valid index and store nothing)."""
+    n, H, nh = 45, 23, 16
+    q, diff, d, veh, ld, S0, PR, desc, wts = setup(n, H, 1, seed=5, n_hist=nh, hidden=hid,
+                                                   ckpt=6, lanes=lanes)
+    actor = O.init_params(d, 0, 18 + 4 * nh, hid, 4).astype(np.float32)
+    AW = torch.tensor(actor, device="cuda")
+    loss = torch.zeros(ld, device="cuda")
+    gw = torch.zeros_like(AW)
+    gp = torch.zeros(4, ld, device="cuda")
+    aout = torch.zeros(H, 4, ld, device="cuda")
+    ws = torch.empty(q.qsim_vjp_workspace(desc) // 4 + 1, device="cuda")
+    q.qsim_rollout_vjp(desc, veh, S0, PR, None, AW, None, loss, None, gw, gp, aout, ws)
+    torch.cuda.synchronize()
+    ref = O.diff_run(d, f64(S0)[:, :n].T, f64(PR)[:, :n].T, H, wts, mode=1,
+                     actor=actor.astype(np.float64), hidden=hid, n_hist=nh)
+    close(f64(loss)[:n], ref["loss"], "loss")
+    close(f64(aout)[:, :, :n].transpose(2, 0, 1), ref["act_out"], "actions")
+    close(f64(gw), ref["g_actor"], "g_actor")
+    close(f64(gp)[:, :n].T, ref["g_prm"][:, :4], "g_params")
+
+
+def test_vjp_rejects_bad_lane_groups(gpu):
+    q, diff, d, veh, ld, S0, PR, desc, wts = setup(8, 5, 1, lanes=12)
+    assert q.qsim_vjp_workspace(desc) == 0
 
 
 def test_vjp_matches_finite_differences_of_oracle_forward(gpu):

@@ -343,6 +343,39 @@ def test_recalc_rewards_parity(gpu):
         q.qsim_destroy(h)
 
 
+def test_recalc_rewards_batch_equals_per_set(gpu):
+    """One launch over several env sets (different sizes, fill levels and reward constants)
+    gives bit for bit what qsim_recalc_rewards gives on each set."""
+    q = gpu
+    sets = []
+    try:
+        for k, (n, cap, steps) in enumerate(((40, 30, 45), (7, 16, 9), (300, 12, 20), (64, 8, 0))):
+            d, cfg, veh = lib_config(q, "c2", n_envs=n, capacity=cap, episode_len=7, learning_starts=0,
+                                     seed=k, run_id=k)
+            pair = []
+            for _ in range(2):
+                h = q.qsim_create(cfg, veh)
+                q.qsim_rollout_engine(h, SIMT)
+                if steps:
+                    q.qsim_rollout(h, torch.tensor(_actor(d, 64), device="cuda"), 64, steps, 0.3)
+                C2 = list(W.REWARD)
+                C2[4] = 0.2 + 0.1 * k
+                q.qsim_set_reward(h, C2, 0.1)
+                pair.append(h)
+            sets.append(pair)
+        for a, _ in sets:
+            q.qsim_recalc_rewards(a)
+        q.qsim_recalc_rewards_batch([b for _, b in sets])
+        torch.cuda.synchronize()
+        for a, b in sets:
+            ra, rb = cpu(q.qsim_info_get(a)["records"]), cpu(q.qsim_info_get(b)["records"])
+            assert np.array_equal(ra.view(np.uint32), rb.view(np.uint32))
+    finally:
+        for pair in sets:
+            for h in pair:
+                q.qsim_destroy(h)
+
+
 def test_partitioned_schedule_is_bitwise_identical(gpu):
     """Env partitions on internal streams, advanced in time chunks, give exactly the
     single-launch results (same per-env arithmetic, different launch grouping)."""

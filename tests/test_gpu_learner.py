@@ -86,11 +86,15 @@ def make_run(q, n_env=3, cap=64, hidden=32, batch=64, cluster=1, layout=0, steps
                                                          (4, 1, 32, 128), (1, 2, 16, 32),
                                                          (8, 0, 128, 256), (1, 0, 128, 128),
                                                          (2, 3, 64, 64), (16, 0, 64, 256),
-                                                         (1, 0, 128, 512), (0, 1, 64, 256)])
+                                                         (1, 0, 128, 512), (0, 1, 64, 256),
+                                                         (1, 0, 64, 256), (1, 1, 64, 128),
+                                                         (1, 0, 32, 128), (2, 0, 64, 256)])
 def test_ac_update_parity(gpu, cluster, layout, hidden, batch):
     """Cluster 16 at hidden 64 / batch 256 is the single run's automatic choice; hidden 128
     with batch 512 on one CTA is the largest shape of the batched workload; cluster 0 is
-    the automatic choice with the privileged critic."""
+    the automatic choice with the privileged critic.  CTAs holding whole 128-sample tiles
+    (1 x 128 .. 512, 2 x 128) run the target actor and target critics on the tensor cores,
+    at hidden 32, 64 and 128 and with the privileged critic."""
     q = gpu
     d, h, a, hp = make_run(q, hidden=hidden, batch=batch, cluster=cluster, layout=layout)
     try:
