@@ -46,7 +46,7 @@ BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, fl
 # Set to None whenever the kernel changes until it is captured again.
 NCU_DRAM_BYTES_PER_ENV_STEP = (46.710016e6 + 289.403648e6) / (32768 * 100)
 # same for the tensor-core kernel k_rollout_tc (profiles/k_rollout_tc_c2_65536x1000.md)
-NCU_DRAM_BYTES_PER_ENV_STEP_TC = (35.502592e6 + 98.719744e6) / (65536 * 20)
+NCU_DRAM_BYTES_PER_ENV_STEP_TC = (35.447040e6 + 98.399488e6) / (65536 * 20)
 
 
 def parse():
@@ -66,6 +66,7 @@ def parse():
                     help="only reward recalculation over a filled ring of --envs x SLOTS records")
     ap.add_argument("--only-dynamics", type=int, default=0, metavar="STEPS",
                     help="only the dynamics-only kernel, 8,192 envs x STEPS steps (profiling)")
+    ap.add_argument("--dyn-envs", type=int, default=8192, help="with --only-dynamics: envs")
     ap.add_argument("--only-c5", action="store_true",
                     help="only the c5 sample (full replay rings, recalculation), for profiling")
     ap.add_argument("--only-diff", action="store_true",
@@ -739,11 +740,12 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         q.load()
         veh = q.make_params(W.config("c1"))
-        out = torch.empty(17, 8192, device="cuda")
+        n = args.dyn_envs
+        out = torch.empty(17, q.padded(n), device="cuda")
         for _ in range(2):
-            q.qsim_dynamics_bench(veh, 8192, 8192, args.only_dynamics, 0.01, out)
+            q.qsim_dynamics_bench(veh, n, q.padded(n), args.only_dynamics, 0.01, out)
         torch.cuda.synchronize()
-        print(json.dumps({"dynamics_only": {"envs": 8192, "steps": args.only_dynamics,
+        print(json.dumps({"dynamics_only": {"envs": n, "steps": args.only_dynamics,
                                             "finite": bool(torch.isfinite(out).all())}}))
         return
     if args.only_c5:

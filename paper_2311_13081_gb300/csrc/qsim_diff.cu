@@ -864,8 +864,18 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g, int fs, int 
             const float* src = j < H ? dZ1 + (size_t)j * fs : (j < 2 * H ? dZ2 + (size_t)(j - H) * fs
                                                                          : dZ3 + (size_t)(j - 2 * H) * fs);
             float* dst = j < H ? gb1 + j : (j < 2 * H ? gb2 + (j - H) : gb3 + (j - 2 * H));
-            float s = 0.0f;
-            for (int q = 0; q < nk; ++q) s += ldcg(src + (size_t)q * es);
+            // 8 loads in flight per thread, 8 running sums added in a fixed order
+            float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            int q = 0;
+            for (; q + 8 <= nk; q += 8) {
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = ldcg(src + (size_t)(q + u) * es);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] += v[u];
+            }
+            for (; q < nk; ++q) acc[0] += ldcg(src + (size_t)q * es);
+            const float s = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
             *dst = first ? s : *dst + s;
         }
         __syncthreads();
