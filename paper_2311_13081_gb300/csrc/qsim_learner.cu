@@ -433,7 +433,9 @@ __device__ __noinline__ void env_step_small(RunDesc& R, uint32_t t, int64_t slot
     float* mus = h2 + 8 * LH;                         // [8][4]
     float* park = mus + 8 * 4;                        // [8][32]: env data across the layers
     if (!warm) {
-        const int nv = PA >> 2;
+        // 16-byte copies need a 16-byte aligned source (the actor opens the learner's
+        // allocation, so it is); otherwise every element goes through the tail loop
+        const int nv = ((uintptr_t)R.actor & 15u) == 0 ? PA >> 2 : 0;
         const uint32_t sW = (uint32_t)__cvta_generic_to_shared(Ws);
         for (int v = threadIdx.x; v < nv; v += LT)
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(sW + 16u * (uint32_t)v),
