@@ -221,11 +221,13 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Same with A stored [k][m] (lda): used for the weight gradients dW = dZ^T X, whose
-// reduction runs over the chunk's rows.
-template <class Epi>
-__device__ __forceinline__ void gemm_km(int M, int N, int K, const float* A, int lda,
-                                        const float* B, int ldb, Epi epi) {
+// Weight-gradient accumulation G(m, n) (+)= sum_k A(m, k) B(k, n) with A stored [k][m]
+// (lda) and B [k][n] (ldb): dW = dZ^T X, reduced over the chunk's rows.  G (row stride ldg)
+// is overwritten when `first`, else added to; its previous values are read before the
+// reduction starts, 16 independent loads per tile whose latency the k loop hides (G may be
+// the L2-resident gradient output itself).
+__device__ __forceinline__ void gemm_km_acc(int M, int N, int K, const float* A, int lda,
+                                            const float* B, int ldb, float* G, int ldg, bool first) {
     const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
     for (int m0 = 0; m0 < M; m0 += 64)
         for (int n0 = 0; n0 < N; n0 += 64) {
@@ -235,7 +237,8 @@ __device__ __forceinline__ void gemm_km(int M, int N, int K, const float* A, int
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+                for (int j = 0; j < 4; ++j)
+                    acc[i][j] = (!first && mb + i < M && nb + j < N) ? G[(mb + i) * ldg + nb + j] : 0.0f;
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
                 const float4 a = *reinterpret_cast<const float4*>(A + k * lda + mb);
@@ -250,7 +253,7 @@ __device__ __forceinline__ void gemm_km(int M, int N, int K, const float* A, int
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (mb + i < M && nb + j < N) epi(mb + i, nb + j, acc[i][j]);
+                    if (mb + i < M && nb + j < N) G[(mb + i) * ldg + nb + j] = acc[i][j];
         }
     __syncthreads();
 }
@@ -418,9 +421,7 @@ __device__ __forceinline__ void backward(int in, int H, int out, int r0, int mc,
     }
     __syncthreads();
     if (want_w) {
-        gemm_km(H, H, mc, b.dZ2s, as, b.H1s, as, [&](int m, int n, float v) {
-            b.gW2[m * b.g2 + n] = first ? v : b.gW2[m * b.g2 + n] + v;
-        });
+        gemm_km_acc(H, H, mc, b.dZ2s, as, b.H1s, as, b.gW2, b.g2, first);
         for (int j = threadIdx.x; j < H; j += LT) {
             float s = 0.0f;
             for (int r = 0; r < mc; ++r) s += b.dZ2s[r * as + j];
@@ -431,9 +432,7 @@ __device__ __forceinline__ void backward(int in, int H, int out, int r0, int mc,
         b.dZ1s[m * as + n] = b.H1s[m * as + n] > 0.0f ? v : 0.0f;
     });
     if (want_w) {
-        gemm_km(H, in, mc, b.dZ1s, as, b.Xs, INP, [&](int m, int n, float v) {
-            b.gW1[m * b.g1 + n] = first ? v : b.gW1[m * b.g1 + n] + v;
-        });
+        gemm_km_acc(H, in, mc, b.dZ1s, as, b.Xs, INP, b.gW1, b.g1, first);
         for (int j = threadIdx.x; j < H; j += LT) {
             float s = 0.0f;
             for (int r = 0; r < mc; ++r) s += b.dZ1s[r * as + j];
