@@ -205,6 +205,21 @@ qsim_status qsim_sync(qsim_handle* h);
  * (No counterpart in the paper.) */
 int32_t qsim_set_wait_limit(qsim_handle* h, int32_t polls);
 
+/* Debug bounds checks (no counterpart in the paper).  The library built with
+ * -DQSIM_BOUNDS_CHECK=1 (paper_2311_13081_gb300.build.build(bounds_check=True), a separate
+ * shared object) checks every replay-ring slot and SoA env index that a kernel computes
+ * before it reads or writes the ring (rollouts, env step, learner env step and replay
+ * gather, reward recalculation) against the allocation; the first index outside [0, n)
+ * skips that access and is reported by qsim_sync as QSIM_ESTATE, with the site, the index
+ * and n in qsim_last_error().  qsim_bounds_checked() returns 1 in that build, 0 otherwise.
+ * qsim_bounds_probe reads the packed flag word of (slot, env) into *flags_out (device,
+ * 4 bytes) through the same check: in the checked build an index outside the ring is
+ * passed to the kernel, which records it and skips the read; in the default build it is
+ * refused on the host with QSIM_EINVAL.  Asynchronous on `stream`. */
+int32_t qsim_bounds_checked(void);
+qsim_status qsim_bounds_probe(qsim_handle* h, int64_t slot, int64_t env, uint32_t* flags_out,
+                              void* stream);
+
 /* Actor and critic observations of the current states (Sec. IV: o_a = {p, R, v, omega,
  * H} with noise of the current step; o_c privileged and noise-free, except in the
  * symmetric layout QSIM_CRITIC_ACTOR, where o_c = o_a).  obs_a

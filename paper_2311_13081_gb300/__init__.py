@@ -114,6 +114,8 @@ _SIGS = {
     "qsim_set_counters": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64]),
     "qsim_sync": (C.c_int, [P]),
     "qsim_set_wait_limit": (C.c_int32, [P, C.c_int32]),
+    "qsim_bounds_checked": (C.c_int32, []),
+    "qsim_bounds_probe": (C.c_int, [P, C.c_int64, C.c_int64, P, P]),
     "qsim_observe": (C.c_int, [P, P, P, P]),
     "qsim_step": (C.c_int, [P, P, P, P, P, P, P, P]),
     "qsim_rollout": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_float, P]),
@@ -344,6 +346,18 @@ def qsim_set_wait_limit(h, polls) -> int:
     if r < 0:
         _chk(r)
     return r
+
+
+def qsim_bounds_checked() -> bool:
+    """True when the loaded library was built with the debug bounds checks."""
+    load()
+    return bool(_lib.qsim_bounds_checked())
+
+
+def qsim_bounds_probe(h, slot, env, out: torch.Tensor, stream=None):
+    """Flag word of ring record (slot, env) into out (int32, 1 element) through the debug
+    bounds check (out-of-range indices: see include/qsim.h)."""
+    _chk(_lib.qsim_bounds_probe(h, int(slot), int(env), _ptr(out), _stream(stream)))
 
 
 def qsim_observe(h, obs_a=None, obs_c=None, stream=None):

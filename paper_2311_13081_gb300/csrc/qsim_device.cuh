@@ -397,10 +397,41 @@ __device__ __forceinline__ unsigned long long f2fma(unsigned long long a, unsign
 }
 
 // Device status codes (first error wins).
-enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADSIZE = 2, DEV_RANGE = 3 };
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADSIZE = 2, DEV_RANGE = 3, DEV_BOUNDS = 4 };
+
+// A handle's status is STATUS_WORDS ints: [0] the code above; with DEV_BOUNDS also [1] the
+// site, [2..3] the index and [4..5] the bound (64-bit, low word first).
+constexpr int STATUS_WORDS = 8;
 
 __device__ __forceinline__ void set_status(int* st, int code) {
     if (st) atomicCAS(st, DEV_OK, code);
+}
+
+// Debug bounds checks, compiled in with -DQSIM_BOUNDS_CHECK=1 (a separate build of the
+// library) and out otherwise.  Every replay-ring slot and every SoA env index that a kernel
+// computes before touching the ring is checked against its allocation; the first index
+// outside [0, n) records DEV_BOUNDS, the site, the index and n in the status words, and the
+// access is skipped.
+#ifndef QSIM_BOUNDS_CHECK
+#define QSIM_BOUNDS_CHECK 0
+#endif
+enum : int { SITE_RING_WRITE = 1, SITE_RING_READ = 2, SITE_SOA = 3, SITE_PROBE = 4 };
+
+__device__ __forceinline__ bool in_bounds(int* st, int64_t i, int64_t n, int site) {
+#if QSIM_BOUNDS_CHECK
+    if (i >= 0 && i < n) return true;
+    if (st && atomicCAS(st, DEV_OK, DEV_BOUNDS) == DEV_OK) {
+        st[1] = site;
+        st[2] = (int)(uint32_t)(uint64_t)i;
+        st[3] = (int)(uint32_t)((uint64_t)i >> 32);
+        st[4] = (int)(uint32_t)(uint64_t)n;
+        st[5] = (int)(uint32_t)((uint64_t)n >> 32);
+    }
+    return false;
+#else
+    (void)st; (void)i; (void)n; (void)site;
+    return true;
+#endif
 }
 
 }  // namespace qsim

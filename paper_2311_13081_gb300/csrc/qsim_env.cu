@@ -249,7 +249,8 @@ __global__ void k_step(EnvCfg C, EnvPtrs p, const float* __restrict__ actions, u
     const uint32_t ep_after = ep_before + 1;
     const bool term = terminated(C, s2);
     const bool trunc = !term && (int)ep_after >= C.episode_len;
-    if (has_buffer) {
+    if (has_buffer && in_bounds(p.status, slot, p.rows, SITE_RING_WRITE) &&
+        in_bounds(p.status, e, ld, SITE_SOA)) {
         float* rec = p.rec + (size_t)slot * C.F * ld;
 #pragma unroll
         for (int i = 0; i < NS; ++i) rec[i * ld + e] = s[i];
@@ -503,6 +504,7 @@ extern "C" qsim_status qsim_create(const qsim_config* cfg, const qsim_params* ve
     h->ld = (cfg->n_envs + 31) & ~31;
     h->dc = make_env_cfg(*cfg, *veh, h->n, h->ld);
     h->capacity = cfg->replay_capacity;
+    h->p.rows = h->capacity;
     h->t_now = h->head = h->size = 0;
     h->next_curriculum = cfg->curriculum_interval > 0 ? cfg->curriculum_interval : -1;
     h->rollout_warps = 0;
@@ -522,7 +524,8 @@ extern "C" qsim_status qsim_create(const qsim_config* cfg, const qsim_params* ve
               alloc((void**)&h->p.ep_ret, ld * 4) && alloc((void**)&h->p.ret_sum, ld * 4) &&
               alloc((void**)&h->p.ep_index, ld * 4) && alloc((void**)&h->p.ep_step, ld * 4) &&
               alloc((void**)&h->p.n_done, ld * 4) && alloc((void**)&h->p.len_sum, ld * 4) &&
-              alloc((void**)&h->p.rewardC, 8 * 4) && alloc((void**)&h->p.status, 4);
+              alloc((void**)&h->p.rewardC, 8 * 4) &&
+              alloc((void**)&h->p.status, STATUS_WORDS * 4);
     if (ok && h->capacity > 0) {
         ok = alloc((void**)&h->p.rec, (size_t)h->capacity * h->dc.F * ld * 4) &&
              alloc((void**)&h->p.side, (size_t)h->capacity * NS * ld * 4);
@@ -587,6 +590,28 @@ extern "C" qsim_status qsim_set_counters(qsim_handle* h, int64_t t_now, int64_t 
     return QSIM_OK;
 }
 
+// Reads the flag word of (slot, env) through the debug bounds check (a one-thread probe of
+// the status path: out-of-range indices reach it only in the checked build).
+__global__ void k_bounds_probe(EnvCfg C, EnvPtrs p, int64_t slot, int64_t env, uint32_t* out) {
+    if (in_bounds(p.status, slot, p.rows, SITE_PROBE) && in_bounds(p.status, env, C.ld, SITE_SOA))
+        *out = __float_as_uint(p.rec[((size_t)slot * C.F + 22) * (size_t)C.ld + (size_t)env]);
+}
+
+extern "C" int32_t qsim_bounds_checked(void) { return QSIM_BOUNDS_CHECK ? 1 : 0; }
+
+extern "C" qsim_status qsim_bounds_probe(qsim_handle* h, int64_t slot, int64_t env, uint32_t* flags_out,
+                                         void* stream) {
+    if (!h || !flags_out) return fail(QSIM_EINVAL, "qsim_bounds_probe: null argument");
+    if (h->capacity == 0) return fail(QSIM_ESTATE, "qsim_bounds_probe: env set has no replay buffer");
+    const bool inside = slot >= 0 && slot < h->capacity && env >= 0 && env < h->dc.ld;
+    if (!QSIM_BOUNDS_CHECK && !inside)
+        return fail(QSIM_EINVAL, "qsim_bounds_probe: (%lld, %lld) outside the ring (library built "
+                                 "without bounds checks)", (long long)slot, (long long)env);
+    k_bounds_probe<<<1, 1, 0, (cudaStream_t)stream>>>(h->dc, h->p, slot, env, flags_out);
+    QCHECK_CUDA(cudaGetLastError());
+    return QSIM_OK;
+}
+
 extern "C" int32_t qsim_set_wait_limit(qsim_handle* h, int32_t polls) {
     if (!h) return fail(QSIM_EINVAL, "qsim_set_wait_limit: null handle");
     if (polls < 0 || polls > (1 << 30)) return fail(QSIM_EINVAL, "qsim_set_wait_limit: %d polls", polls);
@@ -597,15 +622,23 @@ extern "C" int32_t qsim_set_wait_limit(qsim_handle* h, int32_t polls) {
 
 extern "C" qsim_status qsim_sync(qsim_handle* h) {
     if (!h) return fail(QSIM_EINVAL, "qsim_sync: null handle");
-    int st = 0;
-    QCHECK_CUDA(cudaMemcpy(&st, h->p.status, 4, cudaMemcpyDeviceToHost));
-    if (st != DEV_OK) {
-        cudaMemset(h->p.status, 0, 4);
-        if (st == DEV_TIMEOUT) return fail(QSIM_ETIMEOUT, "device-side wait ran out");
-        if (st == DEV_RANGE)
+    int st[STATUS_WORDS] = {};
+    QCHECK_CUDA(cudaMemcpy(st, h->p.status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st[0] != DEV_OK) {
+        cudaMemset(h->p.status, 0, sizeof(st));
+        if (st[0] == DEV_TIMEOUT) return fail(QSIM_ETIMEOUT, "device-side wait ran out");
+        if (st[0] == DEV_RANGE)
             return fail(QSIM_ESTATE, "tensor-core rollout: an actor weight, input or hidden activation "
                                      "was outside the half-precision range (|x| >= 65504) or not finite");
-        return fail(QSIM_ESTATE, "device reported status %d", st);
+        if (st[0] == DEV_BOUNDS) {
+            static const char* const sites[] = {"index", "replay-ring write slot", "replay-ring read slot",
+                                                "SoA env index", "probe slot"};
+            const int site = st[1] >= 1 && st[1] <= 4 ? st[1] : 0;
+            const long long idx = (long long)(((uint64_t)(uint32_t)st[3] << 32) | (uint32_t)st[2]);
+            const long long lim = (long long)(((uint64_t)(uint32_t)st[5] << 32) | (uint32_t)st[4]);
+            return fail(QSIM_ESTATE, "bounds check: %s %lld outside [0, %lld)", sites[site], idx, lim);
+        }
+        return fail(QSIM_ESTATE, "device reported status %d", st[0]);
     }
     return QSIM_OK;
 }

@@ -15,6 +15,7 @@ struct EnvPtrs {
     float *state, *prm, *dist, *hist, *ep_ret, *ret_sum;
     uint32_t *ep_index, *ep_step, *n_done, *len_sum;
     float *rec, *side;
+    int64_t rows;    // slots allocated in rec and side (the replay capacity)
     float* rewardC;  // [8]: C_rp C_rq C_rv C_rw C_ra C_rab C_rs, sigma_e
     int* status;
 };

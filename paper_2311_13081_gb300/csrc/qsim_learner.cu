@@ -351,7 +351,8 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
         const bool term = terminated(C, s2);
         const uint32_t ep_after = ep_step + 1;
         const bool trunc = !term && (int)ep_after >= C.episode_len;
-        if (R.capacity > 0) {
+        if (R.capacity > 0 && in_bounds(R.E.status, slot, R.E.rows, SITE_RING_WRITE) &&
+            in_bounds(R.E.status, e, ld, SITE_SOA)) {
             float* rec = R.E.rec + (size_t)slot * C.F * ld + e;
 #pragma unroll
             for (int i = 0; i < NS; ++i) rec[i * ld] = s[i];
@@ -559,7 +560,8 @@ __device__ __noinline__ void env_step_small(RunDesc& R, uint32_t t, int64_t slot
     const bool term = terminated(C, s2);
     const uint32_t ep_after = ep_step + 1;
     const bool trunc = !term && (int)ep_after >= C.episode_len;
-    if (R.capacity > 0) {
+    if (R.capacity > 0 && in_bounds(R.E.status, slot, R.E.rows, SITE_RING_WRITE) &&
+        in_bounds(R.E.status, e, ld, SITE_SOA)) {
         float* rec = R.E.rec + (size_t)slot * C.F * ld + e;
 #pragma unroll
         for (int i = 0; i < NS; ++i) rec[i * ld] = s[i];
@@ -634,6 +636,8 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
     float* T_oc2 = T_oc + (size_t)G * DC;
     float* T_r = T_oc2 + (size_t)G * DC;
     float* T_term = T_r + G;
+    int* const bst = R.E.status;
+    const int64_t rows = R.E.rows;
     if (jl < G) {
         const int j = j0 + g0 + jl;
         const int64_t lost = size == CAP ? nh : 0;
@@ -646,85 +650,90 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
         const int env = (int)(idx % (uint32_t)NE);
         const int64_t slot = ring(head - size + lost + k, CAP);
         const uint32_t t_rec = (uint32_t)(t_now - size + lost + k);
-        const float* rec = R.E.rec + (size_t)slot * F * ld + env;
-        const uint32_t fl = __float_as_uint(ldcg(rec + 22 * ld));
-        const bool done = (fl & 3u) != 0;
-        const uint32_t ep = fl >> 8;
-        float* oa = T_oa + (size_t)jl * DA;
-        float* oa2 = T_oa2 + (size_t)jl * DA;
-        float* oc = T_oc + (size_t)jl * DC;
-        float* oc2 = T_oc2 + (size_t)jl * DC;
-        if (w < 2) {
-            // w == 0: s_t -> o_a, o_c (+ stored action, reward, flag); w == 1: s_{t+1} -> o_a', o_c'
-            const float* src = w == 0 ? rec
-                                      : (done ? R.E.side + (size_t)slot * NS * ld + env
-                                              : R.E.rec + (size_t)ring(slot + 1, CAP) * F * ld + env);
-            float st[NS], a[4], pv[NPRIV];
+        // (debug builds) a slot or env outside the ring skips the sample, status set
+        if (in_bounds(bst, slot, rows, SITE_RING_READ) && in_bounds(bst, env, ld, SITE_SOA)) {
+            const float* rec = R.E.rec + (size_t)slot * F * ld + env;
+            const uint32_t fl = __float_as_uint(ldcg(rec + 22 * ld));
+            const bool done = (fl & 3u) != 0;
+            const uint32_t ep = fl >> 8;
+            float* oa = T_oa + (size_t)jl * DA;
+            float* oa2 = T_oa2 + (size_t)jl * DA;
+            float* oc = T_oc + (size_t)jl * DC;
+            float* oc2 = T_oc2 + (size_t)jl * DC;
+            const bool nxt_ok = w != 1 || done || in_bounds(bst, ring(slot + 1, CAP), rows, SITE_RING_READ);
+            if (w < 2 && nxt_ok) {
+                // w == 0: s_t -> o_a, o_c (+ stored action, reward, flag); w == 1: s_{t+1} -> o_a', o_c'
+                const float* src = w == 0 ? rec
+                                          : (done ? R.E.side + (size_t)slot * NS * ld + env
+                                                  : R.E.rec + (size_t)ring(slot + 1, CAP) * F * ld + env);
+                float st[NS], a[4], pv[NPRIV];
 #pragma unroll
-            for (int i = 0; i < NS; ++i) st[i] = ldcg(src + i * ld);
+                for (int i = 0; i < NS; ++i) st[i] = ldcg(src + i * ld);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = w == 0 ? ldcg(rec + (17 + i) * ld) : 0.0f;
+                for (int i = 0; i < 4; ++i) a[i] = w == 0 ? ldcg(rec + (17 + i) * ld) : 0.0f;
 #pragma unroll
-            for (int q = 0; q < NPRIV; ++q) pv[q] = C.n_priv ? ldcg(rec + (23 + q) * ld) : 0.0f;
-            const float r = w == 0 ? ldcg(rec + 21 * ld) : 0.0f;
-            float* ocx = w == 0 ? oc : oc2;
-            float* oax = w == 0 ? oa : oa2;
-            float o[18];
-            obs_state(st, o);
-            // critic observations (noise-free; the symmetric layout 3 copies the actor's
-            // noisy observation below)
-            if (C.critic_layout != 3) {
+                for (int q = 0; q < NPRIV; ++q) pv[q] = C.n_priv ? ldcg(rec + (23 + q) * ld) : 0.0f;
+                const float r = w == 0 ? ldcg(rec + 21 * ld) : 0.0f;
+                float* ocx = w == 0 ? oc : oc2;
+                float* oax = w == 0 ? oa : oa2;
+                float o[18];
+                obs_state(st, o);
+                // critic observations (noise-free; the symmetric layout 3 copies the actor's
+                // noisy observation below)
+                if (C.critic_layout != 3) {
 #pragma unroll
-                for (int q = 0; q < 18; ++q) ocx[q] = o[q];
-                const int rpm_at = C.critic_layout == 2 ? 18 : DA;
+                    for (int q = 0; q < 18; ++q) ocx[q] = o[q];
+                    const int rpm_at = C.critic_layout == 2 ? 18 : DA;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) ocx[rpm_at + i] = rpm_norm(C.veh, st[13 + i]);
-                if (C.critic_layout != 0) {
+                    for (int i = 0; i < 4; ++i) ocx[rpm_at + i] = rpm_norm(C.veh, st[13 + i]);
+                    if (C.critic_layout != 0) {
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) ocx[rpm_at + 4 + q] = pv[q];
+                        for (int q = 0; q < 6; ++q) ocx[rpm_at + 4 + q] = pv[q];
+                    }
                 }
-            }
-            if (w == 0) {
+                if (w == 0) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) oc[DC - 4 + i] = a[i];
-                T_r[jl] = r;
-                T_term[jl] = (fl & 1u) ? 1.0f : 0.0f;
-            }
-            if (C.any_noise) {
-                float nz[18];
-                obs_noise(C, (uint32_t)env, t_rec + (uint32_t)w, nz);
+                    for (int i = 0; i < 4; ++i) oc[DC - 4 + i] = a[i];
+                    T_r[jl] = r;
+                    T_term[jl] = (fl & 1u) ? 1.0f : 0.0f;
+                }
+                if (C.any_noise) {
+                    float nz[18];
+                    obs_noise(C, (uint32_t)env, t_rec + (uint32_t)w, nz);
 #pragma unroll
-                for (int q = 0; q < 18; ++q) o[q] += nz[q];
-            }
-#pragma unroll
-            for (int q = 0; q < 18; ++q) oax[q] = o[q];
-            if (C.critic_layout == 3) {
-#pragma unroll
-                for (int q = 0; q < 18; ++q) ocx[q] = o[q];
-            }
-        } else {
-            // history: o_a has a_{t-1..t-NH}, o_a' has a_t, a_{t-1..t-NH+1}; zeros before the
-            // episode start.  Warp w handles lags i = w-1, w+5, w+11.
-            for (int i = w - 1; i <= nh; i += 6) {
-                const bool ok = (uint32_t)i <= ep;
-                const bool ok2 = i == 1 || (uint32_t)(i - 1) <= ep;
-                const float* ap = R.E.rec + (size_t)ring(slot - i, CAP) * F * ld + env + 17 * ld;
-                const float* ap2 = i == 1 ? rec + 17 * ld
-                                          : R.E.rec + (size_t)ring(slot - i + 1, CAP) * F * ld + env + 17 * ld;
-                float h[4], h2[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    h[c] = ok ? ldcg(ap + c * ld) : 0.0f;
-                    h2[c] = ok2 ? ldcg(ap2 + c * ld) : 0.0f;
+                    for (int q = 0; q < 18; ++q) o[q] += nz[q];
                 }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int q = 18 + 4 * (i - 1) + c;
-                    oa[q] = h[c];
-                    oa2[q] = h2[c];
-                    if (C.critic_layout != 2) {
-                        oc[q] = h[c];
-                        oc2[q] = h2[c];
+                for (int q = 0; q < 18; ++q) oax[q] = o[q];
+                if (C.critic_layout == 3) {
+#pragma unroll
+                    for (int q = 0; q < 18; ++q) ocx[q] = o[q];
+                }
+            } else if (w >= 2) {
+                // history: o_a has a_{t-1..t-NH}, o_a' has a_t, a_{t-1..t-NH+1}; zeros before the
+                // episode start.  Warp w handles lags i = w-1, w+5, w+11.
+                for (int i = w - 1; i <= nh; i += 6) {
+                    const bool ok = (uint32_t)i <= ep && in_bounds(bst, ring(slot - i, CAP), rows, SITE_RING_READ);
+                    const bool ok2 = i == 1 || ((uint32_t)(i - 1) <= ep &&
+                                                in_bounds(bst, ring(slot - i + 1, CAP), rows, SITE_RING_READ));
+                    const float* ap = R.E.rec + (size_t)ring(slot - i, CAP) * F * ld + env + 17 * ld;
+                    const float* ap2 = i == 1 ? rec + 17 * ld
+                                              : R.E.rec + (size_t)ring(slot - i + 1, CAP) * F * ld + env + 17 * ld;
+                    float h[4], h2[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        h[c] = ok ? ldcg(ap + c * ld) : 0.0f;
+                        h2[c] = ok2 ? ldcg(ap2 + c * ld) : 0.0f;
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int q = 18 + 4 * (i - 1) + c;
+                        oa[q] = h[c];
+                        oa2[q] = h2[c];
+                        if (C.critic_layout != 2) {
+                            oc[q] = h[c];
+                            oc2[q] = h2[c];
+                        }
                     }
                 }
             }

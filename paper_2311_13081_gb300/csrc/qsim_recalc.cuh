@@ -67,7 +67,13 @@ __device__ __forceinline__ void recalc_range(const EnvCfg& C, const EnvPtrs& p, 
         int64_t slot = head - size + (int64_t)k;  // in [-capacity, capacity)
         if (slot < 0) slot += capacity;
         const int64_t next = slot + 1 == capacity ? 0 : slot + 1;
-        recalc_quad(C, p, Cr, slot, next, (int64_t)k == size - 1, (int)q);
+        const bool newest = (int64_t)k == size - 1;
+        // (debug builds) slots and the env quad checked against the allocation
+        if (!in_bounds(p.status, slot, p.rows, SITE_RING_READ) ||
+            (!newest && !in_bounds(p.status, next, p.rows, SITE_RING_READ)) ||
+            !in_bounds(p.status, 4 * (int64_t)q + 3, C.ld, SITE_SOA))
+            continue;
+        recalc_quad(C, p, Cr, slot, next, newest, (int)q);
     }
 }
 

@@ -449,23 +449,25 @@ __global__ void __launch_bounds__(NW * 32) k_rollout(EnvCfg C, EnvPtrs p,
         const bool trunc = !term && (int)ep_after >= C.episode_len;
         // ---------------- transition record (field-major, streaming stores)
         if (capacity > 0) {
-            float* rec = p.rec + (size_t)slot * F * ld + g;
+            if (in_bounds(p.status, slot, p.rows, SITE_RING_WRITE) && in_bounds(p.status, g, ld, SITE_SOA)) {
+                float* rec = p.rec + (size_t)slot * F * ld + g;
 #pragma unroll
-            for (int i = 0; i < NS; ++i) __stcs(rec + i * ld, s[i]);
+                for (int i = 0; i < NS; ++i) __stcs(rec + i * ld, s[i]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) __stcs(rec + (17 + i) * ld, a[i]);
-            __stcs(rec + 21 * ld, r);
-            __stcs(rec + 22 * ld, __uint_as_float(pack_flags(term, trunc, ep_step)));
-            if (C.n_priv) {
-                float pv[NPRIV];
-                priv_vals(C, P, d, pv);
+                for (int i = 0; i < 4; ++i) __stcs(rec + (17 + i) * ld, a[i]);
+                __stcs(rec + 21 * ld, r);
+                __stcs(rec + 22 * ld, __uint_as_float(pack_flags(term, trunc, ep_step)));
+                if (C.n_priv) {
+                    float pv[NPRIV];
+                    priv_vals(C, P, d, pv);
 #pragma unroll
-                for (int k = 0; k < NPRIV; ++k) __stcs(rec + (23 + k) * ld, pv[k]);
-            }
-            if (term || trunc) {
-                float* sd = p.side + (size_t)slot * NS * ld + g;
+                    for (int k = 0; k < NPRIV; ++k) __stcs(rec + (23 + k) * ld, pv[k]);
+                }
+                if (term || trunc) {
+                    float* sd = p.side + (size_t)slot * NS * ld + g;
 #pragma unroll
-                for (int i = 0; i < NS; ++i) __stcs(sd + i * ld, s2[i]);
+                    for (int i = 0; i < NS; ++i) __stcs(sd + i * ld, s2[i]);
+                }
             }
             slot = (slot + 1 == capacity) ? 0 : slot + 1;
         }

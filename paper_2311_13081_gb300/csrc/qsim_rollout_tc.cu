@@ -644,7 +644,8 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 }
                 // ---------------- transition record (field-major, streaming stores)
                 if (capacity > 0) {
-                    if (active) {
+                    if (active && in_bounds(p.status, slot, p.rows, SITE_RING_WRITE) &&
+                        in_bounds(p.status, g, ld, SITE_SOA)) {
                         float* rec = p.rec + (size_t)slot * F * ld + g;
 #pragma unroll
                         for (int i = 0; i < NS; ++i) __stcs(rec + i * ld, s[i]);

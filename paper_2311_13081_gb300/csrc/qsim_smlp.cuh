@@ -5,9 +5,10 @@
 // activations stay in shared memory between layers; weight gradients accumulate across
 // chunks and are written out once.  Compared with the global-scratch path this replaces
 // ~30 L2 round trips per update with one weight stage per pass.  Two shapes: hidden <= 64
-// (64-row chunks, gradient accumulators in shared memory) and hidden <= 128 (32-row
+// (64-row chunks, gradient accumulators in shared memory) and hidden <= 128 (64-row
 // chunks, gradients accumulated directly in the CTA's own gradient output, which stays in
-// L2: there is no room for both next to the 128-wide weights).
+// L2: there is no room for both next to the 128-wide weights; the backward's deltas
+// overwrite the hidden activations they are masked with, dZ2 over H2 and dZ1 over H1).
 //
 // Layouts (floats): everything row-major with padded row strides chosen == 4 (mod 32) so
 // that the GEMMs' 128-bit shared loads are conflict-free: input chunk Xs[r][k], hidden
@@ -25,7 +26,7 @@ constexpr int LD1 = 100;  // row stride of W1 [j][k] (>= input width, == 4 mod 3
 constexpr int LD2 = 68;   // row stride of W2 [j][k]
 constexpr int MC = 64;    // rows per chunk
 // the 128-wide shape
-constexpr int HP2 = 128, AS2 = 132, LD22 = 132, MC2 = 32;
+constexpr int HP2 = 128, AS2 = 132, LD22 = 132, MC2 = 64;
 
 struct Buf {
     float *Xs, *H1s, *H2s, *dZ2s, *dZ1s, *dZ3s;
@@ -43,7 +44,7 @@ __host__ __device__ constexpr int floats() {
 }
 
 __host__ __device__ constexpr int floats2() {
-    return MC2 * INP + 4 * MC2 * AS2 + MC2 * 4 +                  // activations
+    return MC2 * INP + 2 * MC2 * AS2 + MC2 * 4 +                  // activations (deltas in place)
            HP2 * LD1 + HP2 + HP2 * LD22 + HP2 + 4 * HP2 + 4 + 64;  // weights (+ slack)
 }
 
@@ -81,8 +82,8 @@ __device__ __forceinline__ Buf carve2(float* sm) {
     b.Xs = p; p += MC2 * INP;
     b.H1s = p; p += MC2 * AS2;
     b.H2s = p; p += MC2 * AS2;
-    b.dZ2s = p; p += MC2 * AS2;
-    b.dZ1s = p; p += MC2 * AS2;
+    b.dZ2s = b.H2s;  // each delta replaces the activation that masks it (see backward)
+    b.dZ1s = b.H1s;
     b.dZ3s = p; p += MC2 * 4;
     b.W1s = p; p += HP2 * LD1;
     b.b1 = p; p += HP2;
@@ -412,7 +413,10 @@ __device__ __forceinline__ void backward(int in, int H, int out, int r0, int mc,
             for (int r = 0; r < mc; ++r) s += b.dZ3s[r * 4 + threadIdx.x];
             b.gb3[threadIdx.x] = first ? s : b.gb3[threadIdx.x] + s;
         }
+        if (b.dZ2s == b.H2s) __syncthreads();  // H2 read above, overwritten below
     }
+    // dZ2 in place over H2 is safe: each element is read (mask) and written by one thread;
+    // likewise dZ1 over H1 in gemm_mk's epilogue, whose operands are dZ2 and W2
     for (int i = threadIdx.x; i < mc * H; i += LT) {
         const int r = i / H, j = i - r * H;
         float v = 0.0f;
