@@ -483,37 +483,44 @@ __device__ __noinline__ void env_step_small(RunDesc& R, uint32_t t, int64_t slot
     if (!warm) {
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
-        // layer 1 and 2: one warp per output unit, lanes over the inputs, shuffle sums
+        // layers: one warp per output unit; the warp's lanes split into n groups of L (one
+        // group per env), each group's lanes over the inputs, group-wide shuffle sums
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int L = n <= 1 ? 32 : (n <= 2 ? 16 : (n <= 4 ? 8 : 4));
+        const int r = lane / L, kq = lane - r * L;
+        const bool on = r < n;
+        auto gsum = [&](float v) {
+            for (int o = L >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            return v;
+        };
         const float* b1 = Ws + H * DA;
         const float* W2 = b1 + H;
         const float* b2 = W2 + H * H;
         const float* W3 = b2 + H;
         const float* b3 = W3 + 4 * H;
         for (int j = warp; j < H; j += LT / 32) {
-            for (int r = 0; r < n; ++r) {
-                float acc = 0.0f;
-                for (int k = lane; k < DA; k += 32) acc = fmaf(Ws[j * DA + k], xs[r * LX + k], acc);
-                acc = smlp::warp_sum(acc) + b1[j];
-                if (lane == 0) h1[r * LH + j] = fmaxf(acc, 0.0f);
-            }
+            float acc = 0.0f;
+            if (on)
+                for (int k = kq; k < DA; k += L) acc = fmaf(Ws[j * DA + k], xs[r * LX + k], acc);
+            acc = gsum(acc) + b1[j];
+            if (on && kq == 0) h1[r * LH + j] = fmaxf(acc, 0.0f);
         }
         __syncthreads();
         for (int j = warp; j < H; j += LT / 32) {
-            for (int r = 0; r < n; ++r) {
-                float acc = 0.0f;
-                for (int k = lane; k < H; k += 32) acc = fmaf(W2[j * H + k], h1[r * LH + k], acc);
-                acc = smlp::warp_sum(acc) + b2[j];
-                if (lane == 0) h2[r * LH + j] = fmaxf(acc, 0.0f);
-            }
+            float acc = 0.0f;
+            if (on)
+                for (int k = kq; k < H; k += L) acc = fmaf(W2[j * H + k], h1[r * LH + k], acc);
+            acc = gsum(acc) + b2[j];
+            if (on && kq == 0) h2[r * LH + j] = fmaxf(acc, 0.0f);
         }
         __syncthreads();
-        for (int item = warp; item < 4 * n; item += LT / 32) {
-            const int r = item >> 2, o = item & 3;
+        if (warp < 4) {
+            const int o = warp;
             float acc = 0.0f;
-            for (int k = lane; k < H; k += 32) acc = fmaf(W3[o * H + k], h2[r * LH + k], acc);
-            acc = smlp::warp_sum(acc) + b3[o];
-            if (lane == 0) mus[r * 4 + o] = tanhf(acc);
+            if (on)
+                for (int k = kq; k < H; k += L) acc = fmaf(W3[o * H + k], h2[r * LH + k], acc);
+            acc = gsum(acc) + b3[o];
+            if (on && kq == 0) mus[r * 4 + o] = tanhf(acc);
         }
     }
     __syncthreads();
@@ -1162,6 +1169,14 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
     // the pure forward passes (target actor, target critics) on the tensor cores when the
     // CTA holds whole 128-row tiles
     const bool tcf_on = tmem_ok && tcf::eligible(R, Bc);
+    // With an even cluster whose CTA pairs' rows fit one chunk, the twin critics are split
+    // over the two halves: CTA rk runs critic cs = rk / half (target and current) on the
+    // rows of the pair (rr, rr + half), rr = rk mod half, read from both owners' scratch.
+    const int half = nS >> 1;
+    const bool split = !tcf_on && half > 0 && (nS & 1) == 0 && 2 * Bc <= MC;
+    const int cs = split ? rk / half : 0, rr = split ? rk - cs * half : rk;
+    const ptrdiff_t d0 = (ptrdiff_t)(rr - rk) * (ptrdiff_t)scr_stride;
+    const ptrdiff_t d1 = (ptrdiff_t)(rr + half - rk) * (ptrdiff_t)scr_stride;
     // a10: target actor + smoothing
     if (tcf_on) {
         tc_forward(R.actor_t, DA, H, 4, S.oa2, DA, Bc, S.mu, 4, true, sm, tmem, R.E.status);
@@ -1181,7 +1196,13 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
     }
     __syncthreads();
     // a11: twin target critics
-    if (tcf_on) {
+    if (split) {
+        cluster_sync_all(nS);  // the pair's o_c' rows are complete
+        float* qt = cs ? S.q2 : S.q1;
+        stage(cs ? R.c2_t : R.c1_t, DC, H, 1, b);
+        forward2(DC, H, 1, S.oc2 + d0, S.oc2 + d1, DC, Bc, 2 * Bc, b, qt + d0, qt + d1, 1, false);
+        cluster_sync_all(nS);  // both target values of the pair's rows are complete
+    } else if (tcf_on) {
         tc_forward(R.c1_t, DC, H, 1, S.oc2, DC, Bc, S.q1, 1, false, sm, tmem, R.E.status);
         tc_forward(R.c2_t, DC, H, 1, S.oc2, DC, Bc, S.q2, 1, false, sm, tmem, R.E.status);
     } else {
@@ -1190,14 +1211,34 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
         stage(R.c2_t, DC, H, 1, b);
         for (int r0 = 0; r0 < Bc; r0 += MC) forward(DC, H, 1, S.oc2, DC, r0, min(MC, Bc - r0), b, S.q2, 1, false);
     }
-    for (int jl = threadIdx.x; jl < Bc; jl += LT) {
-        const float qmin = fminf(S.q1[jl], S.q2[jl]);
-        S.y[jl] = S.r[jl] + (S.term[jl] != 0.0f ? 0.0f : hp.gamma * qmin);
+    if (!split) {
+        for (int jl = threadIdx.x; jl < Bc; jl += LT) {
+            const float qmin = fminf(S.q1[jl], S.q2[jl]);
+            S.y[jl] = S.r[jl] + (S.term[jl] != 0.0f ? 0.0f : hp.gamma * qmin);
+        }
     }
     __syncthreads();
     // a12: critic regression, forward + backward chunk by chunk
     float lsum = 0.0f;
-    for (int c = 0; c < 2; ++c) {
+    if (split) {
+        // one chunk: the pair's 2 Bc rows through critic cs; Q into dz3 (scratch of this CTA)
+        float* g = cs ? S.g2 : S.g1;
+        stage(cs ? R.c2 : R.c1, DC, H, 1, b);
+        if constexpr (HT == 128) bind_grads(b, g, DC, H, 1);
+        forward2(DC, H, 1, S.oc + d0, S.oc + d1, DC, Bc, 2 * Bc, b, S.dz3, S.dz3 + Bc, 1, false);
+        for (int r = threadIdx.x; r < 2 * Bc; r += LT) {
+            const ptrdiff_t o = (r < Bc ? d0 : d1) + (r < Bc ? r : r - Bc);
+            const float qmin = fminf(S.q1[o], S.q2[o]);
+            const float y = S.r[o] + (S.term[o] != 0.0f ? 0.0f : hp.gamma * qmin);
+            const float e = S.dz3[r] - y;
+            b.dZ3s[r * 4] = 2.0f * e / (float)B;
+            lsum += e * e / (float)B;
+        }
+        __syncthreads();
+        backward(DC, H, 1, 0, 2 * Bc, b, true, true, nullptr, 0, 0);
+        store_grads(g, DC, H, 1, b);
+    }
+    for (int c = 0; c < (split ? 0 : 2); ++c) {
         const float* W = c ? R.c2 : R.c1;
         float* q = c ? S.q2 : S.q1;
         stage(W, DC, H, 1, b);
@@ -1225,8 +1266,11 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
         const size_t g1off = (size_t)(S.g1 - scr_base), g2off = (size_t)(S.g2 - scr_base);
         const float* cl0 = scr_base - (size_t)rk * scr_stride;
         const int lo = (int)((int64_t)PC * rk / nS), hi = (int)((int64_t)PC * (rk + 1) / nS);
-        adam_slice(R.c1, cl0, scr_stride, nS, (int)g1off, R.m_c1, R.v_c1, lo, hi, t_c, hp, 1.0f);
-        adam_slice(R.c2, cl0, scr_stride, nS, (int)g2off, R.m_c2, R.v_c2, lo, hi, t_c, hp, 1.0f);
+        // split: critic 1's partials are in CTAs [0, half), critic 2's in [half, nS)
+        const int np = split ? half : nS;
+        adam_slice(R.c1, cl0, scr_stride, np, (int)g1off, R.m_c1, R.v_c1, lo, hi, t_c, hp, 1.0f);
+        adam_slice(R.c2, cl0 + (split ? (size_t)half * scr_stride : 0), scr_stride, np, (int)g2off,
+                   R.m_c2, R.v_c2, lo, hi, t_c, hp, 1.0f);
         if (rk == 0 && threadIdx.x == 0) {
             float l = 0.0f;
             for (int s2 = 0; s2 < nS; ++s2) l += ldcg(cl0 + (size_t)s2 * scr_stride + (S.loss - scr_base));
@@ -1643,6 +1687,21 @@ static qsim_status learner_run(ac_handle* a, qsim_handle* env, int64_t n_iters, 
 }
 
 // All runs in one persistent launch (clusters walk a longest-processing-time-first list).
+// Estimated time of one training iteration of a run (microseconds; a fit to the persistent
+// kernel's measured step times at one CTA per run and 8 envs, hidden 32-128, batch
+// 128-512): the env step plus updates_per_step x (a part fixed per update: Adam over the
+// parameters, barriers, weight staging; and a part per sample on a CTA: gather, the
+// networks' passes).  Only its ratios matter: it balances the longest-processing-time-first
+// assignment of runs to clusters, where a pure FLOP count left the small runs' fixed costs
+// out and piled them onto the same clusters.
+static double run_cost(const ac_handle* a, int nS) {
+    const double h = a->hidden, b = (double)a->batch / std::max(1, nS);
+    const double env = 16.0 + 0.34 * h;
+    const double per_sample = 1.042 + 3.98e-5 * (h * (a->obs_dim + a->critic_in) + 3.0 * h * h);
+    const double upd = 32.3 + 0.71 * h + 0.0109 * h * h + b * per_sample;
+    return env + std::max(1, (int)a->cfg.updates_per_step) * upd;
+}
+
 static qsim_status launch_train(std::vector<ac_handle*>& A, std::vector<qsim_handle*>& E,
                                 int64_t n_iters, int do_env, int nS, cudaStream_t st,
                                 int n_clusters_in) {
@@ -1660,10 +1719,7 @@ static qsim_status launch_train(std::vector<ac_handle*>& A, std::vector<qsim_han
     std::vector<int> order(n), off(n_clusters + 1, 0);
     {
         std::vector<double> cost(n);
-        for (int i = 0; i < n; ++i) {
-            const double h = A[i]->hidden;
-            cost[i] = (double)A[i]->batch * (h * (A[i]->obs_dim + A[i]->critic_in) + 3 * h * h) + 1.0;
-        }
+        for (int i = 0; i < n; ++i) cost[i] = run_cost(A[i], nS);
         std::vector<int> idx(n);
         std::iota(idx.begin(), idx.end(), 0);
         std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
@@ -2085,10 +2141,7 @@ extern "C" qsim_status ac_plan_create(ac_handle* const* runs, qsim_handle* const
     std::vector<int> order(n), off(p->n_clusters + 1, 0);
     {
         std::vector<double> cost(n);
-        for (int i = 0; i < n; ++i) {
-            const double h = p->A[i]->hidden;
-            cost[i] = (double)p->A[i]->batch * (h * (p->A[i]->obs_dim + p->A[i]->critic_in) + 3 * h * h) + 1.0;
-        }
+        for (int i = 0; i < n; ++i) cost[i] = run_cost(p->A[i], nS);
         std::vector<int> idx(n);
         std::iota(idx.begin(), idx.end(), 0);
         std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });

@@ -359,28 +359,36 @@ __device__ __forceinline__ void stage(const float* W, int in, int H, int out, co
     __syncthreads();
 }
 
-// Forward of rows [r0, r0 + mc) of X (global [rows][ldx]): hidden activations stay in
-// shared memory; the outputs go to Y (global [rows][ldy]).
-__device__ __forceinline__ void forward(int in, int H, int out, const float* X, int ldx, int r0,
-                                        int mc, const Buf& b, float* Y, int ldy, bool tanh_out) {
+// Loads rows [r0, r0 + n) of X (global [rows][ldx]) into rows [d0, d0 + n) of the input
+// chunk, zero-padded to a multiple of 4 columns (no barrier).
+__device__ __forceinline__ void load_rows(int in, const float* X, int ldx, int r0, int n, int d0,
+                                          const Buf& b) {
     const int K4 = k4(in);
+    float* Xd = b.Xs + d0 * INP;
     if (ldx == in) {
         // rows contiguous: one range, float4 body
-        load_scatter(X + (size_t)r0 * ldx, mc * in, [&](int i, float v) {
+        load_scatter(X + (size_t)r0 * ldx, n * in, [&](int i, float v) {
             const int r = i / in;
-            b.Xs[r * INP + (i - r * in)] = v;
+            Xd[r * INP + (i - r * in)] = v;
         });
-        for (int i = threadIdx.x; i < mc * (K4 - in); i += LT) {
+        for (int i = threadIdx.x; i < n * (K4 - in); i += LT) {
             const int r = i / (K4 - in);
-            b.Xs[r * INP + in + (i - r * (K4 - in))] = 0.0f;
+            Xd[r * INP + in + (i - r * (K4 - in))] = 0.0f;
         }
     } else {
-        batched_copy(mc * K4, X + (size_t)r0 * ldx, b.Xs, [&](int i) { return (i / K4) * ldx + i % K4; },
+        batched_copy(n * K4, X + (size_t)r0 * ldx, Xd, [&](int i) { return (i / K4) * ldx + i % K4; },
                      [&](int i) { return (i / K4) * INP + i % K4; }, [&](int i) { return i % K4 < in; });
     }
+}
+
+// The layers of the mc-row chunk held in Xs: hidden activations stay in shared memory;
+// emit(r, o, y) stores output o of chunk row r.
+template <class Emit>
+__device__ __forceinline__ void forward_core(int in, int H, int out, int mc, const Buf& b, bool tanh_out,
+                                             Emit emit) {
     __syncthreads();
     const int as = b.as;
-    gemm_nt(mc, H, K4, b.Xs, INP, b.W1s, LD1,
+    gemm_nt(mc, H, k4(in), b.Xs, INP, b.W1s, LD1,
             [&](int m, int n, float v) { b.H1s[m * as + n] = fmaxf(v + b.b1[n], 0.0f); });
     gemm_nt(mc, H, H, b.H1s, as, b.W2s, b.ld2,
             [&](int m, int n, float v) { b.H2s[m * as + n] = fmaxf(v + b.b2[n], 0.0f); });
@@ -390,9 +398,31 @@ __device__ __forceinline__ void forward(int in, int H, int out, const float* X, 
         float acc = 0.0f;
         for (int j = lane; j < H; j += 32) acc = fmaf(b.W3s[o * b.hp + j], b.H2s[r * as + j], acc);
         acc = warp_sum(acc) + b.b3[o];
-        if (lane == 0) Y[(size_t)(r0 + r) * ldy + o] = tanh_out ? tanhf(acc) : acc;
+        if (lane == 0) emit(r, o, tanh_out ? tanhf(acc) : acc);
     }
     __syncthreads();
+}
+
+// Forward of rows [r0, r0 + mc) of X (global [rows][ldx]); the outputs go to Y (global
+// [rows][ldy]).
+__device__ __forceinline__ void forward(int in, int H, int out, const float* X, int ldx, int r0,
+                                        int mc, const Buf& b, float* Y, int ldy, bool tanh_out) {
+    load_rows(in, X, ldx, r0, mc, 0, b);
+    forward_core(in, H, out, mc, b, tanh_out,
+                 [&](int r, int o, float y) { Y[(size_t)(r0 + r) * ldy + o] = y; });
+}
+
+// Forward of one chunk made of two row blocks: rows [0, n0) of X0 and [0, mc - n0) of X1
+// (both [rows][ldx]); outputs to Y0 and Y1 ([rows][ldy]) in the same split.
+__device__ __forceinline__ void forward2(int in, int H, int out, const float* X0, const float* X1, int ldx,
+                                         int n0, int mc, const Buf& b, float* Y0, float* Y1, int ldy,
+                                         bool tanh_out) {
+    load_rows(in, X0, ldx, 0, n0, 0, b);
+    load_rows(in, X1, ldx, 0, mc - n0, n0, b);
+    forward_core(in, H, out, mc, b, tanh_out, [&](int r, int o, float y) {
+        if (r < n0) Y0[(size_t)r * ldy + o] = y;
+        else Y1[(size_t)(r - n0) * ldy + o] = y;
+    });
 }
 
 // Reverse of the chunk just run by forward(); dZ3s [mc][4] holds dLoss/d(output

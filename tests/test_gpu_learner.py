@@ -88,13 +88,16 @@ def make_run(q, n_env=3, cap=64, hidden=32, batch=64, cluster=1, layout=0, steps
                                                          (2, 3, 64, 64), (16, 0, 64, 256),
                                                          (1, 0, 128, 512), (0, 1, 64, 256),
                                                          (1, 0, 64, 256), (1, 1, 64, 128),
-                                                         (1, 0, 32, 128), (2, 0, 64, 256)])
+                                                         (1, 0, 32, 128), (2, 0, 64, 256),
+                                                         (4, 2, 32, 64)])
 def test_ac_update_parity(gpu, cluster, layout, hidden, batch):
     """Cluster 16 at hidden 64 / batch 256 is the single run's automatic choice; hidden 128
     with batch 512 on one CTA is the largest shape of the batched workload; cluster 0 is
     the automatic choice with the privileged critic.  CTAs holding whole 128-sample tiles
     (1 x 128 .. 512, 2 x 128) run the target actor and target critics on the tensor cores,
-    at hidden 32, 64 and 128 and with the privileged critic."""
+    at hidden 32, 64 and 128 and with the privileged critic.  Even clusters whose CTA pairs
+    hold at most 64 rows (2 x 64, 4 x 128, 8 x 256, 16 x 256, 2 x 64 symmetric, 4 x 64
+    with the 28-D critic) split the twin critics over the cluster's two halves."""
     q = gpu
     d, h, a, hp = make_run(q, hidden=hidden, batch=batch, cluster=cluster, layout=layout)
     try:
