@@ -718,28 +718,39 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
                 }
             } else if (w >= 2) {
                 // history: o_a has a_{t-1..t-NH}, o_a' has a_t, a_{t-1..t-NH+1}; zeros before the
-                // episode start.  Warp w handles lags i = w-1, w+5, w+11.
-                for (int i = w - 1; i <= nh; i += 6) {
-                    const bool ok = (uint32_t)i <= ep && in_bounds(bst, ring(slot - i, CAP), rows, SITE_RING_READ);
-                    const bool ok2 = i == 1 || ((uint32_t)(i - 1) <= ep &&
-                                                in_bounds(bst, ring(slot - i + 1, CAP), rows, SITE_RING_READ));
+                // episode start.  Warp w handles lags i = w-1, w+5, w+11, all their loads issued
+                // before the first store.
+                static_assert(HMAX <= 18, "history lags: at most 3 per warp of 6");
+                float h[3][4], h2[3][4];
+#pragma unroll
+                for (int u3 = 0; u3 < 3; ++u3) {
+                    const int i = w - 1 + 6 * u3;
+                    const bool lag = i <= nh;
+                    const bool ok = lag && (uint32_t)i <= ep &&
+                                    in_bounds(bst, ring(slot - i, CAP), rows, SITE_RING_READ);
+                    const bool ok2 = lag && (i == 1 || ((uint32_t)(i - 1) <= ep &&
+                                                        in_bounds(bst, ring(slot - i + 1, CAP), rows, SITE_RING_READ)));
                     const float* ap = R.E.rec + (size_t)ring(slot - i, CAP) * F * ld + env + 17 * ld;
                     const float* ap2 = i == 1 ? rec + 17 * ld
                                               : R.E.rec + (size_t)ring(slot - i + 1, CAP) * F * ld + env + 17 * ld;
-                    float h[4], h2[4];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        h[c] = ok ? ldcg(ap + c * ld) : 0.0f;
-                        h2[c] = ok2 ? ldcg(ap2 + c * ld) : 0.0f;
+                        h[u3][c] = ok ? ldcg(ap + c * ld) : 0.0f;
+                        h2[u3][c] = ok2 ? ldcg(ap2 + c * ld) : 0.0f;
                     }
+                }
+#pragma unroll
+                for (int u3 = 0; u3 < 3; ++u3) {
+                    const int i = w - 1 + 6 * u3;
+                    if (i > nh) continue;
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const int q = 18 + 4 * (i - 1) + c;
-                        oa[q] = h[c];
-                        oa2[q] = h2[c];
+                        oa[q] = h[u3][c];
+                        oa2[q] = h2[u3][c];
                         if (C.critic_layout != 2) {
-                            oc[q] = h[c];
-                            oc2[q] = h2[c];
+                            oc[q] = h[u3][c];
+                            oc2[q] = h2[u3][c];
                         }
                     }
                 }
@@ -771,34 +782,41 @@ __device__ __forceinline__ void gather_all(const RunDesc& R, int j0, int Bc, uin
     for (int g0 = 0; g0 < Bc; g0 += 32) gather_group(R, j0, g0, min(32, Bc - g0), u, head, size, t_now, S, sm);
 }
 
+// Adam on parameters [lo, hi) from the sum of S gradient partials (partial s at
+// gpart_base + s * part_stride + goff, summed in the order s = 0..S-1); with tg != nullptr
+// the target copy also takes its Polyak step tg = tau th + (1 - tau) tg from the new th
+// (the fused form of polyak_slice, for steps that update the targets).
 __device__ void adam_slice(float* th, const float* gpart_base, size_t part_stride, int S,
                            int goff, float* m, float* v, int lo, int hi, int64_t t,
-                           const LearnHyper& hp, float gscale) {
+                           const LearnHyper& hp, float gscale, float* tg = nullptr) {
     const float bc1 = 1.0f - powf(hp.beta1, (float)t);
     const float bc2 = 1.0f - powf(hp.beta2, (float)t);
-    // U elements per thread per pass, all their loads issued before the arithmetic; each
-    // element's partial sum keeps the fixed order s = 0..S-1
-    constexpr int U = 4;
+    const float tau = hp.tau;
+    // U elements per thread per pass, all their loads issued before the arithmetic
+    constexpr int U = 8;
     for (int i0 = lo + threadIdx.x; i0 < hi; i0 += U * LT) {
-        float g[U], mo[U], vo[U], to[U];
+        float g[U], mo[U], vo[U], to[U], tt[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             const int i = i0 + k * LT;
-            g[k] = 0.0f; mo[k] = 0.0f; vo[k] = 0.0f; to[k] = 0.0f;
-            if (i < hi) { mo[k] = m[i]; vo[k] = v[i]; to[k] = th[i]; }
+            g[k] = 0.0f; mo[k] = 0.0f; vo[k] = 0.0f; to[k] = 0.0f; tt[k] = 0.0f;
+            if (i < hi) {
+                mo[k] = m[i]; vo[k] = v[i]; to[k] = th[i];
+                if (tg) tt[k] = tg[i];
+            }
         }
-        // partials in batches of 8 (8 x U loads in flight), summed in the order s = 0..S-1
-        for (int s0 = 0; s0 < S; s0 += 8) {
-            float x[8][U];
+        // partials in batches of 4 (4 x U loads in flight)
+        for (int s0 = 0; s0 < S; s0 += 4) {
+            float x[4][U];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 4; ++q) {
                 const float* gp = gpart_base + (size_t)(s0 + q) * part_stride + goff;
 #pragma unroll
                 for (int k = 0; k < U; ++k)
                     x[q][k] = s0 + q < S && i0 + k * LT < hi ? ldcg(gp + i0 + k * LT) : 0.0f;
             }
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
+            for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int k = 0; k < U; ++k)
                     if (s0 + q < S) g[k] += x[q][k];
@@ -812,7 +830,9 @@ __device__ void adam_slice(float* th, const float* gpart_base, size_t part_strid
             const float vi = fmaf(hp.beta2, vo[k], (1.0f - hp.beta2) * gk * gk);
             m[i] = mi;
             v[i] = vi;
-            th[i] = to[k] - hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + hp.eps);
+            const float ti = to[k] - hp.lr * (mi / bc1) / (sqrtf(vi / bc2) + hp.eps);
+            th[i] = ti;
+            if (tg) tg[i] = fmaf(tau, ti, (1.0f - tau) * tt[k]);
         }
     }
 }
@@ -1268,9 +1288,13 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
         const int lo = (int)((int64_t)PC * rk / nS), hi = (int)((int64_t)PC * (rk + 1) / nS);
         // split: critic 1's partials are in CTAs [0, half), critic 2's in [half, nS)
         const int np = split ? half : nS;
-        adam_slice(R.c1, cl0, scr_stride, np, (int)g1off, R.m_c1, R.v_c1, lo, hi, t_c, hp, 1.0f);
+        // on steps that update the actor, the critics' targets take their Polyak step here
+        // (the actor phase reads the critics, not their targets)
+        const bool pol = (int64_t)(u % (uint32_t)hp.policy_delay) == (int64_t)(hp.policy_delay - 1);
+        adam_slice(R.c1, cl0, scr_stride, np, (int)g1off, R.m_c1, R.v_c1, lo, hi, t_c, hp, 1.0f,
+                   pol ? R.c1_t : nullptr);
         adam_slice(R.c2, cl0 + (split ? (size_t)half * scr_stride : 0), scr_stride, np, (int)g2off,
-                   R.m_c2, R.v_c2, lo, hi, t_c, hp, 1.0f);
+                   R.m_c2, R.v_c2, lo, hi, t_c, hp, 1.0f, pol ? R.c2_t : nullptr);
         if (rk == 0 && threadIdx.x == 0) {
             float l = 0.0f;
             for (int s2 = 0; s2 < nS; ++s2) l += ldcg(cl0 + (size_t)s2 * scr_stride + (S.loss - scr_base));
@@ -1324,17 +1348,12 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
         const size_t gaoff = (size_t)(S.ga - scr_base);
         const float* cl0 = scr_base - (size_t)rk * scr_stride;
         const int lo = (int)((int64_t)PA * rk / nS), hi = (int)((int64_t)PA * (rk + 1) / nS);
-        adam_slice(R.actor, cl0, scr_stride, nS, (int)gaoff, R.m_a, R.v_a, lo, hi, t_a, hp, 1.0f);
+        adam_slice(R.actor, cl0, scr_stride, nS, (int)gaoff, R.m_a, R.v_a, lo, hi, t_a, hp, 1.0f, R.actor_t);
         if (rk == 0 && threadIdx.x == 0) {
             float l = 0.0f;
             for (int s2 = 0; s2 < nS; ++s2) l += ldcg(cl0 + (size_t)s2 * scr_stride + (S.loss - scr_base) + 1);
             R.stats[1] = l;
         }
-        __syncthreads();
-        polyak_slice(R.actor_t, R.actor, lo, hi, hp.tau);
-        const int clo = (int)((int64_t)PC * rk / nS), chi = (int)((int64_t)PC * (rk + 1) / nS);
-        polyak_slice(R.c1_t, R.c1, clo, chi, hp.tau);
-        polyak_slice(R.c2_t, R.c2, clo, chi, hp.tau);
     }
     cluster_sync_all(nS);
 }

@@ -225,38 +225,56 @@ __device__ __forceinline__ float warp_sum(float v) {
 // Weight-gradient accumulation G(m, n) (+)= sum_k A(m, k) B(k, n) with A stored [k][m]
 // (lda) and B [k][n] (ldb): dW = dZ^T X, reduced over the chunk's rows.  G (row stride ldg)
 // is overwritten when `first`, else added to; its previous values are read before the
-// reduction starts, 16 independent loads per tile whose latency the k loop hides (G may be
-// the L2-resident gradient output itself).
-__device__ __forceinline__ void gemm_km_acc(int M, int N, int K, const float* A, int lda,
-                                            const float* B, int ldb, float* G, int ldg, bool first) {
+// reduction starts, 4 x NC independent loads per tile whose latency the k loop hides (G
+// may be the L2-resident gradient output itself).  Lane (tm, tn) owns rows 4 tm .. 4 tm + 3
+// and columns NC tn .. NC tn + NC - 1 of a 64 x 16 NC block; NC = 6 covers the input widths
+// 65..96 in one block (B read as float2: 8-byte aligned, conflict-free).
+template <int NC>
+__device__ __forceinline__ void gemm_km_acc_t(int M, int N, int K, const float* A, int lda,
+                                              const float* B, int ldb, float* G, int ldg, bool first) {
     const int tm = threadIdx.x >> 4, tn = threadIdx.x & 15;
     for (int m0 = 0; m0 < M; m0 += 64)
-        for (int n0 = 0; n0 < N; n0 += 64) {
-            const int mb = m0 + tm * 4, nb = n0 + tn * 4;
+        for (int n0 = 0; n0 < N; n0 += 16 * NC) {
+            const int mb = m0 + tm * 4, nb = n0 + tn * NC;
             if (mb >= M || nb >= N) continue;
-            float acc[4][4];
+            float acc[4][NC];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < NC; ++j)
                     acc[i][j] = (!first && mb + i < M && nb + j < N) ? G[(mb + i) * ldg + nb + j] : 0.0f;
 #pragma unroll 4
             for (int k = 0; k < K; ++k) {
                 const float4 a = *reinterpret_cast<const float4*>(A + k * lda + mb);
-                const float4 b = *reinterpret_cast<const float4*>(B + k * ldb + nb);
-                const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+                float bv[NC];
+                if constexpr (NC == 4) {
+                    const float4 b = *reinterpret_cast<const float4*>(B + k * ldb + nb);
+                    bv[0] = b.x; bv[1] = b.y; bv[2] = b.z; bv[3] = b.w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NC; j += 2) {
+                        const float2 b = *reinterpret_cast<const float2*>(B + k * ldb + nb + j);
+                        bv[j] = b.x; bv[j + 1] = b.y;
+                    }
+                }
+                const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                    for (int j = 0; j < NC; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
+                for (int j = 0; j < NC; ++j)
                     if (mb + i < M && nb + j < N) G[(mb + i) * ldg + nb + j] = acc[i][j];
         }
     __syncthreads();
+}
+__device__ __forceinline__ void gemm_km_acc(int M, int N, int K, const float* A, int lda,
+                                            const float* B, int ldb, float* G, int ldg, bool first) {
+    if (N > 64 && N <= 96) gemm_km_acc_t<6>(M, N, K, A, lda, B, ldb, G, ldg, first);
+    else gemm_km_acc_t<4>(M, N, K, A, lda, B, ldb, G, ldg, first);
 }
 
 __device__ __forceinline__ int k4(int in) { return (in + 3) & ~3; }
