@@ -884,6 +884,109 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g, int fs, int 
     for (int i = threadIdx.x; i < a.PA; i += LT) out[i] = P[i];
 }
 
+// Actor-weight gradient of segment g over env chunk blockIdx.x from the lane-group kernels'
+// env-major records: the chunk's env x step rows are contiguous, NR floats each
+// [x (DA) | h1 | h2 | dz1 | dz2 | dz3 (4)].  The rows stream through shared memory in blocks
+// of WB (cp.async, double-buffered) and every thread keeps its outputs in registers over
+// the whole segment: dW1 = dz1^T x and dW2 = dz2^T h1 on an (H/4) x TN thread grid (4 rows
+// x J columns each, columns tn + TN j), dW3 = dz3^T h2 one element per thread, and the bias
+// sums; each element sums the rows in order (deterministic); the partial is written once.
+template <int H>
+__global__ void __launch_bounds__(LT) k_vjp_wgrad_rows(VjpArgs a, int g) {
+    constexpr int MT = H / 4, TN = LT / MT, J1 = (96 + TN - 1) / TN, J2 = H / TN, WB = 32;
+    static_assert(MT * TN == LT && J2 * TN == H, "thread grid");
+    extern __shared__ __align__(16) float sm[];
+    const int DA = a.DA, NR = DA + 4 * H + 4;
+    const int t0 = g * a.ckpt, t1 = min(a.H, t0 + a.ckpt);
+    const int e0 = blockIdx.x * a.chunk;
+    const int ne = min(a.chunk, a.n - e0);
+    if (ne <= 0) return;
+    const int nrow = ne * (t1 - t0), nblk = (nrow + WB - 1) / WB;
+    // 16-byte aligned: the records start aligned and a chunk or block offset is a multiple
+    // of 32 rows of NR floats (128 NR bytes)
+    const float* base = a.rec + (size_t)e0 * (t1 - t0) * NR;
+    const int tid = threadIdx.x, tm = tid / TN, tn = tid - tm * TN;
+    auto issue = [&](int blk) {
+        float* dst = sm + (size_t)(blk & 1) * WB * NR;
+        const int r0 = blk * WB, n = min(WB, nrow - r0) * NR, n4 = n >> 2;
+        const float* src = base + (size_t)r0 * NR;
+        const uint32_t sd = (uint32_t)__cvta_generic_to_shared(dst);
+        for (int v = tid; v < n4; v += LT)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(sd + 16u * (uint32_t)v),
+                         "l"(src + 4 * v) : "memory");
+        for (int i = 4 * n4 + tid; i < n; i += LT) dst[i] = ldcg(src + i);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    float acc1[4][J1], acc2[4][J2], acc3 = 0.0f, accb = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < J1; ++j) acc1[i][j] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < J2; ++j) acc2[i][j] = 0.0f;
+    }
+    // dW3 element (o3, j3) for tid < 4 H; bias element tid < 2 H + 4 (b1, b2, b3)
+    const int o3 = tid / H, j3 = tid - o3 * H;
+    const int boff = tid < H ? DA + 2 * H + tid : (tid < 2 * H ? DA + 3 * H + (tid - H) : DA + 4 * H + (tid - 2 * H));
+    issue(0);
+    for (int blk = 0; blk < nblk; ++blk) {
+        if (blk + 1 < nblk) {
+            issue(blk + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const float* Rb = sm + (size_t)(blk & 1) * WB * NR;
+        const int nr = min(WB, nrow - blk * WB);
+        for (int r = 0; r < nr; ++r) {
+            const float* R = Rb + r * NR;
+            const float* D1 = R + DA + 2 * H;
+            const float* D2 = D1 + H;
+            const float2 d1a = *reinterpret_cast<const float2*>(D1 + 4 * tm);
+            const float2 d1b = *reinterpret_cast<const float2*>(D1 + 4 * tm + 2);
+            const float2 d2a = *reinterpret_cast<const float2*>(D2 + 4 * tm);
+            const float2 d2b = *reinterpret_cast<const float2*>(D2 + 4 * tm + 2);
+            const float d1[4] = {d1a.x, d1a.y, d1b.x, d1b.y}, d2[4] = {d2a.x, d2a.y, d2b.x, d2b.y};
+            float xv[J1], hv[J2];
+#pragma unroll
+            for (int j = 0; j < J1; ++j) xv[j] = R[min(tn + TN * j, DA - 1)];
+#pragma unroll
+            for (int j = 0; j < J2; ++j) hv[j] = R[DA + tn + TN * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                for (int j = 0; j < J1; ++j) acc1[i][j] = fmaf(d1[i], xv[j], acc1[i][j]);
+#pragma unroll
+                for (int j = 0; j < J2; ++j) acc2[i][j] = fmaf(d2[i], hv[j], acc2[i][j]);
+            }
+            if (tid < 4 * H) acc3 = fmaf(R[DA + 4 * H + o3], R[DA + H + j3], acc3);
+            if (tid < 2 * H + 4) accb += R[boff];
+        }
+        __syncthreads();  // the buffer is refilled two blocks later
+    }
+    float* out = a.part + (size_t)blockIdx.x * a.PA;
+    float* oW1 = out;
+    float* ob1 = oW1 + H * DA;
+    float* oW2 = ob1 + H;
+    float* ob2 = oW2 + H * H;
+    float* oW3 = ob2 + H;
+    float* ob3 = oW3 + 4 * H;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = 4 * tm + i;
+#pragma unroll
+        for (int j = 0; j < J1; ++j)
+            if (tn + TN * j < DA) oW1[m * DA + tn + TN * j] = acc1[i][j];
+#pragma unroll
+        for (int j = 0; j < J2; ++j) oW2[m * H + tn + TN * j] = acc2[i][j];
+    }
+    if (tid < 4 * H) oW3[o3 * H + j3] = acc3;
+    if (tid < H) ob1[tid] = accb;
+    else if (tid < 2 * H) ob2[tid - H] = accb;
+    else if (tid < 2 * H + 4) ob3[tid - 2 * H] = accb;
+}
+
 // g_actor += sum over chunks (fixed order).
 __global__ void k_vjp_wreduce(VjpArgs a) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1036,6 +1139,17 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
     }
     const int NR = a.DA + 4 * a.hid + 4;
     const size_t smem_wg = sizeof(float) * (size_t)(GEMM_SMEM + a.PA);
+    // the lane-group path's row-streaming weight gradient: two blocks of 32 records
+    const size_t smem_wr = sizeof(float) * 2 * 32 * (size_t)NR;
+    if (d->mode == 1 && g_actor && warp_path) {
+        static bool wr_configured[2] = {false, false};
+        const int hi = a.hid == 64;
+        if (!wr_configured[hi]) {
+            QCHECK_CUDA(cudaFuncSetAttribute(hi ? k_vjp_wgrad_rows<64> : k_vjp_wgrad_rows<32>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 32 * (96 + 4 * 64 + 4) * 4));
+            wr_configured[hi] = true;
+        }
+    }
     if (d->mode == 1 && g_actor) {
         static size_t wg_configured = 0;
         if (smem_wg > 48 * 1024 && smem_wg > wg_configured) {
@@ -1051,7 +1165,12 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
         }
         QCHECK_LAUNCH("k_vjp_backward");
         if (d->mode == 1 && g_actor) {
-            k_vjp_wgrad<<<a.nchunk, LT, smem_wg, cs>>>(a, g, warp_path ? 1 : a.ld, warp_path ? NR : 1);
+            if (warp_path) {
+                if (a.hid == 64) k_vjp_wgrad_rows<64><<<a.nchunk, LT, smem_wr, cs>>>(a, g);
+                else k_vjp_wgrad_rows<32><<<a.nchunk, LT, smem_wr, cs>>>(a, g);
+            } else {
+                k_vjp_wgrad<<<a.nchunk, LT, smem_wg, cs>>>(a, g, a.ld, 1);
+            }
             QCHECK_LAUNCH("k_vjp_wgrad");
             k_vjp_wreduce<<<(a.PA + 255) / 256, 256, 0, cs>>>(a);
             QCHECK_LAUNCH("k_vjp_wreduce");
