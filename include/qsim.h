@@ -135,7 +135,7 @@ typedef struct qsim_info {
     float* ret_sum;           /* [ld] sum of completed episode returns */
     float* records;           /* [capacity][record_fields][ld]; flags are uint32 bits:
                                  bit0 terminated, bit1 truncated, bits 8.. episode step */
-    float* side;              /* [capacity][17][ld] s' where the episode ended */
+    float* side;              /* [capacity][ld][17] s' where the episode ended (env-major) */
     float* reward_c;          /* [8] device: current C_* (7) and exploration std-dev */
 } qsim_info;
 

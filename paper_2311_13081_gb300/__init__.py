@@ -327,7 +327,8 @@ def qsim_info_get(h) -> dict:
     out["reward_c"] = view(inf.reward_c, (8,))
     if cap > 0:
         out["records"] = view(inf.records, (cap, F, ld))
-        out["side"] = view(inf.side, (cap, 17, ld))
+        # env-major on the device; returned as a [capacity][17][ld] view like the records
+        out["side"] = view(inf.side, (cap, ld, 17)).permute(0, 2, 1)
     return out
 
 

@@ -252,17 +252,22 @@ __device__ __forceinline__ void obs_state(const float* s, float* o) {
 }
 
 // Observation noise of env `env` at global step t: 18 normals, two per Philox block.
+// Observation noise components 2b and 2b + 1 (b < 9) of env `env` at step t: one Philox
+// block, two Box-Muller normals scaled by their component's sigma.
+__device__ __forceinline__ void obs_noise_pair(const EnvCfg& C, uint32_t env, uint32_t t, int b, float& n0,
+                                               float& n1) {
+    const uint4 r = draw_rolled(C, env, t, TAG_OBS, (uint32_t)b);
+    const int k = 2 * b;
+    const float s0 = k < 3 ? C.sig[0] : (k < 12 ? C.sig[1] : (k < 15 ? C.sig[2] : C.sig[3]));
+    const float s1 = (k + 1) < 3 ? C.sig[0]
+                     : ((k + 1) < 12 ? C.sig[1] : ((k + 1) < 15 ? C.sig[2] : C.sig[3]));
+    n0 = s0 * gauss(r.x, r.y);
+    n1 = s1 * gauss(r.z, r.w);
+}
+
 __device__ __forceinline__ void obs_noise(const EnvCfg& C, uint32_t env, uint32_t t, float* nz) {
 #pragma unroll 1
-    for (int b = 0; b < 9; ++b) {
-        const uint4 r = draw_rolled(C, env, t, TAG_OBS, (uint32_t)b);
-        const int k = 2 * b;
-        const float s0 = k < 3 ? C.sig[0] : (k < 12 ? C.sig[1] : (k < 15 ? C.sig[2] : C.sig[3]));
-        const float s1 = (k + 1) < 3 ? C.sig[0]
-                         : ((k + 1) < 12 ? C.sig[1] : ((k + 1) < 15 ? C.sig[2] : C.sig[3]));
-        nz[k] = s0 * gauss(r.x, r.y);
-        nz[k + 1] = s1 * gauss(r.z, r.w);
-    }
+    for (int b = 0; b < 9; ++b) obs_noise_pair(C, env, t, b, nz[2 * b], nz[2 * b + 1]);
 }
 
 __device__ __forceinline__ float rpm_norm(const Vehicle& V, float w) {

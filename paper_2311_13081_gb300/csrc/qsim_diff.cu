@@ -25,7 +25,7 @@ namespace qsim {
 
 struct VjpArgs {
     Vehicle V;
-    int n, ld, H, ckpt, mode, nh, hid, DA, PA, nseg, nchunk, chunk;
+    int n, ld, H, ckpt, mode, nh, hid, DA, PA, nseg, nchunk, chunk, npart;  // npart: weight-gradient partials
     float w_p, w_q, w_v, w_a, dt;
     int renorm;
     const float *s0, *prm, *actions, *actor, *seed;
@@ -888,9 +888,11 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad(VjpArgs a, int g, int fs, int 
 // env-major records: the chunk's env x step rows are contiguous, NR floats each
 // [x (DA) | h1 | h2 | dz1 | dz2 | dz3 (4)].  The rows stream through shared memory in blocks
 // of WB (cp.async, double-buffered) and every thread keeps its outputs in registers over
-// the whole segment: dW1 = dz1^T x and dW2 = dz2^T h1 on an (H/4) x TN thread grid (4 rows
-// x J columns each, columns tn + TN j), dW3 = dz3^T h2 one element per thread, and the bias
-// sums; each element sums the rows in order (deterministic); the partial is written once.
+// its rows: dW1 = dz1^T x and dW2 = dz2^T h1 on an (H/4) x TN thread grid (4 rows x J
+// columns each, columns tn + TN j), dW3 = dz3^T h2 one element per thread, and the bias
+// sums; each element sums its rows in order (deterministic).  Two CTAs share a chunk (the
+// first and second half of its rows, split at a multiple of WB), each writing its own
+// partial: twice the CTAs of the chunk count, so that every SM has work.
 template <int H>
 __global__ void __launch_bounds__(LT) k_vjp_wgrad_rows(VjpArgs a, int g) {
     constexpr int MT = H / 4, TN = LT / MT, J1 = (96 + TN - 1) / TN, J2 = H / TN, WB = 32;
@@ -898,13 +900,16 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad_rows(VjpArgs a, int g) {
     extern __shared__ __align__(16) float sm[];
     const int DA = a.DA, NR = DA + 4 * H + 4;
     const int t0 = g * a.ckpt, t1 = min(a.H, t0 + a.ckpt);
-    const int e0 = blockIdx.x * a.chunk;
+    const int e0 = (blockIdx.x >> 1) * a.chunk, half = blockIdx.x & 1;
     const int ne = min(a.chunk, a.n - e0);
     if (ne <= 0) return;
-    const int nrow = ne * (t1 - t0), nblk = (nrow + WB - 1) / WB;
-    // 16-byte aligned: the records start aligned and a chunk or block offset is a multiple
-    // of 32 rows of NR floats (128 NR bytes)
-    const float* base = a.rec + (size_t)e0 * (t1 - t0) * NR;
+    const int nrow_all = ne * (t1 - t0);
+    const int split = ((nrow_all / 2 + WB - 1) / WB) * WB;
+    const int rbeg = half ? min(split, nrow_all) : 0, nrow = half ? nrow_all - rbeg : min(split, nrow_all);
+    const int nblk = (nrow + WB - 1) / WB;
+    // 16-byte aligned: the records start aligned and a chunk, half or block offset is a
+    // multiple of 32 rows of NR floats (128 NR bytes)
+    const float* base = a.rec + ((size_t)e0 * (t1 - t0) + rbeg) * NR;
     const int tid = threadIdx.x, tm = tid / TN, tn = tid - tm * TN;
     auto issue = [&](int blk) {
         float* dst = sm + (size_t)(blk & 1) * WB * NR;
@@ -928,7 +933,7 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad_rows(VjpArgs a, int g) {
     // dW3 element (o3, j3) for tid < 4 H; bias element tid < 2 H + 4 (b1, b2, b3)
     const int o3 = tid / H, j3 = tid - o3 * H;
     const int boff = tid < H ? DA + 2 * H + tid : (tid < 2 * H ? DA + 3 * H + (tid - H) : DA + 4 * H + (tid - 2 * H));
-    issue(0);
+    if (nblk > 0) issue(0);
     for (int blk = 0; blk < nblk; ++blk) {
         if (blk + 1 < nblk) {
             issue(blk + 1);
@@ -987,12 +992,12 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad_rows(VjpArgs a, int g) {
     else if (tid < 2 * H + 4) ob3[tid - 2 * H] = accb;
 }
 
-// g_actor += sum over chunks (fixed order).
+// g_actor += sum over the partials (fixed order).
 __global__ void k_vjp_wreduce(VjpArgs a) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.PA) return;
     float s = 0.0f;
-    for (int c = 0; c < a.nchunk; ++c) s += a.part[(size_t)c * a.PA + p];
+    for (int c = 0; c < a.npart; ++c) s += a.part[(size_t)c * a.PA + p];
     a.g_actor[p] += s;
 }
 
@@ -1016,7 +1021,7 @@ static WsLayout ws_layout(const qsim_vjp_desc& d, int DA, int PA, int nchunk) {
     const size_t NR = (size_t)DA + 4 * (size_t)d.hidden + 4;
     w.rec = take(d.mode == 1 ? (size_t)d.ckpt * NR * ld : 0);
     w.fo = take(d.mode == 1 ? ((size_t)DA + 2 * (size_t)d.hidden) * ld : 0);
-    w.part = take(d.mode == 1 ? (size_t)nchunk * PA : 0);
+    w.part = take(d.mode == 1 ? 2 * (size_t)nchunk * PA : 0);  // up to two partials per chunk
     w.total = off;
     return w;
 }
@@ -1090,6 +1095,7 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
     a.nseg = (d->H + d->ckpt - 1) / d->ckpt;
     a.chunk = kChunk;
     a.nchunk = (d->n + kChunk - 1) / kChunk;
+    a.npart = a.nchunk;
     a.w_p = d->w_p; a.w_q = d->w_q; a.w_v = d->w_v; a.w_a = d->w_a; a.dt = d->dt;
     a.renorm = d->renorm;
     a.s0 = s0; a.prm = params; a.actions = actions; a.actor = actor; a.seed = seed;
@@ -1166,8 +1172,9 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
         QCHECK_LAUNCH("k_vjp_backward");
         if (d->mode == 1 && g_actor) {
             if (warp_path) {
-                if (a.hid == 64) k_vjp_wgrad_rows<64><<<a.nchunk, LT, smem_wr, cs>>>(a, g);
-                else k_vjp_wgrad_rows<32><<<a.nchunk, LT, smem_wr, cs>>>(a, g);
+                a.npart = 2 * a.nchunk;  // two CTAs (row halves) per chunk
+                if (a.hid == 64) k_vjp_wgrad_rows<64><<<a.npart, LT, smem_wr, cs>>>(a, g);
+                else k_vjp_wgrad_rows<32><<<a.npart, LT, smem_wr, cs>>>(a, g);
             } else {
                 k_vjp_wgrad<<<a.nchunk, LT, smem_wg, cs>>>(a, g, a.ld, 1);
             }

@@ -263,9 +263,9 @@ __global__ void k_step(EnvCfg C, EnvPtrs p, const float* __restrict__ actions, u
             for (int k = 0; k < NPRIV; ++k) rec[(23 + k) * ld + e] = pv[k];
         }
         if (term || trunc) {
-            float* sd = p.side + (size_t)slot * NS * ld;
+            float* sd = p.side + ((size_t)slot * ld + e) * NS;
 #pragma unroll
-            for (int i = 0; i < NS; ++i) sd[i * ld + e] = s2[i];
+            for (int i = 0; i < NS; ++i) sd[i] = s2[i];
         }
     }
     // history: newest first

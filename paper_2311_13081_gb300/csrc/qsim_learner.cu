@@ -36,8 +36,8 @@ namespace qsim {
 
 constexpr int SMEM_ENGINE = smlp::floats() > smlp::floats2() ? smlp::floats() : smlp::floats2();
 constexpr int SMEM_MAIN = GEMM_SMEM > SMEM_ENGINE ? GEMM_SMEM : SMEM_ENGINE;
-// the small-run env step keeps an actor of hidden <= 64 and <= 128 inputs in shared memory
-static_assert(SMEM_MAIN >= 64 * 128 + 64 + 64 * 64 + 64 + 4 * 64 + 4 + 4 + 8 * (132 + 2 * 68 + 4 + 32),
+// the small-run env step keeps an actor of hidden <= 128 and <= 128 inputs in shared memory
+static_assert(SMEM_MAIN >= 128 * 128 + 128 + 128 * 128 + 128 + 4 * 128 + 4 + 4 + 8 * (132 + 2 * 132 + 4 + 32),
               "learner shared memory too small for the small-run env step");
 
 struct LearnHyper {
@@ -367,9 +367,9 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
                 for (int k = 0; k < NPRIV; ++k) rec[(23 + k) * ld] = pv[k];
             }
             if (term || trunc) {
-                float* sd = R.E.side + (size_t)slot * NS * ld + e;
+                float* sd = R.E.side + ((size_t)slot * ld + e) * NS;
 #pragma unroll
-                for (int i = 0; i < NS; ++i) sd[i * ld] = s2[i];
+                for (int i = 0; i < NS; ++i) sd[i] = s2[i];
             }
         }
         {
@@ -421,12 +421,11 @@ __device__ __noinline__ void env_step_cta(RunDesc& R, const Scr& S, uint32_t t, 
 // history and builds its observation in shared memory; the three layers then read
 // shared memory only; the env's data stay in registers from the observation to the
 // write-back, and the history shift reads the observation row already in shared memory.
-// Same arithmetic, in the same order per output, as env_step_cta's small-batch path.
 __device__ __noinline__ void env_step_small(RunDesc& R, uint32_t t, int64_t slot, float* sm) {
     const EnvCfg& C = R.C;
     const int ld = C.ld, n = R.n_env, DA = R.DA, H = R.H, PA = R.PA;
     const bool warm = (int64_t)t < (int64_t)C.learning_starts;
-    constexpr int LX = 132, LH = 68;
+    constexpr int LX = 132, LH = 132;
     float* Ws = sm;                                   // actor parameters, as stored
     float* xs = sm + ((PA + 3) & ~3);                 // [8][LX] observations
     float* h1 = xs + 8 * LX;                          // [8][LH]
@@ -583,9 +582,9 @@ __device__ __noinline__ void env_step_small(RunDesc& R, uint32_t t, int64_t slot
             for (int k = 0; k < NPRIV; ++k) rec[(23 + k) * ld] = pv[k];
         }
         if (term || trunc) {
-            float* sd = R.E.side + (size_t)slot * NS * ld + e;
+            float* sd = R.E.side + ((size_t)slot * ld + e) * NS;
 #pragma unroll
-            for (int i = 0; i < NS; ++i) sd[i * ld] = s2[i];
+            for (int i = 0; i < NS; ++i) sd[i] = s2[i];
         }
     }
     float ret = ret0 + r;
@@ -643,6 +642,8 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
     float* T_oc2 = T_oc + (size_t)G * DC;
     float* T_r = T_oc2 + (size_t)G * DC;
     float* T_term = T_r + G;
+    int* T_env = reinterpret_cast<int*>(T_term + G);  // sample's env (-1: skipped) and t_rec,
+    uint32_t* T_trec = reinterpret_cast<uint32_t*>(T_env + G);  // for the noise pass
     int* const bst = R.E.status;
     const int64_t rows = R.E.rows;
     if (jl < G) {
@@ -658,7 +659,12 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
         const int64_t slot = ring(head - size + lost + k, CAP);
         const uint32_t t_rec = (uint32_t)(t_now - size + lost + k);
         // (debug builds) a slot or env outside the ring skips the sample, status set
-        if (in_bounds(bst, slot, rows, SITE_RING_READ) && in_bounds(bst, env, ld, SITE_SOA)) {
+        const bool sample_ok = in_bounds(bst, slot, rows, SITE_RING_READ) && in_bounds(bst, env, ld, SITE_SOA);
+        if (w == 0) {
+            T_env[jl] = sample_ok ? env : -1;
+            T_trec[jl] = t_rec;
+        }
+        if (sample_ok) {
             const float* rec = R.E.rec + (size_t)slot * F * ld + env;
             const uint32_t fl = __float_as_uint(ldcg(rec + 22 * ld));
             const bool done = (fl & 3u) != 0;
@@ -670,12 +676,15 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
             const bool nxt_ok = w != 1 || done || in_bounds(bst, ring(slot + 1, CAP), rows, SITE_RING_READ);
             if (w < 2 && nxt_ok) {
                 // w == 0: s_t -> o_a, o_c (+ stored action, reward, flag); w == 1: s_{t+1} -> o_a', o_c'
+                // the side slot is env-major (an env's 17 values contiguous), the records field-major
+                const bool from_side = w == 1 && done;
                 const float* src = w == 0 ? rec
-                                          : (done ? R.E.side + (size_t)slot * NS * ld + env
-                                                  : R.E.rec + (size_t)ring(slot + 1, CAP) * F * ld + env);
+                                          : (from_side ? R.E.side + ((size_t)slot * ld + env) * NS
+                                                       : R.E.rec + (size_t)ring(slot + 1, CAP) * F * ld + env);
+                const size_t sst = from_side ? 1 : (size_t)ld;
                 float st[NS], a[4], pv[NPRIV];
 #pragma unroll
-                for (int i = 0; i < NS; ++i) st[i] = ldcg(src + i * ld);
+                for (int i = 0; i < NS; ++i) st[i] = ldcg(src + i * sst);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[i] = w == 0 ? ldcg(rec + (17 + i) * ld) : 0.0f;
 #pragma unroll
@@ -704,12 +713,7 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
                     T_r[jl] = r;
                     T_term[jl] = (fl & 1u) ? 1.0f : 0.0f;
                 }
-                if (C.any_noise) {
-                    float nz[18];
-                    obs_noise(C, (uint32_t)env, t_rec + (uint32_t)w, nz);
-#pragma unroll
-                    for (int q = 0; q < 18; ++q) o[q] += nz[q];
-                }
+                // the observation noise is added by all warps below
 #pragma unroll
                 for (int q = 0; q < 18; ++q) oax[q] = o[q];
                 if (C.critic_layout == 3) {
@@ -758,6 +762,27 @@ __device__ __noinline__ void gather_group(const RunDesc& R, int j0, int g0, int 
         }
     }
     __syncthreads();
+    if (C.any_noise) {
+        // the actor's observation noise of s_t (side 0, step t_rec) and s_{t+1} (side 1, step
+        // t_rec + 1): 9 Philox blocks per side, the 18 (side, block) pairs over the 8 warps
+        if (jl < G && T_env[jl] >= 0) {
+            const uint32_t env = (uint32_t)T_env[jl], t_rec = T_trec[jl];
+            for (int pr = w; pr < 18; pr += LT / 32) {
+                const int side = pr >= 9, blk = pr - 9 * side;
+                float n0, n1;
+                obs_noise_pair(C, env, t_rec + (uint32_t)side, blk, n0, n1);
+                float* oax = (side ? T_oa2 : T_oa) + (size_t)jl * DA;
+                oax[2 * blk] += n0;
+                oax[2 * blk + 1] += n1;
+                if (C.critic_layout == 3) {
+                    float* ocx = (side ? T_oc2 : T_oc) + (size_t)jl * DC;
+                    ocx[2 * blk] += n0;
+                    ocx[2 * blk + 1] += n1;
+                }
+            }
+        }
+        __syncthreads();
+    }
     // coalesced write-out of the six scratch ranges of this group
     const int n1 = G * DA, n2 = G * DC;
     for (int i = threadIdx.x; i < n1; i += LT) {
@@ -1408,7 +1433,7 @@ __global__ void __launch_bounds__(LT) k_train(RunDesc* runs, const int* order, c
             int n_upd = 1;
             if (do_env) {
                 if (rk == 0) {
-                    if (R.n_env <= 8 && R.H <= 64 && R.DA <= 128)
+                    if (R.n_env <= 8 && R.H <= 128 && R.DA <= 128)
                         env_step_small(R, (uint32_t)t_now, head, sm);
                     else
                         env_step_cta(R, S, (uint32_t)t_now, head, sm);

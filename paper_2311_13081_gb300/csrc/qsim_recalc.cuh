@@ -31,14 +31,23 @@ __device__ __forceinline__ void recalc_quad(const EnvCfg& C, const EnvPtrs& p, c
     for (int i = 0; i < NS; ++i) s2[i] = ld4s(src + i * ld, q);
     const bool d0 = (fl.x & 3u) != 0, d1 = (fl.y & 3u) != 0, d2 = (fl.z & 3u) != 0, d3 = (fl.w & 3u) != 0;
     if (d0 || d1 || d2 || d3) {
-        const float* sd = p.side + (size_t)slot * NS * ld;
+        // env-major side slot: the 17 values of an ended env are contiguous (68 B), read only
+        // for the envs whose episode ended
+        const float* sd = p.side + ((size_t)slot * ld + 4 * (size_t)q) * NS;
+        const bool dj[4] = {d0, d1, d2, d3};
 #pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            const float4 x = ld4s(sd + i * ld, q);
-            if (d0) s2[i].x = x.x;
-            if (d1) s2[i].y = x.y;
-            if (d2) s2[i].z = x.z;
-            if (d3) s2[i].w = x.w;
+        for (int j = 0; j < 4; ++j) {
+            if (!dj[j]) continue;
+            float x[NS];
+#pragma unroll
+            for (int i = 0; i < NS; ++i) x[i] = __ldcs(sd + j * NS + i);
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                if (j == 0) s2[i].x = x[i];
+                else if (j == 1) s2[i].y = x[i];
+                else if (j == 2) s2[i].z = x[i];
+                else s2[i].w = x[i];
+            }
         }
     }
     float r[4];

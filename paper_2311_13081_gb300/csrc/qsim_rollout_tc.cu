@@ -660,9 +660,9 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                             for (int k = 0; k < NPRIV; ++k) __stcs(rec + (23 + k) * ld, pv[k]);
                         }
                         if (term || trunc) {
-                            float* sd = p.side + (size_t)slot * NS * ld + g;
+                            float* sd = p.side + ((size_t)slot * ld + g) * NS;
 #pragma unroll
-                            for (int i = 0; i < NS; ++i) __stcs(sd + i * ld, s2[i]);
+                            for (int i = 0; i < NS; ++i) __stcs(sd + i, s2[i]);
                         }
                     }
                     slot = (slot + 1 == capacity) ? 0 : slot + 1;
