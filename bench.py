@@ -42,11 +42,12 @@ FLOP_DYN = 672        # RK4 (4 derivative evaluations + stage/accumulation arith
 FLOP_MISC = 60        # observation rotation matrix, reward, termination, action map
 BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, flags)
 # DRAM bytes per env-step of k_rollout<64,*> measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum, 32,768 envs x 100 steps; profiles/k_rollout_c2_65536x1000.md).
-# Set to None whenever the kernel changes until it is captured again.
-NCU_DRAM_BYTES_PER_ENV_STEP = (46.710016e6 + 289.403648e6) / (32768 * 100)
-# same for the tensor-core kernel k_rollout_tc (profiles/k_rollout_tc_c2_65536x1000.md)
-NCU_DRAM_BYTES_PER_ENV_STEP_TC = (35.447040e6 + 98.399488e6) / (65536 * 20)
+# dram__bytes_write.sum).  Set to None whenever the kernel changes until it is captured
+# again: its side-ring stores changed since the last capture.
+NCU_DRAM_BYTES_PER_ENV_STEP = None
+# same for the tensor-core kernel k_rollout_tc: one-pass capture of the bench's own timed
+# launch, 65,536 envs x 1,000 steps (profiles/k_rollout_tc_c2_65536x1000.md)
+NCU_DRAM_BYTES_PER_ENV_STEP_TC = (112.194304e6 + 6279.706112e6) / (65536 * 1000)
 
 
 def parse():

@@ -992,12 +992,24 @@ __global__ void __launch_bounds__(LT) k_vjp_wgrad_rows(VjpArgs a, int g) {
     else if (tid < 2 * H + 4) ob3[tid - 2 * H] = accb;
 }
 
-// g_actor += sum over the partials (fixed order).
-__global__ void k_vjp_wreduce(VjpArgs a) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.PA) return;
+// g_actor += sum over the partials (fixed order): a CTA takes 32 parameters; warp w sums
+// partials w, w + 8, ... (coalesced over the parameters), then the 8 warp sums are added
+// in order.
+__global__ void __launch_bounds__(256) k_vjp_wreduce(VjpArgs a) {
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int p = blockIdx.x * 32 + lane;
     float s = 0.0f;
-    for (int c = 0; c < a.npart; ++c) s += a.part[(size_t)c * a.PA + p];
+    if (p < a.PA) {
+#pragma unroll 4
+        for (int c = w; c < a.npart; c += 8) s += a.part[(size_t)c * a.PA + p];
+    }
+    red[w][lane] = s;
+    __syncthreads();
+    if (w != 0 || p >= a.PA) return;
+    s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += red[k][lane];
     a.g_actor[p] += s;
 }
 
@@ -1179,7 +1191,7 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
                 k_vjp_wgrad<<<a.nchunk, LT, smem_wg, cs>>>(a, g, a.ld, 1);
             }
             QCHECK_LAUNCH("k_vjp_wgrad");
-            k_vjp_wreduce<<<(a.PA + 255) / 256, 256, 0, cs>>>(a);
+            k_vjp_wreduce<<<(a.PA + 31) / 32, 256, 0, cs>>>(a);
             QCHECK_LAUNCH("k_vjp_wreduce");
         }
     }
