@@ -1330,8 +1330,14 @@ __device__ __noinline__ void td3_update_smem(RunDesc& R, int64_t head, int64_t s
     cluster_sync_all(nS);
     // a13: delayed actor update through the updated first critic
     if ((int64_t)(u % (uint32_t)hp.policy_delay) != (int64_t)(hp.policy_delay - 1)) return;
-    stage(R.actor, DA, H, 4, b);
-    for (int r0 = 0; r0 < Bc; r0 += MC) forward(DA, H, 4, S.oa, DA, r0, min(MC, Bc - r0), b, S.mu, 4, true);
+    // mu(o_a) alone (no activations kept): a pure forward pass, on the tensor cores when the
+    // CTA holds whole 128-row tiles
+    if (tcf_on) {
+        tc_forward(R.actor, DA, H, 4, S.oa, DA, Bc, S.mu, 4, true, sm, tmem, R.E.status);
+    } else {
+        stage(R.actor, DA, H, 4, b);
+        for (int r0 = 0; r0 < Bc; r0 += MC) forward(DA, H, 4, S.oa, DA, r0, min(MC, Bc - r0), b, S.mu, 4, true);
+    }
     for (int i = threadIdx.x; i < Bc * 4; i += LT) {
         const int jl = i >> 2, c = i & 3;
         S.oc[(size_t)jl * DC + DC - 4 + c] = S.mu[i];
@@ -1739,9 +1745,10 @@ static qsim_status learner_run(ac_handle* a, qsim_handle* env, int64_t n_iters, 
 // networks' passes).  Only its ratios matter: it balances the longest-processing-time-first
 // assignment of runs to clusters, where a pure FLOP count left the small runs' fixed costs
 // out and piled them onto the same clusters.
-static double run_cost(const ac_handle* a, int nS) {
+static double run_cost(const ac_handle* a, const qsim_handle* e, int nS) {
     const double h = a->hidden, b = (double)a->batch / std::max(1, nS);
-    const double env = 16.0 + 0.34 * h;
+    // the small-run env step (<= 8 envs, one env per lane group) or the CTA-wide one
+    const double env = e->n <= 8 && a->hidden <= 128 ? 13.0 + 0.1 * h : 16.0 + 0.34 * h;
     const double per_sample = 1.042 + 3.98e-5 * (h * (a->obs_dim + a->critic_in) + 3.0 * h * h);
     const double upd = 32.3 + 0.71 * h + 0.0109 * h * h + b * per_sample;
     return env + std::max(1, (int)a->cfg.updates_per_step) * upd;
@@ -1764,7 +1771,7 @@ static qsim_status launch_train(std::vector<ac_handle*>& A, std::vector<qsim_han
     std::vector<int> order(n), off(n_clusters + 1, 0);
     {
         std::vector<double> cost(n);
-        for (int i = 0; i < n; ++i) cost[i] = run_cost(A[i], nS);
+        for (int i = 0; i < n; ++i) cost[i] = run_cost(A[i], E[i], nS);
         std::vector<int> idx(n);
         std::iota(idx.begin(), idx.end(), 0);
         std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
@@ -2186,7 +2193,7 @@ extern "C" qsim_status ac_plan_create(ac_handle* const* runs, qsim_handle* const
     std::vector<int> order(n), off(p->n_clusters + 1, 0);
     {
         std::vector<double> cost(n);
-        for (int i = 0; i < n; ++i) cost[i] = run_cost(p->A[i], nS);
+        for (int i = 0; i < n; ++i) cost[i] = run_cost(p->A[i], p->E[i], nS);
         std::vector<int> idx(n);
         std::iota(idx.begin(), idx.end(), 0);
         std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
