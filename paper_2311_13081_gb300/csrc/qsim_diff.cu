@@ -444,21 +444,29 @@ __global__ void __launch_bounds__(VT) k_vjp_backward(VjpArgs a, int g) {
 // one contiguous row per env).
 constexpr int WV = 4;  // warps per CTA of the lane-group kernels
 
-// Weights in shared memory, one copy each with odd row strides so that both orientations
-// are conflict-free: W1 [H][DA+1], W2 [H][H+1] (lane-varying rows in the forward pass,
-// lane-varying columns in the reverse pass), W3 [4][H], biases.
+// Row stride (floats) for 16-byte loads of consecutive rows by the lanes of a group: a
+// multiple of 4 whose quarter is odd, so that 8 consecutive rows start in 8 distinct bank
+// quads (conflict-free).
+__host__ __device__ constexpr int vstride(int n) {
+    return (((n + 3) & ~3) >> 2) & 1 ? ((n + 3) & ~3) : ((n + 3) & ~3) + 4;
+}
+
+// Weights in shared memory, one copy each: W1 [H][l1] and W2 [H][l2] (row padding zero),
+// W3 [4][H], biases.  Forward products: a lane reads 4 consecutive inputs of one of its
+// rows with one 16-byte load (rows of the group's lanes in distinct bank quads); reverse
+// products: the group's lanes read consecutive columns of one row (conflict-free).
 struct WarpActor {
     const float *W1, *b1, *W2, *b2, *W3, *b3;
-    int l1, l2;  // row strides of W1 and W2
+    int l1, l2;  // row strides
 };
 
 __device__ __forceinline__ WarpActor stage_warp_actor(const float* actor, int DA, int H, float* sm) {
     WarpActor w;
-    const int l1 = DA + 1, l2 = H + 1;
+    const int l1 = vstride(DA), l2 = vstride(H);
     float* W1 = sm;
-    float* b1 = W1 + H * l1;
-    float* W2 = b1 + H;
-    float* b2 = W2 + H * l2;
+    float* W2 = W1 + H * l1;
+    float* b1 = W2 + H * l2;
+    float* b2 = b1 + H;
     float* W3 = b2 + H;
     float* b3 = W3 + 4 * H;
     const float* gW1 = actor;
@@ -467,23 +475,25 @@ __device__ __forceinline__ WarpActor stage_warp_actor(const float* actor, int DA
     const float* gb2 = gW2 + H * H;
     const float* gW3 = gb2 + H;
     const float* gb3 = gW3 + 4 * H;
-    for (int i = threadIdx.x; i < H * DA; i += blockDim.x) {
-        const int j = i / DA;
-        W1[j * l1 + (i - j * DA)] = gW1[i];
+    for (int i = threadIdx.x; i < H * l1; i += blockDim.x) {
+        const int j = i / l1, k = i - j * l1;
+        const float v = k < DA ? gW1[j * DA + k] : 0.0f;
+        W1[i] = v;
     }
-    for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
-        const int j = i / H;
-        W2[j * l2 + (i - j * H)] = gW2[i];
+    for (int i = threadIdx.x; i < H * l2; i += blockDim.x) {
+        const int j = i / l2, k = i - j * l2;
+        W2[i] = k < H ? gW2[j * H + k] : 0.0f;
     }
     for (int i = threadIdx.x; i < H; i += blockDim.x) { b1[i] = gb1[i]; b2[i] = gb2[i]; }
     for (int i = threadIdx.x; i < 4 * H; i += blockDim.x) W3[i] = gW3[i];
     if (threadIdx.x < 4) b3[threadIdx.x] = gb3[threadIdx.x];
-    w.W1 = W1; w.b1 = b1; w.W2 = W2; w.b2 = b2; w.W3 = W3; w.b3 = b3; w.l1 = l1; w.l2 = l2;
+    w.W1 = W1; w.b1 = b1; w.W2 = W2; w.b2 = b2; w.W3 = W3; w.b3 = b3;
+    w.l1 = l1; w.l2 = l2;
     return w;
 }
 
 __host__ __device__ inline int warp_actor_floats(int DA, int H) {
-    return H * (DA + 1) + H * (H + 1) + 2 * H + 4 * H + 4;
+    return H * vstride(DA) + H * vstride(H) + 2 * H + 4 * H + 4;
 }
 
 // Per-lane shape of the lane-group kernels.
@@ -544,25 +554,42 @@ __device__ __forceinline__ void grp_actor_fwd(const WarpActor& w, int DA, const 
     float acc[S::HPL];
 #pragma unroll
     for (int j = 0; j < S::HPL; ++j) acc[j] = w.b1[gl + LPE * j];
+    // inputs in fours: four broadcasts, then one 16-byte weight load and four FMAs (in input
+    // order) per hidden unit; past DA both the inputs and the padded weights are zero
 #pragma unroll
     for (int m = 0; m < S::NX; ++m) {
-        const int kend = min(LPE, DA - LPE * m);
-        for (int kk = 0; kk < kend; ++kk) {
-            const float xk = __shfl_sync(0xffffffffu, x[m], kk, LPE);
+        for (int kk = 0; kk < LPE && LPE * m + kk < DA; kk += 4) {
+            float xk[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xk[q] = __shfl_sync(0xffffffffu, x[m], kk + q, LPE);
             const float* wr = w.W1 + gl * w.l1 + LPE * m + kk;
 #pragma unroll
-            for (int j = 0; j < S::HPL; ++j) acc[j] = fmaf(wr[LPE * j * w.l1], xk, acc[j]);
+            for (int j = 0; j < S::HPL; ++j) {
+                const float4 wv = *reinterpret_cast<const float4*>(wr + LPE * j * w.l1);
+                acc[j] = fmaf(wv.x, xk[0], acc[j]);
+                acc[j] = fmaf(wv.y, xk[1], acc[j]);
+                acc[j] = fmaf(wv.z, xk[2], acc[j]);
+                acc[j] = fmaf(wv.w, xk[3], acc[j]);
+            }
         }
     }
 #pragma unroll
     for (int j = 0; j < S::HPL; ++j) { h1[j] = fmaxf(acc[j], 0.0f); acc[j] = w.b2[gl + LPE * j]; }
 #pragma unroll
     for (int m = 0; m < S::HPL; ++m)
-        for (int kk = 0; kk < LPE; ++kk) {
-            const float hk = __shfl_sync(0xffffffffu, h1[m], kk, LPE);
+        for (int kk = 0; kk < LPE; kk += 4) {
+            float hk[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) hk[q] = __shfl_sync(0xffffffffu, h1[m], kk + q, LPE);
             const float* wr = w.W2 + gl * w.l2 + LPE * m + kk;
 #pragma unroll
-            for (int j = 0; j < S::HPL; ++j) acc[j] = fmaf(wr[LPE * j * w.l2], hk, acc[j]);
+            for (int j = 0; j < S::HPL; ++j) {
+                const float4 wv = *reinterpret_cast<const float4*>(wr + LPE * j * w.l2);
+                acc[j] = fmaf(wv.x, hk[0], acc[j]);
+                acc[j] = fmaf(wv.y, hk[1], acc[j]);
+                acc[j] = fmaf(wv.z, hk[2], acc[j]);
+                acc[j] = fmaf(wv.w, hk[3], acc[j]);
+            }
         }
 #pragma unroll
     for (int j = 0; j < S::HPL; ++j) h2[j] = fmaxf(acc[j], 0.0f);
@@ -643,7 +670,7 @@ __global__ void __launch_bounds__(32 * WV) k_vjp_forward_w(VjpArgs a) {
 
 // Reverse sweep over segment g, one env per lane group.
 template <int H, int LPE>
-__global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g) {
+__global__ void __launch_bounds__(32 * WV, 2) k_vjp_backward_w(VjpArgs a, int g) {
     using S = Grp<H, LPE>;
     constexpr int HPL = S::HPL, NX = S::NX;
     extern __shared__ __align__(16) float sm[];
@@ -738,11 +765,16 @@ __global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g)
             for (int i = 0; i < HPL; ++i) acc[i] = 0.0f;
 #pragma unroll
             for (int m = 0; m < HPL; ++m)
-                for (int jj = 0; jj < LPE; ++jj) {
-                    const float dj = __shfl_sync(0xffffffffu, dz2[m], jj, LPE);
-                    const float* wr = w.W2 + (LPE * m + jj) * w.l2 + gl;
+                for (int jj = 0; jj < LPE; jj += 4) {
+                    float dj[4];
 #pragma unroll
-                    for (int i = 0; i < HPL; ++i) acc[i] = fmaf(wr[LPE * i], dj, acc[i]);
+                    for (int q = 0; q < 4; ++q) dj[q] = __shfl_sync(0xffffffffu, dz2[m], jj + q, LPE);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float* wr = w.W2 + (LPE * m + jj + q) * w.l2 + gl;
+#pragma unroll
+                        for (int i = 0; i < HPL; ++i) acc[i] = fmaf(wr[LPE * i], dj[q], acc[i]);
+                    }
                 }
 #pragma unroll
             for (int i = 0; i < HPL; ++i) dz1[i] = h1[i] > 0.0f ? acc[i] : 0.0f;
@@ -752,12 +784,17 @@ __global__ void __launch_bounds__(32 * WV, 3) k_vjp_backward_w(VjpArgs a, int g)
         for (int q = 0; q < NX; ++q) dx[q] = 0.0f;
 #pragma unroll
         for (int m = 0; m < HPL; ++m)
-            for (int jj = 0; jj < LPE; ++jj) {
-                const float dj = __shfl_sync(0xffffffffu, dz1[m], jj, LPE);
-                const float* wr = w.W1 + (LPE * m + jj) * w.l1 + gl;
+            for (int jj = 0; jj < LPE; jj += 4) {
+                float dj[4];
 #pragma unroll
-                for (int q = 0; q < NX; ++q)
-                    if (gl + LPE * q < DA) dx[q] = fmaf(wr[LPE * q], dj, dx[q]);
+                for (int q = 0; q < 4; ++q) dj[q] = __shfl_sync(0xffffffffu, dz1[m], jj + q, LPE);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float* wr = w.W1 + (LPE * m + jj + r) * w.l1 + gl;
+#pragma unroll
+                    for (int q = 0; q < NX; ++q)
+                        if (gl + LPE * q < DA) dx[q] = fmaf(wr[LPE * q], dj[r], dx[q]);
+                }
             }
         // observation part -> state adjoint (every lane), history part -> earlier actions
         float go[18];
