@@ -499,7 +499,13 @@ qsim_status ac_load(ac_handle* a, qsim_handle* env, const char* path);
  * the forward pass runs.
  * States are checkpointed every `ckpt` steps and recomputed inside each segment, so the
  * workspace (device, 16-byte aligned, qsim_vjp_workspace() bytes, caller-owned) grows with
- * H/ckpt + ckpt, not H.  s0 [17][ld], params [8][ld] (m Jx Jy Jz kf km T_m -). */
+ * H/ckpt + ckpt, not H.  s0 [17][ld], params [8][ld] (m Jx Jy Jz kf km T_m -).
+ * Asynchronous on `stream`.  In closed loop with g_actor, each segment's weight gradient
+ * runs on an internal low-priority stream of the calling host thread (created on its first
+ * such call on the device) while the next segment's reverse sweep runs; it forks from and
+ * joins back into `stream` through events, so the call completes in `stream` order and
+ * can be captured in a CUDA graph once that stream exists (make one uncaptured call first).
+ * Results are bitwise reproducible for a given descriptor. */
 typedef struct qsim_vjp_desc {
     int32_t n, ld, H, ckpt, mode, n_hist, hidden;
     int32_t lanes_per_env;  /* closed loop at hidden 32 / 64 with <= 96 actor inputs: lanes

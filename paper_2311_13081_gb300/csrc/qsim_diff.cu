@@ -442,7 +442,12 @@ __global__ void __launch_bounds__(VT) k_vjp_backward(VjpArgs a, int g) {
 // the history-input adjoints live in per-env rings of 16 x 4 floats in shared memory.
 // Activation records for the weight gradient are written env-major ([step][env][field]:
 // one contiguous row per env).
-constexpr int WV = 4;  // warps per CTA of the lane-group kernels
+// Warps per CTA of the lane-group kernels: 4 (two CTAs per SM), or 7 at 8 lanes per env
+// (one CTA per SM), whichever leaves the fewest warps on the busiest SM for the env count
+// (host: lane_group_warps).  At 4,096 envs 7 gives 147 CTAs of 7 warps, one wave, against
+// 256 CTAs of 4 that put 8 warps on most SMs.
+constexpr int kWvSmall = 4, kWvWide = 7;
+constexpr int SB = 2;  // steps per pass through the hidden layers in the reverse sweep's recompute
 
 // Row stride (floats) for 16-byte loads of consecutive rows by the lanes of a group: a
 // multiple of 4 whose quarter is odd, so that 8 consecutive rows start in 8 distinct bank
@@ -602,10 +607,83 @@ __device__ __forceinline__ void grp_actor_fwd(const WarpActor& w, int DA, const 
     }
 }
 
+// The actor's hidden layers h1, h2 (this lane's units) for SB steps of this group's env at
+// once, from their inputs x[b]: each 16-byte weight load serves SB steps.  Every unit sums
+// in the same order as grp_actor_fwd (bias, then the inputs in order), so h1 and h2 are
+// bitwise those of the forward pass.
+template <int H, int LPE, int SB>
+__device__ __forceinline__ void grp_actor_hidden_steps(const WarpActor& w, int DA,
+                                                       const float (&x)[SB][Grp<H, LPE>::NX],
+                                                       float (&h1)[SB][Grp<H, LPE>::HPL],
+                                                       float (&h2)[SB][Grp<H, LPE>::HPL]) {
+    using S = Grp<H, LPE>;
+    const int gl = threadIdx.x & (LPE - 1);
+    float acc[SB][S::HPL];
+#pragma unroll
+    for (int j = 0; j < S::HPL; ++j) {
+        const float b = w.b1[gl + LPE * j];
+#pragma unroll
+        for (int q = 0; q < SB; ++q) acc[q][j] = b;
+    }
+#pragma unroll
+    for (int m = 0; m < S::NX; ++m) {
+        for (int kk = 0; kk < LPE && LPE * m + kk < DA; kk += 4) {
+            float xk[SB][4];
+#pragma unroll
+            for (int q = 0; q < SB; ++q)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) xk[q][i] = __shfl_sync(0xffffffffu, x[q][m], kk + i, LPE);
+            const float* wr = w.W1 + gl * w.l1 + LPE * m + kk;
+#pragma unroll
+            for (int j = 0; j < S::HPL; ++j) {
+                const float4 wv = *reinterpret_cast<const float4*>(wr + LPE * j * w.l1);
+#pragma unroll
+                for (int q = 0; q < SB; ++q) {
+                    acc[q][j] = fmaf(wv.x, xk[q][0], acc[q][j]);
+                    acc[q][j] = fmaf(wv.y, xk[q][1], acc[q][j]);
+                    acc[q][j] = fmaf(wv.z, xk[q][2], acc[q][j]);
+                    acc[q][j] = fmaf(wv.w, xk[q][3], acc[q][j]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < S::HPL; ++j) {
+        const float b = w.b2[gl + LPE * j];
+#pragma unroll
+        for (int q = 0; q < SB; ++q) { h1[q][j] = fmaxf(acc[q][j], 0.0f); acc[q][j] = b; }
+    }
+#pragma unroll
+    for (int m = 0; m < S::HPL; ++m)
+        for (int kk = 0; kk < LPE; kk += 4) {
+            float hk[SB][4];
+#pragma unroll
+            for (int q = 0; q < SB; ++q)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) hk[q][i] = __shfl_sync(0xffffffffu, h1[q][m], kk + i, LPE);
+            const float* wr = w.W2 + gl * w.l2 + LPE * m + kk;
+#pragma unroll
+            for (int j = 0; j < S::HPL; ++j) {
+                const float4 wv = *reinterpret_cast<const float4*>(wr + LPE * j * w.l2);
+#pragma unroll
+                for (int q = 0; q < SB; ++q) {
+                    acc[q][j] = fmaf(wv.x, hk[q][0], acc[q][j]);
+                    acc[q][j] = fmaf(wv.y, hk[q][1], acc[q][j]);
+                    acc[q][j] = fmaf(wv.z, hk[q][2], acc[q][j]);
+                    acc[q][j] = fmaf(wv.w, hk[q][3], acc[q][j]);
+                }
+            }
+        }
+#pragma unroll
+    for (int j = 0; j < S::HPL; ++j)
+#pragma unroll
+        for (int q = 0; q < SB; ++q) h2[q][j] = fmaxf(acc[q][j], 0.0f);
+}
+
 // Env handled by this lane's group, whether it exists, and whether any group of the warp
 // has an env (warp-uniform).  A group past the last env runs on a valid index (the last
 // env) so that the warp's shuffles stay complete, and stores nothing.
-template <int LPE>
+template <int LPE, int WV>
 __device__ __forceinline__ void grp_env(int n, int& e, bool& live, bool& warp_live) {
     constexpr int G = 32 / LPE;
     const int warp = threadIdx.x >> 5, sub = (threadIdx.x & 31) / LPE;
@@ -616,7 +694,7 @@ __device__ __forceinline__ void grp_env(int n, int& e, bool& live, bool& warp_li
     if (!live) e = n - 1;
 }
 
-template <int H, int LPE>
+template <int H, int LPE, int WV>
 __global__ void __launch_bounds__(32 * WV) k_vjp_forward_w(VjpArgs a) {
     using S = Grp<H, LPE>;
     extern __shared__ __align__(16) float sm[];
@@ -627,7 +705,7 @@ __global__ void __launch_bounds__(32 * WV) k_vjp_forward_w(VjpArgs a) {
     __syncthreads();
     int e;
     bool live, warp_live;
-    grp_env<LPE>(a.n, e, live, warp_live);
+    grp_env<LPE, WV>(a.n, e, live, warp_live);
     if (!warp_live) return;  // warp-uniform
     float s[NS];
 #pragma unroll
@@ -669,8 +747,8 @@ __global__ void __launch_bounds__(32 * WV) k_vjp_forward_w(VjpArgs a) {
 }
 
 // Reverse sweep over segment g, one env per lane group.
-template <int H, int LPE>
-__global__ void __launch_bounds__(32 * WV, 2) k_vjp_backward_w(VjpArgs a, int g) {
+template <int H, int LPE, int WV>
+__global__ void __launch_bounds__(32 * WV, WV == kWvSmall ? 2 : 1) k_vjp_backward_w(VjpArgs a, int g) {
     using S = Grp<H, LPE>;
     constexpr int HPL = S::HPL, NX = S::NX;
     extern __shared__ __align__(16) float sm[];
@@ -680,7 +758,7 @@ __global__ void __launch_bounds__(32 * WV, 2) k_vjp_backward_w(VjpArgs a, int g)
     const int gl = threadIdx.x & (LPE - 1);
     int e;
     bool live, warp_live;
-    grp_env<LPE>(a.n, e, live, warp_live);
+    grp_env<LPE, WV>(a.n, e, live, warp_live);
     const int t0 = g * a.ckpt, t1 = min(a.H, t0 + a.ckpt);
     const bool last = (t1 == a.H);
     // history adjoints carried over from the later segments (zero for the last one)
@@ -692,21 +770,56 @@ __global__ void __launch_bounds__(32 * WV, 2) k_vjp_backward_w(VjpArgs a, int g)
     load_vehicle_prm(a, e, P);
     const float d0[6] = {0, 0, 0, 0, 0, 0};
     const float half = 0.5f * (a.V.rpm_max - a.V.rpm_min);
+    const size_t NR = (size_t)DA + 4 * H + 4;
+    // Recompute the segment from its checkpoint: the states (RK4 with the rollout's stored
+    // actions), and the actor's inputs and hidden activations at every step, which go
+    // into the step's activation record (x | h1 | h2) for the reverse sweep and the weight
+    // gradient.  Steps go SB at a time through the hidden layers, so that each weight read
+    // from shared memory serves SB steps.
     float s[NS];
 #pragma unroll
     for (int i = 0; i < NS; ++i) s[i] = a.ck[(size_t)g * NS * ld + (size_t)i * ld + e];
-    for (int t = t0; t < t1; ++t) {
-        float* ss = a.segs + (size_t)(t - t0) * NS * ld + e;
+    auto histA = [&](int tau, int c) { return a.A[((size_t)tau * 4 + c) * ld + e]; };
+    for (int tb = t0; tb < t1; tb += SB) {
+        float xb[SB][NX];
 #pragma unroll
-        for (int r = 0; r < (NS + LPE - 1) / LPE; ++r) {
-            const int i = gl + LPE * r;
-            const float v = pick<NS>(s, i);
-            if (live && i < NS) ss[(size_t)i * ld] = v;
+        for (int q = 0; q < SB; ++q) {
+            const int t = tb + q;
+            if (t < t1) {
+                float* ss = a.segs + (size_t)(t - t0) * NS * ld + e;
+#pragma unroll
+                for (int r = 0; r < (NS + LPE - 1) / LPE; ++r) {
+                    const int i = gl + LPE * r;
+                    const float v = pick<NS>(s, i);
+                    if (live && i < NS) ss[(size_t)i * ld] = v;
+                }
+                grp_actor_input<LPE, NX>(s, t, DA, nh, histA, xb[q]);
+                float u[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) u[c] = fmaf(a.A[((size_t)t * 4 + c) * ld + e] + 1.0f, half, a.V.rpm_min);
+                rk4(a.V, a.dt, a.renorm, s, u, P, d0);
+            } else {
+#pragma unroll
+                for (int m = 0; m < NX; ++m) xb[q][m] = 0.0f;
+            }
         }
-        float u[4];
+        float h1b[SB][HPL], h2b[SB][HPL];
+        grp_actor_hidden_steps<H, LPE, SB>(w, DA, xb, h1b, h2b);
+        if (live) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) u[c] = fmaf(a.A[((size_t)t * 4 + c) * ld + e] + 1.0f, half, a.V.rpm_min);
-        rk4(a.V, a.dt, a.renorm, s, u, P, d0);
+            for (int q = 0; q < SB; ++q) {
+                if (tb + q >= t1) break;
+                float* R = a.rec + ((size_t)e * (t1 - t0) + (tb + q - t0)) * NR;
+#pragma unroll
+                for (int m = 0; m < NX; ++m)
+                    if (gl + LPE * m < DA) R[gl + LPE * m] = xb[q][m];
+#pragma unroll
+                for (int j = 0; j < HPL; ++j) {
+                    R[DA + gl + LPE * j] = h1b[q][j];
+                    R[DA + H + gl + LPE * j] = h2b[q][j];
+                }
+            }
+        }
     }
     __syncwarp();
     float lam[NS], gp[7];
@@ -724,7 +837,6 @@ __global__ void __launch_bounds__(32 * WV, 2) k_vjp_backward_w(VjpArgs a, int g)
 #pragma unroll
         for (int i = 0; i < 7; ++i) gp[i] = a.gp[i * ld + e];
     }
-    const size_t NR = (size_t)DA + 4 * H + 4;
     for (int t = t1 - 1; t >= t0; --t) {
         float st[NS];
         const float* ss = a.segs + (size_t)(t - t0) * NS * ld + e;
@@ -743,14 +855,20 @@ __global__ void __launch_bounds__(32 * WV, 2) k_vjp_backward_w(VjpArgs a, int g)
         for (int c = 0; c < 4; ++c) ga[c] = gu[c] * half + seed * 2.0f * a.w_a * act[c] + adj[(t & 15) * 4 + c];
         __syncwarp();
         if (gl < 4) adj[(t & 15) * 4 + gl] = 0.0f;  // slot now belongs to step t - 16
-        // actor forward at step t (its inputs: the state and the previous actions)
-        float x[NX], h1[HPL], h2[HPL], mu[4];
-        grp_actor_input<LPE, NX>(st, t, DA, nh, [&](int tau, int c) { return a.A[((size_t)tau * 4 + c) * ld + e]; }, x);
-        grp_actor_fwd<H, LPE>(w, DA, x, h1, h2, mu);
+        // the actor at step t: its hidden activations from the step's record (written by
+        // this lane in the recompute above; a group without an env reads env n - 1's), its
+        // output mu = the stored action (the closed loop adds no noise)
+        float* R = a.rec + ((size_t)e * (t1 - t0) + (t - t0)) * NR;
+        float h1[HPL], h2[HPL];
+#pragma unroll
+        for (int j = 0; j < HPL; ++j) {
+            h1[j] = R[DA + gl + LPE * j];
+            h2[j] = R[DA + H + gl + LPE * j];
+        }
         // reverse: output layer, layer 2, layer 1, inputs
         float dz3[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) dz3[c] = ga[c] * (1.0f - mu[c] * mu[c]);
+        for (int c = 0; c < 4; ++c) dz3[c] = ga[c] * (1.0f - act[c] * act[c]);
         float dz2[HPL], dz1[HPL];
 #pragma unroll
         for (int j = 0; j < HPL; ++j) {
@@ -809,17 +927,12 @@ __global__ void __launch_bounds__(32 * WV, 2) k_vjp_backward_w(VjpArgs a, int g)
                 if (t - i >= 0) adj[((t - i) & 15) * 4 + c] += dx[q];
             }
         }
-        // activation record of (step t, env e): x | h1 | h2 | dZ1 | dZ2 | dZ3, env-major over
-        // the segment ([env][step][field]): a chunk of envs is one contiguous run of rows
+        // the rest of the activation record of (step t, env e): x | h1 | h2 | dZ1 | dZ2 | dZ3,
+        // env-major over the segment ([env][step][field]): a chunk of envs is one contiguous
+        // run of rows
         if (live) {
-            float* R = a.rec + ((size_t)e * (t1 - t0) + (t - t0)) * NR;
-#pragma unroll
-            for (int q = 0; q < NX; ++q)
-                if (gl + LPE * q < DA) R[gl + LPE * q] = x[q];
 #pragma unroll
             for (int j = 0; j < HPL; ++j) {
-                R[DA + gl + LPE * j] = h1[j];
-                R[DA + H + gl + LPE * j] = h2[j];
                 R[DA + 2 * H + gl + LPE * j] = dz1[j];
                 R[DA + 3 * H + gl + LPE * j] = dz2[j];
             }
@@ -1068,31 +1181,90 @@ static WsLayout ws_layout(const qsim_vjp_desc& d, int DA, int PA, int nchunk) {
     w.lam = take(NS * ld);
     w.gp = take(8 * ld);
     const size_t NR = (size_t)DA + 4 * (size_t)d.hidden + 4;
-    w.rec = take(d.mode == 1 ? (size_t)d.ckpt * NR * ld : 0);
+    // closed loop: the records of two segments (the weight gradient of one segment runs
+    // while the next segment's reverse sweep writes the other half)
+    w.rec = take(d.mode == 1 ? 2 * (size_t)d.ckpt * NR * ld : 0);
     w.fo = take(d.mode == 1 ? ((size_t)DA + 2 * (size_t)d.hidden) * ld : 0);
     w.part = take(d.mode == 1 ? 2 * (size_t)nchunk * PA : 0);  // up to two partials per chunk
     w.total = off;
     return w;
 }
 
+// The calling host thread's side stream on one device (lowest priority, so that the block
+// scheduler prefers the reverse sweep's blocks) and its fork / join events, created on the
+// first closed-loop gradient call and kept for the thread's life.  The weight gradient of
+// segment g runs there while segment g - 1's reverse sweep runs on the caller's stream.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork[2] = {nullptr, nullptr}, join[2] = {nullptr, nullptr};
+};
+
+static SideStream* side_stream() {
+    constexpr int kMaxDev = 16;
+    thread_local SideStream side[kMaxDev];
+    thread_local bool tried[kMaxDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    SideStream& x = side[dev];
+    if (!tried[dev]) {
+        tried[dev] = true;
+        int least = 0, greatest = 0;
+        bool ok = cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+                  cudaStreamCreateWithPriority(&x.s, cudaStreamNonBlocking, least) == cudaSuccess;
+        for (int i = 0; ok && i < 2; ++i)
+            ok = cudaEventCreateWithFlags(&x.fork[i], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&x.join[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            x.s = nullptr;  // the weight gradient then runs on the caller's stream
+        }
+    }
+    return x.s ? &x : nullptr;
+}
+
 static constexpr int kChunk = 32;  // envs per weight-gradient CTA
 static constexpr int kAutoLanesPerEnv = 8;  // lane-group width of the closed loop by default
 
-// The lane-group kernels of one (hidden, lanes per env) shape.
+// The lane-group kernels of one (hidden, lanes per env, warps per CTA) shape.
 struct GrpKernels {
     void (*fw)(VjpArgs);
     void (*bw)(VjpArgs, int);
+    int wv;
 };
 
-static GrpKernels grp_kernels(int hidden64, int lanes_index) {
-    static const GrpKernels tab[2][3] = {
-        {{k_vjp_forward_w<32, 32>, k_vjp_backward_w<32, 32>},
-         {k_vjp_forward_w<32, 16>, k_vjp_backward_w<32, 16>},
-         {k_vjp_forward_w<32, 8>, k_vjp_backward_w<32, 8>}},
-        {{k_vjp_forward_w<64, 32>, k_vjp_backward_w<64, 32>},
-         {k_vjp_forward_w<64, 16>, k_vjp_backward_w<64, 16>},
-         {k_vjp_forward_w<64, 8>, k_vjp_backward_w<64, 8>}}};
-    return tab[hidden64][lanes_index];
+static GrpKernels grp_kernels(int hidden64, int lanes_index, bool wide) {
+    static const GrpKernels tab[2][4] = {
+        {{k_vjp_forward_w<32, 32, kWvSmall>, k_vjp_backward_w<32, 32, kWvSmall>, kWvSmall},
+         {k_vjp_forward_w<32, 16, kWvSmall>, k_vjp_backward_w<32, 16, kWvSmall>, kWvSmall},
+         {k_vjp_forward_w<32, 8, kWvSmall>, k_vjp_backward_w<32, 8, kWvSmall>, kWvSmall},
+         {k_vjp_forward_w<32, 8, kWvWide>, k_vjp_backward_w<32, 8, kWvWide>, kWvWide}},
+        {{k_vjp_forward_w<64, 32, kWvSmall>, k_vjp_backward_w<64, 32, kWvSmall>, kWvSmall},
+         {k_vjp_forward_w<64, 16, kWvSmall>, k_vjp_backward_w<64, 16, kWvSmall>, kWvSmall},
+         {k_vjp_forward_w<64, 8, kWvSmall>, k_vjp_backward_w<64, 8, kWvSmall>, kWvSmall},
+         {k_vjp_forward_w<64, 8, kWvWide>, k_vjp_backward_w<64, 8, kWvWide>, kWvWide}}};
+    return tab[hidden64][lanes_index == 2 && wide ? 3 : lanes_index];
+}
+
+// Whether the 7-warp CTAs leave fewer warps on the busiest SM than the 4-warp ones (two
+// resident per SM) for n envs at lpe lanes per env: warps per SM ~ ceil(CTAs / SMs) x warps
+// per CTA.
+static bool lane_group_wide(int n, int lpe) {
+    if (lpe != 8) return false;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            sms = v;
+        else
+            sms = 152;
+    }
+    const long warps = (n + 3) / 4;  // 4 envs per warp at 8 lanes per env
+    auto busiest = [&](long wv) { return ((warps + wv - 1) / wv + sms - 1) / sms * wv; };
+    return busiest(kWvWide) < busiest(kWvSmall);
 }
 
 }  // namespace qsim
@@ -1167,6 +1339,8 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
     // closed loop at hidden 32 / 64: one env per group of lpe lanes
     const bool warp_path = d->mode == 1 && (a.hid == 32 || a.hid == 64) && a.DA <= 96;
     const int lpe = d->lanes_per_env == 0 ? kAutoLanesPerEnv : d->lanes_per_env;
+    const bool wide = warp_path && lane_group_wide(d->n, lpe);
+    const int WV = wide ? kWvWide : kWvSmall;
     const int envs_per_cta = WV * (32 / lpe);
     const int gridw = (d->n + envs_per_cta - 1) / envs_per_cta;
     const size_t smem_fw = sizeof(float) * (size_t)(warp_actor_floats(a.DA, a.hid) + 64 * envs_per_cta);
@@ -1174,12 +1348,13 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
     GrpKernels gk{};
     if (warp_path) {
         const int hi = a.hid == 64, li = lpe == 32 ? 0 : (lpe == 16 ? 1 : 2);
-        gk = grp_kernels(hi, li);
-        static bool configured[2][3] = {};
-        if (!configured[hi][li]) {
+        gk = grp_kernels(hi, li, wide);
+        static bool configured[2][4] = {};
+        const int ci = li == 2 && wide ? 3 : li;
+        if (!configured[hi][ci]) {
             QCHECK_CUDA(cudaFuncSetAttribute(gk.fw, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
             QCHECK_CUDA(cudaFuncSetAttribute(gk.bw, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
-            configured[hi][li] = true;
+            configured[hi][ci] = true;
         }
         gk.fw<<<gridw, 32 * WV, smem_fw, cs>>>(a);
     } else {
@@ -1212,24 +1387,59 @@ extern "C" qsim_status qsim_rollout_vjp(const qsim_vjp_desc* d, const qsim_param
             wg_configured = smem_wg;
         }
     }
-    for (int g = a.nseg - 1; g >= 0; --g) {
+    // Lane-group closed loop: segment g's records go to half (g & 1) of the record area,
+    // and its weight gradient (+ the fixed-order reduction into g_actor) runs on the side
+    // stream while segment g - 1's reverse sweep runs: it is submitted after that sweep,
+    // so the sweep's blocks are queued first.  Segment g - 2 reuses the half once the
+    // weight gradient is done; the last one (segment 0) runs on `stream` after the side
+    // stream's, which joins the side stream back (also under stream capture).
+    SideStream* side = (d->mode == 1 && g_actor && warp_path && a.nseg > 1) ? side_stream() : nullptr;
+    const size_t rec_seg = (size_t)a.ckpt * NR * a.ld;
+    auto weight_grad = [&](int g, cudaStream_t ws) -> qsim_status {
+        VjpArgs ag = a;
+        if (side) ag.rec = a.rec + (size_t)(g & 1) * rec_seg;
         if (warp_path) {
-            gk.bw<<<gridw, 32 * WV, smem_bw, cs>>>(a, g);
+            ag.npart = 2 * a.nchunk;  // two CTAs (row halves) per chunk
+            if (a.hid == 64) k_vjp_wgrad_rows<64><<<ag.npart, LT, smem_wr, ws>>>(ag, g);
+            else k_vjp_wgrad_rows<32><<<ag.npart, LT, smem_wr, ws>>>(ag, g);
         } else {
-            k_vjp_backward<<<grid, VT, smem, cs>>>(a, g);
+            k_vjp_wgrad<<<a.nchunk, LT, smem_wg, ws>>>(ag, g, a.ld, 1);
+        }
+        QCHECK_LAUNCH("k_vjp_wgrad");
+        k_vjp_wreduce<<<(a.PA + 31) / 32, 256, 0, ws>>>(ag);
+        QCHECK_LAUNCH("k_vjp_wreduce");
+        return QSIM_OK;
+    };
+    for (int g = a.nseg - 1; g >= 0; --g) {
+        VjpArgs ag = a;
+        if (side) {
+            ag.rec = a.rec + (size_t)(g & 1) * rec_seg;
+            if (g <= a.nseg - 3) QCHECK_CUDA(cudaStreamWaitEvent(cs, side->join[g & 1], 0));
+        }
+        if (warp_path) {
+            gk.bw<<<gridw, 32 * WV, smem_bw, cs>>>(ag, g);
+        } else {
+            k_vjp_backward<<<grid, VT, smem, cs>>>(ag, g);
         }
         QCHECK_LAUNCH("k_vjp_backward");
         if (d->mode == 1 && g_actor) {
-            if (warp_path) {
-                a.npart = 2 * a.nchunk;  // two CTAs (row halves) per chunk
-                if (a.hid == 64) k_vjp_wgrad_rows<64><<<a.npart, LT, smem_wr, cs>>>(a, g);
-                else k_vjp_wgrad_rows<32><<<a.npart, LT, smem_wr, cs>>>(a, g);
+            if (side) {
+                QCHECK_CUDA(cudaEventRecord(side->fork[g & 1], cs));
+                if (g + 1 < a.nseg) {  // segment g + 1's weight gradient, behind sweep g
+                    QCHECK_CUDA(cudaStreamWaitEvent(side->s, side->fork[(g + 1) & 1], 0));
+                    qsim_status st2 = weight_grad(g + 1, side->s);
+                    if (st2 != QSIM_OK) return st2;
+                    QCHECK_CUDA(cudaEventRecord(side->join[(g + 1) & 1], side->s));
+                }
+                if (g == 0) {
+                    QCHECK_CUDA(cudaStreamWaitEvent(cs, side->join[1], 0));
+                    qsim_status st2 = weight_grad(0, cs);
+                    if (st2 != QSIM_OK) return st2;
+                }
             } else {
-                k_vjp_wgrad<<<a.nchunk, LT, smem_wg, cs>>>(a, g, a.ld, 1);
+                qsim_status st2 = weight_grad(g, cs);
+                if (st2 != QSIM_OK) return st2;
             }
-            QCHECK_LAUNCH("k_vjp_wgrad");
-            k_vjp_wreduce<<<(a.PA + 31) / 32, 256, 0, cs>>>(a);
-            QCHECK_LAUNCH("k_vjp_wreduce");
         }
     }
     return QSIM_OK;

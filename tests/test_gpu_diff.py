@@ -84,12 +84,14 @@ def test_closed_loop_vjp_matches_oracle(gpu):
     close(f64(gp)[:, :n].T, ref["g_prm"][:, :4], "g_params")
 
 
-@pytest.mark.parametrize("hid,lanes", [(64, 32), (64, 16), (64, 8), (32, 16), (32, 8)])
-def test_closed_loop_lane_groups_match_oracle(gpu, hid, lanes):
+@pytest.mark.parametrize("hid,lanes,n", [(64, 32, 45), (64, 16, 45), (64, 8, 45), (32, 16, 45),
+                                         (32, 8, 45), (64, 8, 2601), (32, 8, 2601)])
+def test_closed_loop_lane_groups_match_oracle(gpu, hid, lanes, n):
     """The lane-group kernels (hidden 32 / 64, 16 actions of history): one env per 32, 16 or
     8 lanes.  45 envs leave the last warp's groups partly without an env (they run on a
-    valid index and store nothing)."""
-    n, H, nh = 45, 23, 16
+    valid index and store nothing).  2,601 envs at 8 lanes take the 7-warp CTAs (one per
+    SM; 93 CTAs, the last one ragged) instead of the 4-warp ones."""
+    H, nh = 23, 16
     q, diff, d, veh, ld, S0, PR, desc, wts = setup(n, H, 1, seed=5, n_hist=nh, hidden=hid,
                                                    ckpt=6, lanes=lanes)
     actor = O.init_params(d, 0, 18 + 4 * nh, hid, 4).astype(np.float32)
@@ -220,3 +222,39 @@ def test_c3_full_size_sampled(gpu):
     q.qsim_rollout_vjp(desc, veh, S0, PR, None, AW, seed, loss, None, gw, gp, None, ws)
     torch.cuda.synchronize()
     close(f64(gw), ref["g_actor"], "g_actor (6 envs)")
+
+
+def test_closed_loop_gradient_is_reproducible_and_captures_in_a_graph(gpu):
+    """The closed loop's weight gradient of each segment runs on a side stream while the
+    next segment's reverse sweep runs, with two record buffers in turn.  Over 5 segments
+    (both buffers reused) repeated calls, a call on another stream and a replay of the
+    call captured in a CUDA graph give bitwise the same results."""
+    n, H = 300, 50
+    q, diff, d, veh, ld, S0, PR, desc, wts = setup(n, H, 1, seed=4, n_hist=16, hidden=64,
+                                                   ckpt=10, lanes=8)
+    actor = O.init_params(d, 0, 82, 64, 4).astype(np.float32)
+    AW = torch.tensor(actor, device="cuda")
+    loss = torch.zeros(ld, device="cuda")
+    gw = torch.zeros_like(AW)
+    gp = torch.zeros(4, ld, device="cuda")
+    ws = torch.empty(q.qsim_vjp_workspace(desc) // 4 + 1, device="cuda")
+    args = (desc, veh, S0, PR, None, AW, None, loss, None, gw, gp, None, ws)
+    q.qsim_rollout_vjp(*args)
+    torch.cuda.synchronize()
+    ref = (loss.clone(), gw.clone(), gp.clone())
+    assert torch.isfinite(ref[1]).all() and ref[1].abs().sum() > 0
+    for t in (loss, gw, gp):
+        t.zero_()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        q.qsim_rollout_vjp(*args)
+    torch.cuda.synchronize()
+    assert torch.equal(loss, ref[0]) and torch.equal(gw, ref[1]) and torch.equal(gp, ref[2])
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        q.qsim_rollout_vjp(*args)
+    for t in (loss, gw, gp):
+        t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(loss, ref[0]) and torch.equal(gw, ref[1]) and torch.equal(gp, ref[2])
