@@ -505,6 +505,7 @@ qsim_status ac_load(ac_handle* a, qsim_handle* env, const char* path);
  * such call on the device) while the next segment's reverse sweep runs; it forks from and
  * joins back into `stream` through events, so the call completes in `stream` order and
  * can be captured in a CUDA graph once that stream exists (make one uncaptured call first).
+ * Like every handle of this library, that stream does not survive a cudaDeviceReset.
  * Results are bitwise reproducible for a given descriptor. */
 typedef struct qsim_vjp_desc {
     int32_t n, ld, H, ckpt, mode, n_hist, hidden;
