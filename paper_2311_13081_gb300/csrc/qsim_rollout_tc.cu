@@ -83,7 +83,16 @@ constexpr int OFF_UNIT = OFF_ABORT + 16;
 // B lo) for each of its 4 K-steps
 constexpr int OFF_DESC = (OFF_UNIT + 16 + 7) & ~7;
 constexpr int N_DESC1 = 2 * (2 + 16), N_DESC2 = TILES * 4 * 4;
-constexpr int SMEM = OFF_DESC + 8 * (N_DESC1 + N_DESC2);
+// the start of each compute thread's next episode, computed ahead (reset_env for episode
+// ep_index + 1): [NXF][TILE * TILES] floats, field-major (state 17, parameters 7,
+// disturbance 6)
+constexpr int NXF = NS + 7 + 6;
+constexpr int NX_LD = TILE * TILES;
+constexpr int OFF_NXT = (OFF_DESC + 8 * (N_DESC1 + N_DESC2) + 15) & ~15;
+constexpr int SMEM = OFF_NXT + 4 * NXF * NX_LD;
+// steps between the passes that compute the next episodes' starts of the threads whose
+// precomputed start was used (a power of two)
+constexpr int NX_EVERY = 8;
 static_assert(SMEM <= 227 * 1024, "tensor-core rollout: shared memory");
 static_assert(SZ_W1 % 128 == 0 && OFF_A2 % 128 == 0 && SZ_A2 % 128 == 0, "alignment");
 
@@ -428,6 +437,9 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
 
             float s[NS], d[6];
             Prm P = make_prm(1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f, 1.0f);
+            // this thread's precomputed next-episode start (valid while nxt_ok)
+            float* nx = reinterpret_cast<float*>(smb + OFF_NXT) + tid;
+            bool nxt_ok = false;
             uint32_t ep_index = 0, ep_step = 0, n_done = 0, len_sum = 0;
             float ep_ret = 0.0f, ret_sum = 0.0f;
 #pragma unroll
@@ -697,14 +709,29 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                     }
                 }
                 ep_ret += rw;
+                // Episode starts (reset_env) depend only on (env, episode index), so each
+                // thread's next one is computed ahead: a thread that resets takes its
+                // precomputed start if it has one, else computes it now; every NX_EVERY steps
+                // (and after a unit's first step) the threads whose precomputed start was
+                // used compute their next one, together in one pass of the warp, instead of
+                // the whole warp running reset_env whenever one of its envs resets.
+                bool now = false;
                 if (reset) {
                     n_done += 1;
                     len_sum += ep_after;
                     ret_sum += ep_ret;
                     ep_index += 1;
-                    float prm7[7];
-                    reset_env(C, (uint32_t)g, ep_index, s, prm7, d);
-                    P = make_prm(prm7[0], prm7[1], prm7[2], prm7[3], prm7[4], prm7[5], prm7[6]);
+                    if (nxt_ok) {
+#pragma unroll
+                        for (int i = 0; i < NS; ++i) s[i] = nx[i * NX_LD];
+                        P = make_prm(nx[NS * NX_LD], nx[(NS + 1) * NX_LD], nx[(NS + 2) * NX_LD], nx[(NS + 3) * NX_LD],
+                                     nx[(NS + 4) * NX_LD], nx[(NS + 5) * NX_LD], nx[(NS + 6) * NX_LD]);
+#pragma unroll
+                        for (int i = 0; i < 6; ++i) d[i] = nx[(NS + 7 + i) * NX_LD];
+                        nxt_ok = false;
+                    } else {
+                        now = true;
+                    }
                     ep_step = 0;
                     ep_ret = 0.0f;
                 } else {
@@ -713,6 +740,31 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                         for (int i = 0; i < NS; ++i) s[i] = s2[i];
                     }
                     ep_step = ep_after;
+                }
+                if constexpr (!TRACK) {
+                    const bool fill = !now && !nxt_ok && active &&
+                                      (tt == 0 || (t & (uint32_t)(NX_EVERY - 1)) == (uint32_t)(NX_EVERY - 1));
+                    if (__any_sync(0xffffffffu, now || fill)) {
+                        if (now || fill) {
+                            float sn[NS], prm7[7], dn[6];
+                            reset_env(C, (uint32_t)g, now ? ep_index : ep_index + 1u, sn, prm7, dn);
+                            if (now) {
+#pragma unroll
+                                for (int i = 0; i < NS; ++i) s[i] = sn[i];
+                                P = make_prm(prm7[0], prm7[1], prm7[2], prm7[3], prm7[4], prm7[5], prm7[6]);
+#pragma unroll
+                                for (int i = 0; i < 6; ++i) d[i] = dn[i];
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < NS; ++i) nx[i * NX_LD] = sn[i];
+#pragma unroll
+                                for (int i = 0; i < 7; ++i) nx[(NS + i) * NX_LD] = prm7[i];
+#pragma unroll
+                                for (int i = 0; i < 6; ++i) nx[(NS + 7 + i) * NX_LD] = dn[i];
+                                nxt_ok = true;
+                            }
+                        }
+                    }
                 }
             }
             wait_st();
