@@ -97,6 +97,32 @@ __device__ __forceinline__ uint4 draw_rolled(const EnvCfg& C, uint32_t c0, uint3
     return make_uint4(x0, x1, x2, x3);
 }
 
+// N blocks of the same stream with counters (c0, c1, c2[n], run), computed together round
+// by round: the independent blocks interleave (instruction-level parallelism) in one
+// rolled loop; each block equals draw_rolled's.
+template <int N>
+__device__ __forceinline__ void draw_rolled_n(const EnvCfg& C, uint32_t c0, uint32_t c1,
+                                              const uint32_t (&c2)[N], uint4 (&out)[N]) {
+    uint32_t x0[N], x1[N], x2[N], x3[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) { x0[n] = c0; x1[n] = c1; x2[n] = c2[n]; x3[n] = C.run_id; }
+    uint32_t k0 = C.key0, k1 = C.key1;
+#pragma unroll 1
+    for (int r = 0; r < 10; ++r) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            const uint32_t lo0 = 0xD2511F53u * x0[n], hi0 = __umulhi(0xD2511F53u, x0[n]);
+            const uint32_t lo1 = 0xCD9E8D57u * x2[n], hi1 = __umulhi(0xCD9E8D57u, x2[n]);
+            const uint32_t n0 = hi1 ^ x1[n] ^ k0, n2 = hi0 ^ x3[n] ^ k1;
+            x0[n] = n0; x1[n] = lo1; x2[n] = n2; x3[n] = lo0;
+        }
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+#pragma unroll
+    for (int n = 0; n < N; ++n) out[n] = make_uint4(x0[n], x1[n], x2[n], x3[n]);
+}
+
 // ((x >> 9) + 1/2) * 2^-23: exact in float, strictly inside (0, 1).
 __device__ __forceinline__ float u01(uint32_t x) {
     return ((float)(x >> 9) + 0.5f) * 1.1920928955078125e-07f;
@@ -323,10 +349,15 @@ __device__ __forceinline__ void qmul(const float* a, const float* b, float* o) {
 // Initial state, domain-randomised parameters and disturbance of episode `ep` of env.
 __device__ __forceinline__ void reset_env(const EnvCfg& C, uint32_t env, uint32_t ep, float* s,
                                           float* prm7, float* d) {
+    // the four initial-state blocks and the two domain-randomisation blocks, interleaved
+    const uint32_t c2[6] = {TAG_RESET << 24, (TAG_RESET << 24) | 1u, (TAG_RESET << 24) | 2u,
+                            (TAG_RESET << 24) | 3u, TAG_DR << 24, (TAG_DR << 24) | 1u};
+    uint4 R6[6];
+    draw_rolled_n<6>(C, env, ep, c2, R6);
     float U[16];
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        const uint4 r = draw_rolled(C, env, ep, TAG_RESET, (uint32_t)b);
+        const uint4 r = R6[b];
         U[4 * b] = u01(r.x); U[4 * b + 1] = u01(r.y); U[4 * b + 2] = u01(r.z); U[4 * b + 3] = u01(r.w);
     }
 #pragma unroll
@@ -345,7 +376,7 @@ __device__ __forceinline__ void reset_env(const EnvCfg& C, uint32_t env, uint32_
     for (int k = 0; k < 3; ++k) s[10 + k] = C.init_w * (2.0f * U[9 + k] - 1.0f);
 #pragma unroll
     for (int i = 0; i < 4; ++i) s[13 + i] = fmaf(C.init_rpm_hi - C.init_rpm_lo, U[12 + i], C.init_rpm_lo);
-    const uint4 a = draw_rolled(C, env, ep, TAG_DR, 0), b = draw_rolled(C, env, ep, TAG_DR, 1);
+    const uint4 a = R6[4], b = R6[5];
     prm7[0] = C.m0 * (1.0f + C.dr_mass * (2.0f * u01(a.x) - 1.0f));
     prm7[1] = C.Jx0 * (1.0f + C.dr_J * (2.0f * u01(a.y) - 1.0f));
     prm7[2] = C.Jy0 * (1.0f + C.dr_J * (2.0f * u01(a.z) - 1.0f));
