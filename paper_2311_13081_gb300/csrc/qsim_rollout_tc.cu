@@ -91,8 +91,11 @@ constexpr int NX_LD = TILE * TILES;
 constexpr int OFF_NXT = (OFF_DESC + 8 * (N_DESC1 + N_DESC2) + 15) & ~15;
 constexpr int SMEM = OFF_NXT + 4 * NXF * NX_LD;
 // steps between the passes that compute the next episodes' starts of the threads whose
-// precomputed start was used (a power of two)
-constexpr int NX_EVERY = 8;
+// precomputed start was used (a power of two), besides the pass after a unit's first step.
+// Measured on the 65,536 x 1,000 rollout (episodes of ~42 steps, 50-step units): every 4
+// steps 8.1, 8: 8.38, 16: 8.54, 32: 8.61, 64: 8.65 x 10^9 env-steps/s -- a pass costs the
+// warp a full reset for all its lanes, so a rare pass (mostly the one per unit) wins.
+constexpr int NX_EVERY = 64;
 static_assert(SMEM <= 227 * 1024, "tensor-core rollout: shared memory");
 static_assert(SZ_W1 % 128 == 0 && OFF_A2 % 128 == 0 && SZ_A2 % 128 == 0, "alignment");
 
@@ -711,10 +714,11 @@ __global__ void __launch_bounds__(NT, 1) k_rollout_tc(EnvCfg C, EnvPtrs p, const
                 ep_ret += rw;
                 // Episode starts (reset_env) depend only on (env, episode index), so each
                 // thread's next one is computed ahead: a thread that resets takes its
-                // precomputed start if it has one, else computes it now; every NX_EVERY steps
-                // (and after a unit's first step) the threads whose precomputed start was
-                // used compute their next one, together in one pass of the warp, instead of
-                // the whole warp running reset_env whenever one of its envs resets.
+                // precomputed start if it has one, else computes it now; after a unit's first
+                // step (and every NX_EVERY steps) the threads without a precomputed start
+                // compute their next one, together in one pass of the warp, so the first
+                // reset of each env in a unit no longer makes the whole warp run reset_env.
+                // (The sync below takes a value every lane has already computed.)
                 bool now = false;
                 if (reset) {
                     n_done += 1;
