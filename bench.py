@@ -45,10 +45,9 @@ BYTES_STEP = 92       # transition record written per env-step (17 s, 4 a, r, fl
 # dram__bytes_write.sum).  Set to None whenever the kernel changes until it is captured
 # again: its side-ring stores changed since the last capture.
 NCU_DRAM_BYTES_PER_ENV_STEP = None
-# same for the tensor-core kernel k_rollout_tc: one-pass capture of the bench's own timed
-# launch, 65,536 envs x 1,000 steps (profiles/k_rollout_tc_c2_65536x1000.md).  None until
-# the kernel with precomputed episode starts is captured.
-NCU_DRAM_BYTES_PER_ENV_STEP_TC = None
+# same for the tensor-core kernel k_rollout_tc: one-pass capture of a full-size timed launch,
+# 65,536 envs x 1,000 steps (profiles/k_rollout_tc_c2_65536x1000.md)
+NCU_DRAM_BYTES_PER_ENV_STEP_TC = (110.884864e6 + 6301.343488e6) / (65536 * 1000)
 
 
 def parse():
