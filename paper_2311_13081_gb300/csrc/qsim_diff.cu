@@ -5,15 +5,18 @@
 //   forward   : integrate H steps, store the state every `ckpt` steps and the actions,
 //               accumulate the loss.
 //   backward  : for each segment, last to first: recompute the segment's states from its
-//               checkpoint, then sweep it in reverse -- vector-Jacobian product of RK4
-//               (four stage derivatives recomputed, quaternion renormalisation included),
-//               of the action -> RPM map, and in closed loop of the actor (per-thread
-//               backprop with weights in shared memory; history inputs pass their adjoint
-//               to earlier actions).  The adjoint state and parameter gradients carry over
-//               between segments in the workspace.
+//               checkpoint (in closed loop also the actor's inputs and hidden activations,
+//               two steps per pass through the layers), then sweep it in reverse --
+//               vector-Jacobian product of RK4 (four stage derivatives recomputed,
+//               quaternion renormalisation included), of the action -> RPM map, and in
+//               closed loop of the actor (backprop with weights in shared memory; history
+//               inputs pass their adjoint to earlier actions).  The adjoint state and
+//               parameter gradients carry over between segments in the workspace.
 //   weights   : closed loop only -- the per-(step, env) activations and deltas of a
-//               segment are reduced into the actor gradient by CTA-wide GEMMs over env
-//               chunks, then summed over chunks in a fixed order (deterministic).
+//               segment are reduced into the actor gradient over env chunks (on a side
+//               stream while the next segment's reverse sweep runs, with two record
+//               buffers in turn), then summed over chunks in a fixed order
+//               (deterministic).
 // Memory: O(H/ckpt + ckpt) states per env instead of O(H).
 #include <algorithm>
 #include <cstring>
